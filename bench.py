@@ -1,0 +1,454 @@
+#!/usr/bin/env python3
+"""Throughput of the stencil hot path on one GB300 (or N replicas under torchrun).
+
+One step = the non-separable correlation of one 8192x8192 f32 image (pixels uniform
+[0, 1)) with a 5x5 and an 11x11 filter (N(0,1) taps divided by their L1 norm),
+clamp-to-edge, each through ``imagecl_conv2d`` with the variant the auto-tuner picked.
+``value`` is output Mpixel/s of the whole job (both filters, all ranks).  Inputs and
+outputs (268 MB each) are larger than L2, so no flush is needed between steps.
+
+Also reported: per-stencil tuned vs plain throughput and roofline fractions, the
+dominant kernel's roofline (CUDA events on its own stream over the timed region), the
+end-to-end rate through the C ABI with host buffers, SM clocks sampled during the timed
+region, and the CPU oracle timed on a bounded sample (``cpu_baseline``).
+
+``--impl reference`` times the CPU oracle itself (the reference arm) on the same
+workload, one bounded sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpixel/s and % HBM roofline per stencil, tuned vs plain, at stated tol"
+WORKLOAD = ("non-separable 2D correlation, one 8192x8192 f32 image (uniform [0,1)), "
+            "5x5 and 11x11 N(0,1) taps normalised to unit L1 sum, clamp-to-edge")
+SIDE = 8192
+KS = (5, 11)
+FALLBACK_HBM_GBS, FALLBACK_BF16_TFS = 6800.0, 1900.0
+FP32_FMA_PER_SM_CLK = 128          # FP32 lanes per SM (4 sub-partitions x 32)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tune-budget", type=float, default=20.0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+        pg = dist
+    return rank, world, local, pg
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    return FALLBACK_HBM_GBS, FALLBACK_BF16_TFS, 2070.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id: str):
+        self.device_id = device_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.device_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.12)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def gpu_id_for_smi(local_rank):
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(local_rank).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        if vis:
+            return vis.split(",")[local_rank]
+        return str(local_rank)
+
+
+def kernel_source_hash():
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_1605_06399_gb300", "csrc")
+    for f in ("common.cuh", "conv2d_kernels.cuh", "conv2d_tiled.cu"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_record(k):
+    """DRAM bytes per launch from a committed ncu capture, if the kernel is unchanged."""
+    p = os.path.join(ROOT, "profiles", f"conv2d_tiled_k{k}_8192_f32.traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def workload():
+    from paper_1605_06399_gb300 import synth
+    img, w5 = synth.workload_conv_f32(5)
+    _, w11 = synth.workload_conv_f32(11)
+    return img, {5: w5, 11: w11}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def oracle_rate(img, taps_by_k, seconds, gpu_outs=None):
+    import oracle
+    h, w = img.shape
+    # calibrate on a thin band, then size the timed sample to about `seconds`
+    t0 = time.perf_counter()
+    for k, taps in taps_by_k.items():
+        r = k // 2
+        oracle.conv2d(img[h // 2 - r:h // 2 + 8 + r], taps, rows=(r, r + 8))
+    t_cal = time.perf_counter() - t0
+    n = max(8, min(h, int(8 * seconds / max(t_cal, 1e-6))))
+    y0 = (h - n) // 2
+    t0 = time.perf_counter()
+    for k, taps in taps_by_k.items():
+        r = k // 2
+        a, b = max(0, y0 - r), min(h, y0 + n + r)
+        oracle.conv2d(img[a:b], taps, rows=(y0 - a, y0 + n - a))
+    dt = time.perf_counter() - t0
+    px = n * w * len(taps_by_k)
+    errs = {}
+    if gpu_outs is not None:
+        for k, taps in taps_by_k.items():
+            r = k // 2
+            a, b = max(0, y0 - r), min(h, y0 + n + r)
+            ref = oracle.conv2d(img[a:b], taps, rows=(y0 - a, y0 + n - a))
+            s = oracle.conv2d(np.abs(img[a:b].astype(np.float64)), np.abs(taps.astype(np.float64)),
+                              rows=(y0 - a, y0 + n - a))
+            g = gpu_outs[k][y0:y0 + n].astype(np.float64)
+            errs[k] = float(np.max(np.abs(g - ref) / np.maximum(s, 1e-30)))
+    return px / dt / 1e6, n, oracle.num_threads(), dt, errs
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    from paper_1605_06399_gb300 import _abi, ops
+
+    rank, world, local, pg = dist_setup(args.gpus)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    hbm_gbs, _, sm_max_mhz, peak_src = measured_peaks()
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+    fp32_peak = n_sm * FP32_FMA_PER_SM_CLK * 2 * sm_max_mhz * 1e6 / 1e12   # TFLOP/s
+
+    img, taps = workload()
+    x = torch.from_numpy(img).to(dev)
+    ys = {k: torch.empty_like(x) for k in KS}
+    stream = torch.cuda.current_stream()
+    lib = _abi.lib()
+
+    # tune each stencil (untimed), then time plain and tuned
+    tuned = {}
+    for k in KS:
+        prob = ops.problem(_abi.OP_CONV2D, "f32", "f32", k, k, SIDE, SIDE)
+        tuned[k] = ops.tune(prob, budget_s=args.tune_budget, reps=5)
+    xi = ops.image(x)
+    yi = {k: ops.image(ys[k]) for k in KS}
+    tp = {k: np.ascontiguousarray(taps[k], np.float32) for k in KS}
+    variants = {k: _abi.Variant.from_dict(tuned[k]["variant"]) for k in KS}
+    plain = _abi.Variant.from_dict({"kind": _abi.KIND_PLAIN, "bx": 16, "by": 16})
+    sh = ctypes.c_void_p(stream.cuda_stream)
+
+    def launch(k, variant):
+        return lib.imagecl_conv2d(ctypes.byref(xi), ctypes.byref(yi[k]),
+                                  ctypes.c_void_p(tp[k].ctypes.data), _abi.F32, k, k,
+                                  _abi.MEM_HOST, _abi.BORDER_CLAMP, 0.0, ctypes.byref(variant), sh)
+
+    def time_kernel(k, variant, n):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        for _ in range(3):
+            _abi.check(launch(k, variant))
+        torch.cuda.synchronize()
+        evs[0].record(stream)
+        for _ in range(n):
+            _abi.check(launch(k, variant))
+        evs[1].record(stream)
+        torch.cuda.synchronize()
+        return evs[0].elapsed_time(evs[1]) / n
+
+    plain_ms = {k: time_kernel(k, plain, 10) for k in KS}
+
+    # ---------------- timed region: K steps, each = conv 5x5 + conv 11x11
+    for _ in range(args.warmup):
+        for k in KS:
+            _abi.check(launch(k, variants[k]))
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(KS) + 1)] for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(gpu_id_for_smi(local)) if rank == 0 else None
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+        time.sleep(0.2)
+    start.record(stream)
+    for s in range(args.steps):
+        ev[s][0].record(stream)
+        for i, k in enumerate(KS):
+            launch(k, variants[k])
+            ev[s][i + 1].record(stream)
+    end.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    st = ops.device_status()
+    assert st == 0, f"kernel status {st}"
+    elapsed_ms = start.elapsed_time(end)
+    per_k_ms = {k: sum(ev[s][i].elapsed_time(ev[s][i + 1]) for s in range(args.steps)) / args.steps
+                for i, k in enumerate(KS)}
+    if pg:
+        t = torch.tensor([elapsed_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+
+    px = SIDE * SIDE
+    ms_per_step = elapsed_ms / args.steps
+    value = world * px * len(KS) / (ms_per_step / 1e3) / 1e6
+
+    # ---------------- end to end: host buffers, copies inside the timed region
+    h_in = torch.from_numpy(img).pin_memory()
+    h_out = {k: torch.empty((SIDE, SIDE), dtype=torch.float32).pin_memory() for k in KS}
+    for i in range(args.e2e_steps + 2):
+        if i == 2:
+            torch.cuda.synchronize()
+            if pg:
+                pg.barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        x.copy_(h_in, non_blocking=True)
+        for k in KS:
+            launch(k, variants[k])
+            h_out[k].copy_(ys[k], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
+    if pg:
+        t = torch.tensor([e2e_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * px * len(KS) / (e2e_ms / 1e3) / 1e6
+
+    if rank != 0:
+        pg.destroy_process_group()
+        return
+
+    # ---------------- roofline of the dominant kernel
+    bytes_px = 8.0                       # 4 B read + 4 B written per output pixel
+    per_stencil = {}
+    for k in KS:
+        flops = 2.0 * k * k * px
+        t = per_k_ms[k] / 1e3
+        per_stencil[f"{k}x{k}"] = {
+            "tuned_mpx_s": px / t / 1e6,
+            "plain_mpx_s": px / (plain_ms[k] / 1e3) / 1e6,
+            "speedup_vs_plain": plain_ms[k] / per_k_ms[k],
+            "tuned_ms": per_k_ms[k],
+            "plain_ms": plain_ms[k],
+            "hbm_gbs": bytes_px * px / t / 1e9,
+            "hbm_frac": bytes_px * px / t / 1e9 / hbm_gbs,
+            "fp32_tflops": flops / t / 1e12,
+            "fp32_frac": flops / t / 1e12 / fp32_peak,
+            "variant": tuned[k]["variant"],
+        }
+    dom = max(KS, key=lambda k: per_k_ms[k])
+    d = per_stencil[f"{dom}x{dom}"]
+    ai = 2.0 * dom * dom / bytes_px                          # flop per HBM byte
+    ridge = fp32_peak * 1e3 / hbm_gbs
+    traffic = traffic_record(dom)
+    if ai > ridge:
+        roof = {"bound": "alu", "achieved": d["fp32_tflops"], "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": d["fp32_frac"], "traffic": traffic,
+                "kernel": f"k_conv2d_tiled {dom}x{dom} f32",
+                "peak_source": f"{n_sm} SMs x 128 FMA/clk x 2 x {sm_max_mhz:.0f} MHz ({peak_src} max clock)"}
+    else:
+        roof = {"bound": "hbm", "achieved": d["hbm_gbs"], "peak": hbm_gbs, "unit": "GB/s",
+                "frac": d["hbm_frac"], "traffic": traffic,
+                "kernel": f"k_conv2d_tiled {dom}x{dom} f32", "peak_source": f"{peak_src} copy bandwidth"}
+
+    gpu_outs = None
+    cpu = None
+    errs = {}
+    if not args.no_cpu_baseline:
+        for k in KS:
+            launch(k, variants[k])
+        torch.cuda.synchronize()
+        gpu_outs = {k: ys[k].cpu().numpy() for k in KS}
+        rate, rows, threads, secs, errs = oracle_rate(img, taps, args.cpu_seconds, gpu_outs)
+        cpu = {"value": rate, "unit": "Mpixel/s", "cores": threads, "kind": "oracle",
+               "sample": f"rows {rows} of 8192 (all 8192 columns) through both filters, fp64, "
+                         f"{secs:.1f} s"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "image": f"{SIDE}x{SIDE} f32", "filters": list(KS),
+                   "border": "clamp", "l2": "inputs and outputs larger than L2 (no flush)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "Mpixel/s",
+                "h2d_bytes_per_step": px * 4, "d2h_bytes_per_step": px * 4 * len(KS)},
+        "clocks": clocks,
+        "gpu_launches": args.steps * len(KS),
+        "per_stencil": per_stencil,
+        "max_scaled_err": {f"{k}x{k}": errs.get(k) for k in KS} if errs else None,
+        "tolerance": 1e-5,
+    }
+    print(json.dumps(line))
+    if pg:
+        pg.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    img, taps = workload()
+    h, w = img.shape
+    # one bounded sample per step: a band of rows sized from a calibration run
+    t0 = time.perf_counter()
+    for k in KS:
+        r = k // 2
+        oracle.conv2d(img[h // 2 - r:h // 2 + 8 + r], taps[k], rows=(r, r + 8))
+    t_cal = time.perf_counter() - t0
+    budget = 150.0 / max(1, args.steps + args.warmup)            # seconds per step
+    rows = int(max(8, min(h, 8 * budget / max(t_cal, 1e-6))))
+    y0 = (h - rows) // 2
+
+    def step():
+        for k in KS:
+            r = k // 2
+            a, b = max(0, y0 - r), min(h, y0 + rows + r)
+            oracle.conv2d(img[a:b], taps[k], rows=(y0 - a, y0 + rows - a))
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    value = rows * w * len(KS) / dt / 1e6
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD, "image": f"{SIDE}x{SIDE} f32", "filters": list(KS),
+                   "border": "clamp", "sample_rows": rows},
+        "cpu_baseline": {"value": value, "unit": "Mpixel/s", "cores": oracle.num_threads(),
+                         "kind": "oracle",
+                         "sample": f"rows {rows} of 8192 (all columns), both filters, per step"},
+        "e2e": {"value": value, "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

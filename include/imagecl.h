@@ -1,0 +1,172 @@
+/*
+ * imagecl.h -- C ABI of the GB300 (sm_103a) per-pixel stencil library.
+ *
+ * The operators follow the problem statement of ImageCL (Falch & Elster, arXiv
+ * 1605.06399): a kernel runs once per pixel of an output grid (idx, idy) = (x, y)
+ * (§5), reads `Image` inputs at fixed offsets (Listing 1 reads in[idx+i][idy+j]: a
+ * correlation, no filter flip) and out-of-image reads follow a boundary condition,
+ * clamped or constant (§5, Fig. 3).  The library is the "standalone function callable
+ * from any C/C++ application" of §5.1, with the kernel variants of §5.2 / Table 1
+ * (work-group size, thread coarsening, thread mapping, image/L1 versus local memory
+ * staging, constant memory for the taps, loop unrolling) compiled ahead of time, and an
+ * auto-tuner (§4) that times them on the device and caches the winner.
+ *
+ * Conventions for every entry point
+ *  - Images are row-major, x fastest, with a row pitch in bytes; `data` is a DEVICE
+ *    pointer owned by the caller.  The pitch must be a multiple of the element size and
+ *    at least width * element size.
+ *  - Operations are out of place: input and output buffers may not overlap (the paper
+ *    disallows aliasing, §5.2 "Image memory"); overlap -> IMCL_ERR_INVALID.
+ *  - Filter sides are odd (the taps are centred: offset = tap - (K-1)/2), 1..15.
+ *    Taps are row-major, taps[j*kw + i], j the row (dy), i the column (dx).
+ *  - Integer images (u8, i32) take i32 taps, accumulate in i32 with wraparound
+ *    (mod 2^32) and write i32.  Floating images (f32, f16, bf16) take f32 taps,
+ *    accumulate in f32 and write f32, f16 or bf16 (round to nearest even).
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL is the legacy default
+ *    stream) and never synchronise, except imagecl_tune and imagecl_device_status.
+ *  - No call throws.  Each returns an imcl_status; on failure imagecl_last_error()
+ *    (per thread) describes it and nothing has been launched.
+ *  - Kernels never trap.  A kernel that gives up on a bounded wait records a code in a
+ *    per-device status word that imagecl_device_status() reads and clears.
+ */
+#ifndef IMAGECL_H
+#define IMAGECL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    IMCL_OK = 0,
+    IMCL_ERR_INVALID = 1,     /* bad argument: null, size, pitch, dtype mix, aliasing  */
+    IMCL_ERR_UNSUPPORTED = 2, /* well formed but not provided (even K, K > 15, variant) */
+    IMCL_ERR_ALIGN = 3,       /* a requested variant needs alignment the buffers lack   */
+    IMCL_ERR_OOM = 4,         /* device allocation failed (tuner, batch plans)          */
+    IMCL_ERR_CUDA = 5,        /* a CUDA runtime call failed                             */
+    IMCL_ERR_TIMEOUT = 6      /* a kernel gave up on a bounded wait                     */
+} imcl_status;
+
+typedef enum { IMCL_U8 = 0, IMCL_I32 = 1, IMCL_F32 = 2, IMCL_F16 = 3, IMCL_BF16 = 4 } imcl_dtype;
+
+/* Boundary conditions of §5 / Fig. 3. */
+typedef enum { IMCL_BORDER_CLAMP = 0, IMCL_BORDER_CONSTANT = 1 } imcl_border;
+
+/* Where the filter taps live.  HOST taps are copied into the launch's parameter space
+ * (the constant bank: the "constant memory" option of §5.2).  DEVICE taps are read by
+ * the kernel (staged into shared memory) so the call stays asynchronous. */
+typedef enum { IMCL_MEM_HOST = 0, IMCL_MEM_DEVICE = 1 } imcl_mem;
+
+typedef struct {
+    void *data;          /* device pointer, caller-owned                      */
+    int32_t dtype;       /* imcl_dtype                                        */
+    int32_t width;       /* pixels per row (x extent)                         */
+    int32_t height;      /* rows (y extent)                                   */
+    int32_t reserved;    /* must be 0                                         */
+    int64_t pitch_bytes; /* bytes between the starts of consecutive rows      */
+} imcl_image;
+
+/* Kernel variant: one point of the tuning space of §5.2 / Table 1. */
+typedef enum { IMCL_KIND_PLAIN = 0, IMCL_KIND_TILED = 1 } imcl_kind;
+typedef enum { IMCL_LOAD_GLOBAL = 0, IMCL_LOAD_SMEM = 1, IMCL_LOAD_TMA = 2 } imcl_load;
+typedef enum { IMCL_FILT_PARAM = 0, IMCL_FILT_SMEM = 1 } imcl_filt;
+typedef enum { IMCL_MAP_BLOCKED = 0, IMCL_MAP_INTERLEAVED = 1 } imcl_map;
+
+typedef struct {
+    int32_t kind;       /* imcl_kind.  PLAIN: the untuned kernel (one pixel per thread,
+                           direct clamped loads, taps read per use, rolled loops)      */
+    int32_t bx, by;     /* threads per block along x and y (work-group size)          */
+    int32_t px, py;     /* pixels per thread along x and y (thread coarsening)        */
+    int32_t load;       /* imcl_load: L1/texture-path loads, a cooperative shared-memory
+                           halo tile, or a TMA-staged shared-memory halo tile          */
+    int32_t filt;       /* imcl_filt: taps in the constant bank or in shared memory   */
+    int32_t map;        /* imcl_map: a thread's rows contiguous or interleaved by `by` */
+    int32_t unroll;     /* 1: taps fully unrolled (compile-time K); 0: rolled loops   */
+    int32_t persistent; /* 1: one CTA per SM slot looping over tiles; 0: one tile each */
+} imcl_variant;
+
+/* What the tuner and the variant table are keyed on. */
+typedef enum { IMCL_OP_CONV2D = 0, IMCL_OP_SEPCONV = 1, IMCL_OP_HARRIS = 2 } imcl_op;
+
+typedef struct {
+    int32_t op;          /* imcl_op                                                  */
+    int32_t in_dtype;    /* imcl_dtype of the input image                            */
+    int32_t out_dtype;   /* imcl_dtype of the output image                           */
+    int32_t kw, kh;      /* conv2d: filter sides; sepconv: row taps, column taps;
+                            harris: window side (both)                              */
+    int32_t width, height;
+    int32_t border;      /* imcl_border                                              */
+    int32_t taps_mem;    /* imcl_mem                                                 */
+} imcl_problem;
+
+/* ------------------------------------------------------------------ operators */
+
+/*
+ * Non-separable correlation (§6 "non-separable convolution"; Listing 1 with weights):
+ *   out(x, y) = sum_{j<kh, i<kw} taps[j*kw+i] * in(x + i - (kw-1)/2, y + j - (kh-1)/2)
+ * with `border` applied to out-of-image reads of `in` (border_value for CONSTANT).
+ * in:  u8/i32 (taps_dtype IMCL_I32, out IMCL_I32) or f32/f16/bf16 (taps IMCL_F32,
+ *      out f32/f16/bf16).  Same width and height as out.
+ * taps: kw*kh values in host or device memory as `taps_mem` says.  Host taps may be
+ *      freed when the call returns; device taps must stay valid until the kernel ran.
+ * variant: NULL selects the tuned variant for this problem (imagecl_tune's cache) or a
+ *      default; otherwise that variant is used or IMCL_ERR_UNSUPPORTED/ALIGN returned.
+ */
+imcl_status imagecl_conv2d(const imcl_image *in, const imcl_image *out, const void *taps,
+                           int32_t taps_dtype, int32_t kw, int32_t kh, int32_t taps_mem,
+                           int32_t border, double border_value, const imcl_variant *variant,
+                           void *stream);
+
+/* ------------------------------------------------------------------ tuning */
+
+/* Number of compiled variants applicable to `problem` (0 if none), and the idx-th one.
+ * Block shapes (bx, by) of TILED entries are a default; the tuner also sweeps them. */
+int32_t imagecl_variant_count(const imcl_problem *problem);
+imcl_status imagecl_variant_get(const imcl_problem *problem, int32_t idx, imcl_variant *out);
+
+/* The variant imagecl_conv2d / _sepconv / _harris would use for `problem` right now
+ * (the cached tuning result if there is one, else the built-in default). */
+imcl_status imagecl_variant_default(const imcl_problem *problem, imcl_variant *out);
+
+/*
+ * Auto-tune (§4, Fig. 2: pick a configuration, run and time it on the device, repeat,
+ * keep the best): allocates scratch images of the problem's size, runs every
+ * applicable variant and block shape (up to `budget_s` seconds), checks each against
+ * the PLAIN kernel on the same input, times the survivors with CUDA events on `stream`
+ * (median of `reps` runs after warm-up, L2 flushed between runs), and stores the
+ * fastest in the per-process cache, which imagecl_conv2d and friends then use.
+ * Synchronises `stream`.  `best` and `best_ms` / `plain_ms` (nullable) receive the
+ * winner, its time and the PLAIN kernel's time.  Returns IMCL_ERR_OOM if the scratch
+ * images do not fit.
+ */
+imcl_status imagecl_tune(const imcl_problem *problem, double budget_s, int32_t reps,
+                         imcl_variant *best, double *best_ms, double *plain_ms, void *stream);
+
+/* Store / drop a tuning result by hand (the "force an optimisation" directive of §5). */
+imcl_status imagecl_tune_set(const imcl_problem *problem, const imcl_variant *variant);
+void imagecl_tune_clear(void);
+
+/* Write / read the tuning cache as text (one problem and variant per line).  The file
+ * records the device name and SM count; entries for another device are skipped. */
+imcl_status imagecl_tune_save(const char *path);
+imcl_status imagecl_tune_load(const char *path);
+
+/* ------------------------------------------------------------------ status */
+
+/* Human-readable description of this thread's last failed call ("" if none). */
+const char *imagecl_last_error(void);
+
+/* Synchronises `stream`, then reads and clears the current device's kernel status word
+ * (0 = no kernel gave up; 1 = a bounded wait timed out; 2 = a bounds check tripped). */
+imcl_status imagecl_device_status(int32_t *code, void *stream);
+
+/* Library version, e.g. "imagecl-gb300 0.1 sm_103a". */
+const char *imagecl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IMAGECL_H */

@@ -1,0 +1,28 @@
+// abi_internal.h -- helpers shared by the entry-point translation units (not public).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace imcl {
+
+imcl_status check_image(const imcl_image* im, const char* name);
+bool images_overlap(const imcl_image* a, const imcl_image* b);
+imcl_status check_border(int border, double bv, int in_dtype);
+imcl_status check_side(int k, const char* what);
+
+std::string problem_key(const imcl_problem& p);
+bool cache_lookup(const imcl_problem& p, imcl_variant* v);
+void cache_store(const imcl_problem& p, const imcl_variant& v);
+
+imcl_problem conv_problem(const ConvCall& c);
+std::vector<const ConvEntry*> conv_entries_for(int in_dt, int out_dt, int kw, int kh, int taps_mem);
+const ConvEntry* conv_find(const ConvCall& c, const imcl_variant& v);
+imcl_variant conv_default_variant(const ConvCall& c);
+imcl_status conv_prepare(const imcl_image* in, const imcl_image* out, const void* taps, int taps_dtype, int kw,
+                         int kh, int taps_mem, int border, double bv, ConvCall* c);
+imcl_status conv_run(const ConvCall& c, const imcl_variant* variant, cudaStream_t s);
+
+}  // namespace imcl

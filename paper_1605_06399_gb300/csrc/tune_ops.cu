@@ -1,0 +1,108 @@
+// tune_ops.cu -- what each operator gives the tuner: its variant list, its default
+// variant, and a tuning job on scratch images of the problem's size.
+#include <cmath>
+#include <vector>
+
+#include "tune_internal.h"
+
+namespace imcl {
+
+// A ConvCall describing `p` on hypothetical, fully aligned buffers.
+static ConvCall conv_call_for(const imcl_problem& p, const DeviceInfo* dev) {
+    ConvCall c;
+    c.in = reinterpret_cast<const void*>(uintptr_t(256));
+    c.out = reinterpret_cast<void*>(uintptr_t(512));
+    c.in_dtype = p.in_dtype;
+    c.out_dtype = p.out_dtype;
+    c.W = p.width;
+    c.H = p.height;
+    c.in_pitch_b = ((int64_t)p.width * dtype_size(p.in_dtype) + 127) / 128 * 128;
+    c.out_pitch_b = ((int64_t)p.width * dtype_size(p.out_dtype) + 127) / 128 * 128;
+    c.kw = p.kw;
+    c.kh = p.kh;
+    c.taps_mem = p.taps_mem;
+    c.border = p.border;
+    c.dev = dev;
+    c.status = dev ? dev->status : nullptr;
+    return c;
+}
+
+imcl_status list_variants(const imcl_problem& p, std::vector<imcl_variant>* out) {
+    out->clear();
+    if (p.op == IMCL_OP_CONV2D) {
+        for (const ConvEntry* e : conv_entries_for(p.in_dtype, p.out_dtype, p.kw, p.kh, p.taps_mem))
+            out->push_back(e->v);
+        return IMCL_OK;
+    }
+    return fail(IMCL_ERR_UNSUPPORTED, "unknown op");
+}
+
+imcl_status default_variant(const imcl_problem& p, imcl_variant* out) {
+    if (p.op == IMCL_OP_CONV2D) {
+        DeviceInfo* dev = nullptr;
+        imcl_status st = device_info(&dev);
+        if (st != IMCL_OK) return st;
+        *out = conv_default_variant(conv_call_for(p, dev));
+        if (out->kind < 0) return fail(IMCL_ERR_UNSUPPORTED, "no conv2d variant for this problem");
+        return IMCL_OK;
+    }
+    return fail(IMCL_ERR_UNSUPPORTED, "unknown op");
+}
+
+static imcl_status make_conv_job(const imcl_problem& p, cudaStream_t s, TuneJob* job) {
+    imcl_status st;
+    if ((st = check_side(p.kw, "kw")) != IMCL_OK) return st;
+    if ((st = check_side(p.kh, "kh")) != IMCL_OK) return st;
+    DeviceInfo* dev = nullptr;
+    if ((st = device_info(&dev)) != IMCL_OK) return st;
+    ConvCall c = conv_call_for(p, dev);
+    void* in = nullptr;
+    void* out = nullptr;
+    if ((st = job->scratch.image(p.in_dtype, p.width, p.height, 1605u, &in, &c.in_pitch_b, s)) != IMCL_OK) return st;
+    if ((st = job->scratch.image(p.out_dtype, p.width, p.height, 7u, &out, &c.out_pitch_b, s)) != IMCL_OK) return st;
+    c.in = in;
+    c.out = out;
+    const int n = p.kw * p.kh;
+    double l1 = 0;
+    if (is_int_dtype(p.in_dtype)) {
+        for (int i = 0; i < n; ++i) job->taps_i.push_back((int32_t)((i * 37 + 11) % 9) - 4);
+        for (int v : job->taps_i) l1 += std::abs(v);
+        l1 *= 255.0;
+    } else {
+        for (int i = 0; i < n; ++i) job->taps_f.push_back(std::sin(1.0 + 3.7 * i));
+        for (float v : job->taps_f) l1 += std::fabs(v);
+    }
+    const void* host = is_int_dtype(p.in_dtype) ? (const void*)job->taps_i.data() : (const void*)job->taps_f.data();
+    if (p.taps_mem == IMCL_MEM_DEVICE) {
+        void* d = nullptr;
+        if ((st = job->scratch.alloc(&d, n * 4)) != IMCL_OK) return st;
+        cudaError_t e = cudaMemcpy(d, host, n * 4, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "tuner: taps upload");
+        c.taps = d;
+    } else {
+        c.taps = host;
+    }
+    job->conv = c;
+    std::vector<imcl_variant> base;
+    for (const ConvEntry* e : conv_entries_for(p.in_dtype, p.out_dtype, p.kw, p.kh, p.taps_mem))
+        base.push_back(e->v);
+    job->candidates = expand_shapes(base);
+    job->run = [job](const imcl_variant& v, cudaStream_t st2) { return conv_run(job->conv, &v, st2); };
+    job->out = out;
+    job->out_dtype = p.out_dtype;
+    job->W = p.width;
+    job->H = p.height;
+    job->out_pitch_b = c.out_pitch_b;
+    job->working_set_bytes = (double)c.in_pitch_b * p.height + (double)c.out_pitch_b * p.height;
+    if (p.out_dtype == IMCL_F16) job->tol_abs = (float)(l1 * std::ldexp(1.0, -9));
+    else if (p.out_dtype == IMCL_BF16) job->tol_abs = (float)(l1 * std::ldexp(1.0, -6));
+    else job->tol_abs = (float)(l1 * 1e-5);
+    return IMCL_OK;
+}
+
+imcl_status make_tune_job(const imcl_problem& p, cudaStream_t s, TuneJob* job) {
+    if (p.op == IMCL_OP_CONV2D) return make_conv_job(p, s, job);
+    return fail(IMCL_ERR_UNSUPPORTED, "unknown op");
+}
+
+}  // namespace imcl

@@ -1,0 +1,171 @@
+"""Python entry points over the C ABI: argument marshalling only.
+
+Every function takes CUDA tensors (2D, unit stride along x), passes their device
+pointers, sizes and row pitches to ``libimagecl.so`` and launches on the current torch
+stream (or ``stream``).  All stencil arithmetic runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import check, lib
+
+TORCH_TO_DT = {torch.uint8: _abi.U8, torch.int32: _abi.I32, torch.float32: _abi.F32,
+               torch.float16: _abi.F16, torch.bfloat16: _abi.BF16}
+DT_TO_TORCH = {v: k for k, v in TORCH_TO_DT.items()}
+NAME_TO_DT = {"u8": _abi.U8, "i32": _abi.I32, "f32": _abi.F32, "f16": _abi.F16, "bf16": _abi.BF16}
+BORDERS = {"clamp": _abi.BORDER_CLAMP, "constant": _abi.BORDER_CONSTANT}
+
+
+def image(t: torch.Tensor) -> _abi.Image:
+    """Describe a 2D CUDA tensor (H, W) with unit x stride as an ``imcl_image``."""
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("images must be CUDA tensors")
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("images must be 2D (H, W) with unit stride along x")
+    if t.dtype not in TORCH_TO_DT:
+        raise TypeError(f"unsupported pixel type {t.dtype}")
+    return _abi.Image(t.data_ptr(), TORCH_TO_DT[t.dtype], t.size(1), t.size(0), 0,
+                      t.stride(0) * t.element_size())
+
+
+def stream_handle(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream if hasattr(s, "cuda_stream") else int(s)
+
+
+def _variant(v):
+    if v is None:
+        return None
+    if isinstance(v, _abi.Variant):
+        return ctypes.byref(v)
+    return ctypes.byref(_abi.Variant.from_dict(v))
+
+
+class Taps:
+    """Filter taps as the C ABI wants them: a pointer, its memory kind and the sides.
+
+    CUDA tensors are passed as device taps; anything else (numpy, CPU tensors, lists)
+    becomes a contiguous host array kept alive by this object."""
+
+    def __init__(self, taps, integer: bool, ndim: int = 2):
+        want_np = np.int32 if integer else np.float32
+        want_t = torch.int32 if integer else torch.float32
+        if isinstance(taps, torch.Tensor) and taps.is_cuda:
+            t = taps.detach().to(want_t).contiguous()
+            self.keep = t
+            self.ptr = t.data_ptr()
+            self.mem = _abi.MEM_DEVICE
+            shape = tuple(t.shape)
+        else:
+            if isinstance(taps, torch.Tensor):
+                taps = taps.detach().cpu().numpy()
+            a = np.ascontiguousarray(taps, dtype=want_np)
+            self.keep = a
+            self.ptr = a.ctypes.data
+            self.mem = _abi.MEM_HOST
+            shape = a.shape
+        if len(shape) != ndim:
+            raise ValueError(f"taps must be {ndim}-D, got shape {shape}")
+        self.shape = shape
+        self.dtype = _abi.I32 if integer else _abi.F32
+
+
+def _out_like(x: torch.Tensor, out, out_dtype, integer: bool) -> torch.Tensor:
+    if out is not None:
+        return out
+    if integer:
+        dt = torch.int32
+    elif out_dtype is None:
+        dt = torch.float32
+    else:
+        dt = out_dtype if isinstance(out_dtype, torch.dtype) else DT_TO_TORCH[NAME_TO_DT[out_dtype]]
+    return torch.empty(x.shape, dtype=dt, device=x.device)
+
+
+def conv2d(x: torch.Tensor, taps, border: str = "clamp", border_value: float = 0.0, out=None,
+           out_dtype=None, variant=None, stream=None) -> torch.Tensor:
+    """Non-separable correlation of ``x`` (H, W) with ``taps`` (kh, kw), centred, no flip.
+
+    u8 / i32 images take integer taps and give i32; f32 / f16 / bf16 images take f32
+    taps and give f32 (default) or their own 16-bit type (``out_dtype``)."""
+    integer = x.dtype in (torch.uint8, torch.int32)
+    tp = Taps(taps, integer)
+    y = _out_like(x, out, out_dtype, integer)
+    xi, yi = image(x), image(y)
+    kh, kw = tp.shape
+    check(lib().imagecl_conv2d(ctypes.byref(xi), ctypes.byref(yi), ctypes.c_void_p(tp.ptr), tp.dtype,
+                               kw, kh, tp.mem, BORDERS[border], float(border_value),
+                               _variant(variant), ctypes.c_void_p(stream_handle(stream))))
+    return y
+
+
+def problem(op: int, in_dtype, out_dtype, kw: int, kh: int, width: int, height: int,
+            border: str = "clamp", taps_mem: int = _abi.MEM_HOST) -> _abi.Problem:
+    def dt(d):
+        if isinstance(d, torch.dtype):
+            return TORCH_TO_DT[d]
+        return NAME_TO_DT[d] if isinstance(d, str) else int(d)
+    return _abi.Problem(op, dt(in_dtype), dt(out_dtype), kw, kh, width, height, BORDERS[border],
+                        taps_mem)
+
+
+def variants(prob: _abi.Problem) -> list[dict]:
+    """Every compiled variant applicable to ``prob`` (default block shapes)."""
+    n = lib().imagecl_variant_count(ctypes.byref(prob))
+    out = []
+    for i in range(n):
+        v = _abi.Variant()
+        check(lib().imagecl_variant_get(ctypes.byref(prob), i, ctypes.byref(v)))
+        out.append(v.as_dict())
+    return out
+
+
+def default_variant(prob: _abi.Problem) -> dict:
+    v = _abi.Variant()
+    check(lib().imagecl_variant_default(ctypes.byref(prob), ctypes.byref(v)))
+    return v.as_dict()
+
+
+def tune(prob: _abi.Problem, budget_s: float = 20.0, reps: int = 5, stream=None) -> dict:
+    """Run the auto-tuner on ``prob``; returns the winner and its time against PLAIN."""
+    v = _abi.Variant()
+    best_ms, plain_ms = ctypes.c_double(0), ctypes.c_double(0)
+    check(lib().imagecl_tune(ctypes.byref(prob), float(budget_s), int(reps), ctypes.byref(v),
+                             ctypes.byref(best_ms), ctypes.byref(plain_ms),
+                             ctypes.c_void_p(stream_handle(stream))))
+    return {"variant": v.as_dict(), "best_ms": best_ms.value, "plain_ms": plain_ms.value}
+
+
+def tune_set(prob: _abi.Problem, variant) -> None:
+    v = variant if isinstance(variant, _abi.Variant) else _abi.Variant.from_dict(variant)
+    check(lib().imagecl_tune_set(ctypes.byref(prob), ctypes.byref(v)))
+
+
+def tune_clear() -> None:
+    lib().imagecl_tune_clear()
+
+
+def tune_save(path: str) -> None:
+    check(lib().imagecl_tune_save(path.encode()))
+
+
+def tune_load(path: str) -> None:
+    check(lib().imagecl_tune_load(path.encode()))
+
+
+def device_status(stream=None) -> int:
+    """Synchronise, then read and clear the device status word (0: no kernel gave up)."""
+    code = ctypes.c_int32(0)
+    st = lib().imagecl_device_status(ctypes.byref(code), ctypes.c_void_p(stream_handle(stream)))
+    if st not in (_abi.OK, _abi.ERR_TIMEOUT):
+        check(st)
+    return int(code.value)
+
+
+def version() -> str:
+    return lib().imagecl_version().decode()

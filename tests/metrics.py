@@ -1,0 +1,78 @@
+"""Error measures used by the parity tests.
+
+Floating results are compared with the oracle's float64 result y64 on the same
+(storage-rounded) inputs.  The error of an output is scaled by the magnitude of the
+terms that were summed, s(p) = sum |w| |x| (the forward-error bound of a dot product,
+Higham §3.1), so outputs that cancel to near zero are judged fairly:
+
+    e(p) = |y_gpu - y64| / max(s(p), 1e-30)         gate: 1e-5 (f32 storage)
+
+A 16-bit output carries one rounding of its own: f16 (unit roundoff 2^-11) stays within
+2e-3 of s; bf16 (unit roundoff 2^-8 = 3.9e-3, above 2e-3) is gated at one bf16 ulp of
+y64 plus the f32 arithmetic bound.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+import oracle
+
+TOL_F32 = 1e-5
+TOL_16 = 2e-3
+
+
+def to_f64(t) -> np.ndarray:
+    if isinstance(t, torch.Tensor):
+        return t.detach().cpu().to(torch.float64).numpy()
+    return np.asarray(t, dtype=np.float64)
+
+
+def ulp(v: np.ndarray, mant_bits: int) -> np.ndarray:
+    """Spacing of a float format with `mant_bits` stored mantissa bits at |v|."""
+    a = np.maximum(np.abs(v), np.finfo(np.float64).tiny)
+    return np.exp2(np.floor(np.log2(a)) - mant_bits)
+
+
+def scaled_error(gpu, y64: np.ndarray, s: np.ndarray) -> np.ndarray:
+    return np.abs(to_f64(gpu) - y64) / np.maximum(s, 1e-30)
+
+
+def check_float_output(gpu, y64, s, out_dtype: torch.dtype, what: str = "") -> float:
+    """Assert the gate for the output type; return the max scaled error."""
+    g = to_f64(gpu)
+    e = np.abs(g - y64) / np.maximum(s, 1e-30)
+    emax = float(e.max()) if e.size else 0.0
+    if out_dtype == torch.float32:
+        assert emax <= TOL_F32, f"{what}: max scaled error {emax:.3e} > {TOL_F32}"
+    elif out_dtype == torch.float16:
+        assert emax <= TOL_16, f"{what}: max scaled error {emax:.3e} > {TOL_16}"
+    elif out_dtype == torch.bfloat16:
+        bound = ulp(y64, 7) + TOL_F32 * s
+        bad = np.abs(g - y64) > bound
+        assert not bad.any(), f"{what}: {int(bad.sum())} bf16 outputs beyond 1 ulp + f32 bound"
+    else:
+        raise ValueError(out_dtype)
+    return emax
+
+
+def band(x, rows, halo):
+    """Rows [y0 - halo, y1 + halo) of x (cut at the image) and the band's rows inside it.
+    Output rows of the band read only rows of the crop, and the crop meets the image's
+    own edge wherever the boundary rule applies, so the oracle on the crop gives the same
+    values as on the whole image."""
+    h = x.shape[0]
+    y0, y1 = rows
+    a, b = max(0, y0 - halo), min(h, y1 + halo)
+    return x[a:b], (y0 - a, y1 - a)
+
+
+def conv_reference(x, w, border="clamp", bv=0.0, rows=None, halo=None):
+    """(y64, s) for conv2d: the oracle result and the scale sum |w||x|."""
+    if rows is not None and halo is not None:
+        x, rows = band(x, rows, halo)
+    y64 = oracle.conv2d(x, w, border, bv, rows=rows)
+    if np.issubdtype(y64.dtype, np.integer):
+        return y64, None
+    s = oracle.conv2d(np.abs(to_f64(x)), np.abs(to_f64(w)), border, abs(bv), rows=rows)
+    return y64, s

@@ -1,0 +1,187 @@
+"""conv2d on the GPU (through the C ABI) against the CPU oracle, element by element."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from metrics import check_float_output, conv_reference, to_f64
+from paper_1605_06399_gb300 import ImclError, _abi, ops, synth
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(1, 1), (1, 17), (17, 1), (3, 2), (7, 13), (33, 65), (130, 259), (67, 300)]
+EXTRA_SHAPES = [(16, 8), (64, 4), (8, 16)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    yield
+    assert ops.device_status() == 0
+
+
+def _inputs(g, h, w, dt):
+    if dt == "u8":
+        return torch.from_numpy(synth.uniform_u8(g, h, w))
+    return synth.to_storage(synth.uniform_f32(g, h, w), dt)
+
+
+def padded(t: torch.Tensor, device="cuda") -> torch.Tensor:
+    """A (h, w) view of a buffer whose rows are padded to a multiple of 128 bytes."""
+    h, w = t.shape
+    per = 128 // t.element_size()
+    buf = torch.zeros((h, (w + per - 1) // per * per), dtype=t.dtype, device=device)
+    v = buf[:, :w]
+    v.copy_(t.to(device))
+    return v
+
+
+def empty_padded(h, w, dtype):
+    per = 128 // torch.empty((), dtype=dtype).element_size()
+    return torch.empty((h, (w + per - 1) // per * per), dtype=dtype, device="cuda")[:, :w]
+
+
+def _variants_for(in_t, out_t, k, h, w, taps_mem, border):
+    prob = ops.problem(_abi.OP_CONV2D, in_t, out_t, k, k, w, h, border, taps_mem)
+    vs = ops.variants(prob)
+    extra = []
+    for v in vs:
+        if v["kind"] == _abi.KIND_TILED and v["load"] == _abi.LOAD_TMA and v["py"] == 4:
+            for bx, by in EXTRA_SHAPES:
+                extra.append(dict(v, bx=bx, by=by))
+    return vs + extra
+
+
+def _run_all(x_cpu, taps, out_dtype, border, bv, taps_mem, layout):
+    """Run every compiled variant; yield (variant, output) for those that launch.
+    layout 'dense': contiguous tensors; 'padded': rows padded to 128 bytes (TMA-able)."""
+    x = x_cpu.cuda() if layout == "dense" else padded(x_cpu)
+    integer = x.dtype == torch.uint8
+    k = taps.shape[0]
+    t_dev = torch.from_numpy(taps).cuda() if taps_mem == _abi.MEM_DEVICE else taps
+    out_t = torch.int32 if integer else out_dtype
+    for v in _variants_for(x.dtype, out_t, k, x.shape[0], x.shape[1], taps_mem, border):
+        out = None if layout == "dense" else empty_padded(x.shape[0], x.shape[1], out_t)
+        try:
+            y = ops.conv2d(x, t_dev, border, bv, out=out, out_dtype=out_t, variant=v)
+        except ImclError as e:
+            assert e.status in (_abi.ERR_UNSUPPORTED, _abi.ERR_ALIGN), str(e)
+            continue
+        yield v, y
+
+
+CASES = [("u8", torch.int32), ("f32", torch.float32), ("f16", torch.float32),
+         ("f16", torch.float16), ("bf16", torch.float32), ("bf16", torch.bfloat16)]
+
+
+@pytest.mark.parametrize("k", [1, 3, 5, 7, 9, 11, 13, 15])
+@pytest.mark.parametrize("dt,out_dtype", CASES, ids=[f"{a}-{str(b)[6:]}" for a, b in CASES])
+def test_conv2d_every_variant_matches_oracle(dt, out_dtype, k):
+    g = np.random.default_rng(1000 + k)
+    taps = synth.int_filter(g, k) if dt == "u8" else synth.normal_filter_l1(g, k)
+    n_checked = 0
+    for (h, w) in SIZES:
+        x = _inputs(g, h, w, dt)
+        for border, bv in (("clamp", 0.0), ("constant", 3.0 if dt == "u8" else 0.375)):
+            ref, s = conv_reference(x, taps, border, bv)
+            for mem, layout in ((_abi.MEM_HOST, "dense"), (_abi.MEM_HOST, "padded"),
+                                (_abi.MEM_DEVICE, "padded")):
+                for v, y in _run_all(x, taps, out_dtype, border, bv, mem, layout):
+                    what = f"{dt}->{out_dtype} k={k} {h}x{w} {border} mem={mem} {layout} {v}"
+                    if dt == "u8":
+                        assert np.array_equal(y.cpu().numpy(), ref), what
+                    else:
+                        check_float_output(y, ref, s, out_dtype, what)
+                    n_checked += 1
+    assert n_checked > 0
+
+
+def test_rectangular_filter_uses_plain_and_matches():
+    g = np.random.default_rng(5)
+    x = synth.to_storage(synth.uniform_f32(g, 45, 71), "f32")
+    taps = g.standard_normal((3, 7)).astype(np.float32)
+    y = ops.conv2d(x.cuda(), taps)
+    ref, s = conv_reference(x, taps)
+    check_float_output(y, ref, s, torch.float32, "3x7")
+
+
+def test_workload_int3x3_bit_exact():
+    """512x512 u8, 3x3 integer taps in [-4, 4], i32 accumulation: bit-exact."""
+    img, taps = synth.workload_int3x3()
+    x = torch.from_numpy(img).cuda()
+    ref = oracle.conv2d(img, taps)
+    for v in [None] + ops.variants(ops.problem(_abi.OP_CONV2D, "u8", "i32", 3, 3, 512, 512)):
+        y = ops.conv2d(x, taps, variant=v)
+        assert np.array_equal(y.cpu().numpy(), ref), v
+
+
+def test_int_wraparound_matches_oracle():
+    x = torch.full((20, 24), 255, dtype=torch.uint8)
+    taps = np.full((15, 15), 2 ** 25, dtype=np.int32)   # 225 * 255 * 2^25 wraps int32
+    ref = oracle.conv2d(x.numpy(), taps)
+    for v in [None, {"kind": _abi.KIND_PLAIN, "bx": 16, "by": 16}]:
+        assert np.array_equal(ops.conv2d(x.cuda(), taps, variant=v).cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("k", [5, 11])
+def test_workload_8192_f32_tuned_sampled_rows(k):
+    """8192x8192 f32, unit-L1 N(0,1) taps, the tuned launch the benchmark times; checked
+    on row bands at the top, bottom and interior (every column of each band)."""
+    img, taps = synth.workload_conv_f32(k)
+    x = torch.from_numpy(img).cuda()
+    prob = ops.problem(_abi.OP_CONV2D, "f32", "f32", k, k, 8192, 8192)
+    res = ops.tune(prob, budget_s=15.0, reps=3)
+    y = ops.conv2d(x, taps)
+    for rows in [(0, 6), (4093, 4101), (8186, 8192), (1234, 1236)]:
+        ref, s = conv_reference(img, taps, rows=rows, halo=k // 2)
+        check_float_output(y[rows[0]:rows[1]], ref, s, torch.float32, f"k={k} rows={rows} {res}")
+    del x, y
+    torch.cuda.empty_cache()
+
+
+def test_unaligned_buffers_fall_back_and_match():
+    g = np.random.default_rng(9)
+    base = synth.to_storage(synth.uniform_f32(g, 50, 81), "f32").cuda()
+    x = base[:, 1:]                                   # base address off by 4 bytes
+    taps = synth.normal_filter_l1(g, 5)
+    tma = {"kind": 1, "bx": 32, "by": 8, "px": 4, "py": 4, "load": _abi.LOAD_TMA, "filt": 0,
+           "map": 0, "unroll": 1, "persistent": 1}
+    with pytest.raises(ImclError) as ei:
+        ops.conv2d(x, taps, variant=tma)
+    assert ei.value.status == _abi.ERR_ALIGN
+    y = ops.conv2d(x, taps)
+    ref, s = conv_reference(x.cpu(), taps)
+    check_float_output(y, ref, s, torch.float32, "unaligned")
+
+
+def test_wide_and_tall_images():
+    g = np.random.default_rng(10)
+    taps = synth.normal_filter_l1(g, 7)
+    for (h, w) in [(3, 70001), (40001, 5)]:
+        x = synth.to_storage(synth.uniform_f32(g, h, w), "f32")
+        y = ops.conv2d(x.cuda(), taps)
+        ref, s = conv_reference(x, taps)
+        check_float_output(y, ref, s, torch.float32, f"{h}x{w}")
+
+
+def test_aliasing_rejected():
+    x = torch.rand(32, 32, device="cuda")
+    with pytest.raises(ImclError) as ei:
+        ops.conv2d(x, np.ones((3, 3), np.float32), out=x)
+    assert ei.value.status == _abi.ERR_INVALID
+
+
+def test_tuner_reports_and_caches(tmp_path):
+    prob = ops.problem(_abi.OP_CONV2D, "f32", "f32", 5, 5, 1024, 768)
+    ops.tune_clear()
+    res = ops.tune(prob, budget_s=5.0, reps=3)
+    assert res["best_ms"] > 0 and res["plain_ms"] > 0
+    assert res["best_ms"] <= res["plain_ms"] * 1.05
+    assert ops.default_variant(prob) == res["variant"]
+    path = str(tmp_path / "cache.txt")
+    ops.tune_save(path)
+    ops.tune_clear()
+    ops.tune_load(path)
+    assert ops.default_variant(prob) == res["variant"]
