@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--tune-budget", type=float, default=20.0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tune-cache", default=None,
+                    help="tuning cache file: loaded (and tuning skipped) if it exists, "
+                         "written after tuning otherwise")
     return ap.parse_args()
 
 
@@ -152,7 +155,7 @@ def gpu_id_for_smi(local_rank):
 def kernel_source_hash():
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_1605_06399_gb300", "csrc")
-    for f in ("common.cuh", "conv2d_kernels.cuh", "conv2d_tiled.cu"):
+    for f in ("common.cuh", "tile_common.cuh", "conv2d_kernels.cuh", "conv2d_tiled.cu"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -189,12 +192,17 @@ def oracle_rate(img, taps_by_k, seconds, gpu_outs=None):
     n = max(8, min(h, int(8 * seconds / max(t_cal, 1e-6))))
     y0 = (h - n) // 2
     t0 = time.perf_counter()
-    for k, taps in taps_by_k.items():
-        r = k // 2
-        a, b = max(0, y0 - r), min(h, y0 + n + r)
-        oracle.conv2d(img[a:b], taps, rows=(y0 - a, y0 + n - a))
+    passes = 0
+    while True:   # whole passes over the band until the time budget is used
+        for k, taps in taps_by_k.items():
+            r = k // 2
+            a, b = max(0, y0 - r), min(h, y0 + n + r)
+            oracle.conv2d(img[a:b], taps, rows=(y0 - a, y0 + n - a))
+        passes += 1
+        if time.perf_counter() - t0 >= 0.9 * seconds:
+            break
     dt = time.perf_counter() - t0
-    px = n * w * len(taps_by_k)
+    px = passes * n * w * len(taps_by_k)
     errs = {}
     if gpu_outs is not None:
         for k, taps in taps_by_k.items():
@@ -205,7 +213,7 @@ def oracle_rate(img, taps_by_k, seconds, gpu_outs=None):
                               rows=(y0 - a, y0 + n - a))
             g = gpu_outs[k][y0:y0 + n].astype(np.float64)
             errs[k] = float(np.max(np.abs(g - ref) / np.maximum(s, 1e-30)))
-    return px / dt / 1e6, n, oracle.num_threads(), dt, errs
+    return px / dt / 1e6, (n, passes), oracle.num_threads(), dt, errs
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -230,9 +238,17 @@ def run_ours(args):
 
     # tune each stencil (untimed), then time plain and tuned
     tuned = {}
+    cached = args.tune_cache is not None and os.path.exists(args.tune_cache)
+    if cached:
+        ops.tune_load(args.tune_cache)
     for k in KS:
         prob = ops.problem(_abi.OP_CONV2D, "f32", "f32", k, k, SIDE, SIDE)
-        tuned[k] = ops.tune(prob, budget_s=args.tune_budget, reps=5)
+        if cached:
+            tuned[k] = {"variant": ops.default_variant(prob)}
+        else:
+            tuned[k] = ops.tune(prob, budget_s=args.tune_budget, reps=5)
+    if args.tune_cache is not None and not cached and rank == 0:
+        ops.tune_save(args.tune_cache)
     xi = ops.image(x)
     yi = {k: ops.image(ys[k]) for k in KS}
     tp = {k: np.ascontiguousarray(taps[k], np.float32) for k in KS}
@@ -370,8 +386,8 @@ def run_ours(args):
         gpu_outs = {k: ys[k].cpu().numpy() for k in KS}
         rate, rows, threads, secs, errs = oracle_rate(img, taps, args.cpu_seconds, gpu_outs)
         cpu = {"value": rate, "unit": "Mpixel/s", "cores": threads, "kind": "oracle",
-               "sample": f"rows {rows} of 8192 (all 8192 columns) through both filters, fp64, "
-                         f"{secs:.1f} s"}
+               "sample": f"{rows[1]} pass(es) over rows {rows[0]} of 8192 (all 8192 columns) "
+                         f"through both filters, fp64, {secs:.1f} s"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world,

@@ -119,6 +119,52 @@ imcl_status imagecl_conv2d(const imcl_image *in, const imcl_image *out, const vo
                            int32_t border, double border_value, const imcl_variant *variant,
                            void *stream);
 
+/*
+ * Separable correlation (§6 "separable convolution": a row pass then a column pass; §7
+ * names fusing the two with the intermediate on chip):
+ *   t(x, y)   = sum_{i<nrow} row_taps[i] * in(x + i - (nrow-1)/2, y)
+ *   out(x, y) = sum_{j<ncol} col_taps[j] * t(x, y + j - (ncol-1)/2)
+ * Each pass applies `border` to its own input (for CONSTANT, out-of-image reads of `in`
+ * give border_value as an input pixel, those of t give it as an f32).  Under the clamped
+ * rule the result equals imagecl_conv2d with the outer product col x row; under the
+ * constant rule it does not unless border_value is 0.
+ * in: f32, f16 or bf16; out: f32 or the input's own 16-bit type; t is kept in f32.
+ * nrow, ncol: odd, 1..33 (radius up to 16).  Taps are f32, host or device per taps_mem.
+ * The fused variants (the default) need no workspace.  The PLAIN variant runs the two
+ * passes as two kernels with t in `workspace` (width*height*4 bytes, device memory the
+ * caller owns; see imagecl_sepconv_workspace_size); a NULL or short workspace for it
+ * -> IMCL_ERR_INVALID.
+ */
+imcl_status imagecl_sepconv(const imcl_image *in, const imcl_image *out, const float *row_taps,
+                            int32_t nrow, const float *col_taps, int32_t ncol, int32_t taps_mem,
+                            int32_t border, double border_value, const imcl_variant *variant,
+                            void *workspace, size_t workspace_bytes, void *stream);
+
+/* Workspace bytes imagecl_sepconv needs for `variant` on a width x height image (0 for
+ * the fused variants and for NULL, the default). */
+size_t imagecl_sepconv_workspace_size(int32_t width, int32_t height, const imcl_variant *variant);
+
+/*
+ * Harris corner response (§6 corner-detection benchmark: a Sobel kernel then a Harris
+ * kernel, Tables 4 and 5), clamped boundary on each stage's input:
+ *   Ix = Sx (*) in,  Iy = Sy (*) in                  (3x3 correlations, sobel_x / sobel_y)
+ *   Pxx = Ix^2,  Pyy = Iy^2,  Pxy = Ix Iy
+ *   Sc = window (*) Pc                                (wk x wk, c in {xx, yy, xy})
+ *   out = Sxx Syy - Sxy^2 - k (Sxx + Syy)^2
+ * in and out: f32.  sobel_x, sobel_y: 9 taps each; window: wk*wk taps (wk odd, 1..7);
+ * all three host or device per taps_mem.  The fused variants (the default; wk 3 or 5)
+ * need no workspace.  The PLAIN variant (any odd wk up to 7) runs the paper's two
+ * kernels with Ix, Iy in `workspace` (2*width*height*4 bytes, caller-owned device
+ * memory; see imagecl_harris_workspace_size); NULL or short -> IMCL_ERR_INVALID.
+ */
+imcl_status imagecl_harris(const imcl_image *in, const imcl_image *out, const float *sobel_x,
+                           const float *sobel_y, const float *window, int32_t wk, float k,
+                           int32_t taps_mem, const imcl_variant *variant, void *workspace,
+                           size_t workspace_bytes, void *stream);
+
+/* Workspace bytes imagecl_harris needs for `variant` (0 for fused variants and NULL). */
+size_t imagecl_harris_workspace_size(int32_t width, int32_t height, const imcl_variant *variant);
+
 /* ------------------------------------------------------------------ tuning */
 
 /* Number of compiled variants applicable to `problem` (0 if none), and the idx-th one.

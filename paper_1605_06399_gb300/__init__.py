@@ -4,9 +4,9 @@ The compute path is ``libimagecl.so`` (hand-written sm_103a CUDA behind the C AB
 ``include/imagecl.h``); this package only marshals arguments to it.  Build the library
 with ``python -m paper_1605_06399_gb300.build``; calls fail loudly if it is missing.
 """
-from .ops import (conv2d, default_variant, device_status, image, problem, tune, tune_clear,
+from .ops import (conv2d, sepconv, harris, default_variant, device_status, image, problem, tune, tune_clear,
                   tune_load, tune_save, tune_set, variants, version)
 from ._abi import ImclError
 
-__all__ = ["conv2d", "default_variant", "device_status", "image", "problem", "tune", "tune_clear",
+__all__ = ["conv2d", "sepconv", "harris", "default_variant", "device_status", "image", "problem", "tune", "tune_clear",
            "tune_load", "tune_save", "tune_set", "variants", "version", "ImclError"]

@@ -26,6 +26,9 @@ CFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
 
 TILED_K = (3, 5, 7, 9, 11, 13, 15)
 TILED_GROUPS = (0, 1, 2, 3)
+SEP_GROUPS = (0, 1, 2)
+SEP_RSETS = (0, 1)
+MULTI = ("conv2d_tiled.cu", "sepconv_fused.cu")
 
 
 def _nvcc() -> str:
@@ -39,13 +42,18 @@ def units() -> list[tuple[str, list[str], str]]:
     """(source, extra flags, object name) for every translation unit."""
     out = []
     for f in sorted(os.listdir(CSRC)):
-        if f.endswith(".cu") and f != "conv2d_tiled.cu":
+        if f.endswith(".cu") and f not in MULTI:
             out.append((os.path.join(CSRC, f), [], f[:-3] + ".o"))
     for k in TILED_K:
         for g in TILED_GROUPS:
             out.append((os.path.join(CSRC, "conv2d_tiled.cu"),
                         [f"-DIMCL_TILED_K={k}", f"-DIMCL_TILED_GROUP={g}"],
                         f"conv2d_tiled_k{k}_g{g}.o"))
+    for g in SEP_GROUPS:
+        for r in SEP_RSETS:
+            out.append((os.path.join(CSRC, "sepconv_fused.cu"),
+                        [f"-DIMCL_SEP_GROUP={g}", f"-DIMCL_SEP_RSET={r}"],
+                        f"sepconv_fused_g{g}_s{r}.o"))
     return out
 
 
@@ -98,6 +106,8 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
         if "conv2d_tiled" in o:
             k = int(o.split("_k")[1].split("_")[0])
             return -(k * k * (3 if o.endswith("g0.o") else 1))
+        if "sepconv_fused" in o:
+            return -150
         return 0
     todo.sort(key=cost)
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:

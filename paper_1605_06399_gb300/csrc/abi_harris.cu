@@ -1,0 +1,124 @@
+// abi_harris.cu -- imagecl_harris: argument checks and variant selection.
+#include <string>
+
+#include "abi_internal.h"
+
+namespace imcl {
+
+imcl_problem harris_problem(const ConvCall& c) {
+    imcl_problem p = conv_problem(c);
+    p.op = IMCL_OP_HARRIS;
+    return p;
+}
+
+std::vector<const ConvEntry*> harris_entries_for(int wk, int taps_mem) {
+    std::vector<const ConvEntry*> r;
+    for (const ConvEntry& e : harris_table()) {
+        if (e.v.kind == IMCL_KIND_PLAIN) { r.push_back(&e); continue; }
+        if (e.k != wk) continue;
+        if (taps_mem == IMCL_MEM_DEVICE && e.v.filt != IMCL_FILT_SMEM) continue;
+        r.push_back(&e);
+    }
+    return r;
+}
+
+static const ConvEntry* harris_find(const ConvCall& c, const imcl_variant& v) {
+    for (const ConvEntry* e : harris_entries_for(c.kw, c.taps_mem)) {
+        if (v.kind == IMCL_KIND_PLAIN && e->v.kind == IMCL_KIND_PLAIN) return e;
+        if (e->v.kind == v.kind && e->v.py == v.py && e->v.load == v.load && e->v.filt == v.filt) return e;
+    }
+    return nullptr;
+}
+
+imcl_variant harris_default_variant(const ConvCall& c) {
+    imcl_variant v{};
+    if (cache_lookup(harris_problem(c), &v)) return v;
+    const bool tma_ok = (reinterpret_cast<uintptr_t>(c.in) % 16) == 0 && (c.in_pitch_b % 16) == 0;
+    const int filt = c.taps_mem == IMCL_MEM_DEVICE ? IMCL_FILT_SMEM : IMCL_FILT_PARAM;
+    const auto entries = harris_entries_for(c.kw, c.taps_mem);
+    for (const ConvEntry* e : entries)
+        if (e->v.kind == IMCL_KIND_TILED && e->v.filt == filt && e->v.py == 2 &&
+            e->v.load == (tma_ok ? IMCL_LOAD_TMA : IMCL_LOAD_SMEM))
+            return e->v;
+    for (const ConvEntry* e : entries)
+        if (e->v.kind == IMCL_KIND_TILED && e->v.load == IMCL_LOAD_SMEM && e->v.filt == filt) return e->v;
+    for (const ConvEntry* e : entries)
+        if (e->v.kind == IMCL_KIND_PLAIN) return e->v;
+    v.kind = -1;
+    return v;
+}
+
+imcl_status harris_prepare(const imcl_image* in, const imcl_image* out, const float* sx, const float* sy,
+                           const float* win, int wk, float k, int taps_mem, void* ws, size_t ws_bytes,
+                           ConvCall* c) {
+    imcl_status st;
+    if ((st = check_image(in, "in")) != IMCL_OK) return st;
+    if ((st = check_image(out, "out")) != IMCL_OK) return st;
+    if (in->width != out->width || in->height != out->height)
+        return fail(IMCL_ERR_INVALID, "in and out must have the same width and height");
+    if (images_overlap(in, out)) return fail(IMCL_ERR_INVALID, "in and out overlap (operations are out of place)");
+    if (in->dtype != IMCL_F32 || out->dtype != IMCL_F32)
+        return fail(IMCL_ERR_UNSUPPORTED, "harris takes an f32 image and writes f32");
+    if (wk <= 0) return fail(IMCL_ERR_INVALID, "window side must be positive");
+    if (wk % 2 == 0) return fail(IMCL_ERR_UNSUPPORTED, "window side must be odd (centred window)");
+    if (wk > 7) return fail(IMCL_ERR_UNSUPPORTED, "window side above 7 is not provided");
+    if (!sx || !sy || !win) return fail(IMCL_ERR_INVALID, "sobel_x, sobel_y and window must not be NULL");
+    if (taps_mem != IMCL_MEM_HOST && taps_mem != IMCL_MEM_DEVICE)
+        return fail(IMCL_ERR_INVALID, "taps_mem must be IMCL_MEM_HOST or IMCL_MEM_DEVICE");
+    if (!(k == k)) return fail(IMCL_ERR_INVALID, "k must be a number");
+    DeviceInfo* dev = nullptr;
+    if ((st = device_info(&dev)) != IMCL_OK) return st;
+    c->in = in->data;
+    c->out = out->data;
+    c->in_dtype = IMCL_F32;
+    c->out_dtype = IMCL_F32;
+    c->W = in->width;
+    c->H = in->height;
+    c->in_pitch_b = in->pitch_bytes;
+    c->out_pitch_b = out->pitch_bytes;
+    c->kw = wk;
+    c->kh = wk;
+    c->taps = sx;
+    c->taps2 = sy;
+    c->taps3 = win;
+    c->hk = k;
+    c->taps_mem = taps_mem;
+    c->border = IMCL_BORDER_CLAMP;
+    c->workspace = ws;
+    c->ws_bytes = ws_bytes;
+    c->status = dev->status;
+    c->dev = dev;
+    return IMCL_OK;
+}
+
+imcl_status harris_run(const ConvCall& c, const imcl_variant* variant, cudaStream_t s) {
+    imcl_variant v = variant ? *variant : harris_default_variant(c);
+    const ConvEntry* e = harris_find(c, v);
+    if (!e) return fail(IMCL_ERR_UNSUPPORTED, "no compiled harris variant matches the request");
+    if (v.kind == IMCL_KIND_TILED && (v.bx <= 0 || v.by <= 0)) { v.bx = e->v.bx; v.by = e->v.by; }
+    return e->fn(c, v, s);
+}
+
+}  // namespace imcl
+
+using namespace imcl;
+
+extern "C" {
+
+imcl_status imagecl_harris(const imcl_image* in, const imcl_image* out, const float* sobel_x, const float* sobel_y,
+                           const float* window, int32_t wk, float k, int32_t taps_mem, const imcl_variant* variant,
+                           void* workspace, size_t workspace_bytes, void* stream) {
+    ConvCall c;
+    imcl_status st = harris_prepare(in, out, sobel_x, sobel_y, window, wk, k, taps_mem, workspace,
+                                    workspace_bytes, &c);
+    if (st != IMCL_OK) return st;
+    return harris_run(c, variant, static_cast<cudaStream_t>(stream));
+}
+
+size_t imagecl_harris_workspace_size(int32_t width, int32_t height, const imcl_variant* variant) {
+    if (width <= 0 || height <= 0) return 0;
+    if (variant && variant->kind == IMCL_KIND_PLAIN) return (size_t)2 * width * (size_t)height * sizeof(float);
+    return 0;
+}
+
+}  // extern "C"

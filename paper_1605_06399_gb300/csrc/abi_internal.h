@@ -25,4 +25,19 @@ imcl_status conv_prepare(const imcl_image* in, const imcl_image* out, const void
                          int kh, int taps_mem, int border, double bv, ConvCall* c);
 imcl_status conv_run(const ConvCall& c, const imcl_variant* variant, cudaStream_t s);
 
+imcl_problem sep_problem(const ConvCall& c);
+std::vector<const ConvEntry*> sep_entries_for(int in_dt, int out_dt, int nr, int nc, int taps_mem);
+imcl_variant sep_default_variant(const ConvCall& c);
+imcl_status sep_prepare(const imcl_image* in, const imcl_image* out, const float* row, int nr, const float* col,
+                        int nc, int taps_mem, int border, double bv, void* ws, size_t ws_bytes, ConvCall* c);
+imcl_status sep_run(const ConvCall& c, const imcl_variant* variant, cudaStream_t s);
+
+imcl_problem harris_problem(const ConvCall& c);
+std::vector<const ConvEntry*> harris_entries_for(int wk, int taps_mem);
+imcl_variant harris_default_variant(const ConvCall& c);
+imcl_status harris_prepare(const imcl_image* in, const imcl_image* out, const float* sx, const float* sy,
+                           const float* win, int wk, float k, int taps_mem, void* ws, size_t ws_bytes,
+                           ConvCall* c);
+imcl_status harris_run(const ConvCall& c, const imcl_variant* variant, cudaStream_t s);
+
 }  // namespace imcl

@@ -53,7 +53,12 @@ struct ConvCall {
     int64_t in_pitch_b = 0, out_pitch_b = 0;   // bytes
     int kw = 0, kh = 0;
     const void* taps = nullptr;                // host or device, per taps_mem
+    const void* taps2 = nullptr;               // sepconv: column taps; harris: Sobel y
+    const void* taps3 = nullptr;               // harris: window taps
+    float hk = 0.f;                            // harris: k of the response
     int taps_mem = IMCL_MEM_HOST;
+    void* workspace = nullptr;                 // caller scratch (unfused variants)
+    size_t ws_bytes = 0;
     int border = IMCL_BORDER_CLAMP;
     double border_value = 0.0;
     int* status = nullptr;
@@ -90,6 +95,22 @@ IMCL_DECL_TILED(15)
 
 const std::vector<ConvEntry>& conv_table();
 
+// Separable correlation: the same entry type; `k` is the radius R a fused kernel is
+// specialised for (0 for the plain two-kernel path).  kw / kh of the call are the row
+// and column tap counts.
+constexpr int kMaxSepTaps = 33;
+#define IMCL_DECL_SEP(G)                                          \
+    void register_sep_fused_g##G##_s0(std::vector<ConvEntry>& t); \
+    void register_sep_fused_g##G##_s1(std::vector<ConvEntry>& t);
+IMCL_DECL_SEP(0)
+IMCL_DECL_SEP(1)
+IMCL_DECL_SEP(2)
+#undef IMCL_DECL_SEP
+const std::vector<ConvEntry>& sep_table();
+
+// Harris: `k` is the window side a fused kernel is specialised for (0 for the plain path).
+const std::vector<ConvEntry>& harris_table();
+
 // Shared argument block of the conv2d kernels (device-visible by value).
 struct ConvArgs {
     const void* in;
@@ -104,6 +125,10 @@ struct ConvArgs {
     int vec_in, vec_out;             // 1 if vector loads / stores are aligned
     int kw, kh;                      // runtime sides (plain kernel)
     const void* taps_dev;            // device taps or nullptr
+    const void* taps2_dev;           // sepconv: device column taps or nullptr
+    const void* taps3_dev;           // harris: device window taps or nullptr
+    float hk;                        // harris: k
+    void* work;                      // caller workspace (unfused variants)
     int* status;
 };
 

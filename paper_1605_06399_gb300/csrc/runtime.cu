@@ -155,6 +155,10 @@ ConvArgs make_conv_args(const ConvCall& c, const imcl_variant& v, int in_align, 
     a.kw = c.kw;
     a.kh = c.kh;
     a.taps_dev = c.taps_mem == IMCL_MEM_DEVICE ? c.taps : nullptr;
+    a.taps2_dev = c.taps_mem == IMCL_MEM_DEVICE ? c.taps2 : nullptr;
+    a.taps3_dev = c.taps_mem == IMCL_MEM_DEVICE ? c.taps3 : nullptr;
+    a.hk = c.hk;
+    a.work = c.workspace;
     a.status = c.status;
     return a;
 }

@@ -1,0 +1,319 @@
+// sepconv_kernels.cuh -- separable correlation (§6 separable convolution benchmark).
+//
+//   t(x, y)   = sum_i row[i] * in(b(x + i - rr, y))        row pass, boundary rule on in
+//   out(x, y) = sum_j col[j] * t(x, b(y + j - rc))         column pass, boundary rule on t
+//
+// The paper runs the two passes as two kernels (Table 2: R and C) and notes (§7) that
+// fusing them with the intermediate kept in on-chip memory is what its language could
+// not express.  Here:
+//  * k_sep_row_plain / k_sep_col_plain: the untuned two-kernel form (one pixel per
+//    thread, clamped global loads, rolled loops, t in a caller workspace in f32);
+//  * k_sepconv_fused: one kernel.  A CTA stages its input tile plus R halo rows and PAD
+//    halo columns (TMA double-buffered ring, cooperative loads, or the L1 path), runs
+//    the row pass for the TH + 2R rows the column pass needs into an f32 buffer in
+//    shared memory, then the column pass from that buffer, and writes the tile once:
+//    one HBM read and one write per pixel.
+// Row and column tap counts may differ: both are zero-padded (exactly neutral) to the
+// kernel's radius R = max(rr, rc).
+#pragma once
+
+#include "tile_common.cuh"
+
+namespace imcl {
+
+// ------------------------------------------------------------------ plain, unfused
+template <typename Tin>
+__global__ void __launch_bounds__(256)
+    k_sep_row_plain(const ConvArgs a, const __grid_constant__ TapsParam<float, 2 * 33> tp) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= a.W || y >= a.H) return;
+    const Tin* in = static_cast<const Tin*>(a.in);
+    const float* row = a.taps_dev ? static_cast<const float*>(a.taps_dev) : tp.w;
+    const float bv = to_acc(border_pixel<Tin>(a));
+    const int rr = (a.kw - 1) / 2;
+    float acc = 0.f;
+#pragma unroll 1
+    for (int i = 0; i < a.kw; ++i) {
+        const int gx = x + i - rr;
+        float v;
+        if (gx >= 0 && gx < a.W) v = to_acc(in[(long long)y * a.in_pitch + gx]);
+        else if (a.border == IMCL_BORDER_CONSTANT) v = bv;
+        else v = to_acc(in[(long long)y * a.in_pitch + clampi(gx, 0, a.W - 1)]);
+        acc = __fmaf_rn(row[i], v, acc);
+    }
+    static_cast<float*>(a.work)[(long long)y * a.W + x] = acc;
+}
+
+template <typename Tout>
+__global__ void __launch_bounds__(256)
+    k_sep_col_plain(const ConvArgs a, const __grid_constant__ TapsParam<float, 2 * 33> tp) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= a.W || y >= a.H) return;
+    const float* t = static_cast<const float*>(a.work);
+    const float* col = a.taps2_dev ? static_cast<const float*>(a.taps2_dev) : tp.w + 33;
+    const int rc = (a.kh - 1) / 2;
+    float acc = 0.f;
+#pragma unroll 1
+    for (int j = 0; j < a.kh; ++j) {
+        const int gy = y + j - rc;
+        float v;
+        if (gy >= 0 && gy < a.H) v = t[(long long)gy * a.W + x];
+        else if (a.border == IMCL_BORDER_CONSTANT) v = a.bv_f;
+        else v = t[(long long)clampi(gy, 0, a.H - 1) * a.W + x];
+        acc = __fmaf_rn(col[j], v, acc);
+    }
+    static_cast<Tout*>(a.out)[(long long)y * a.out_pitch + x] = Store<Tout, float>::cvt(acc);
+}
+
+// ------------------------------------------------------------------ fused
+template <typename Tin, typename Tout, int R, int PX, int PY, int LOAD, int FILT>
+__global__ void __launch_bounds__(256, 1)
+    k_sepconv_fused(const ConvArgs a, const __grid_constant__ TapsParam<float, 2 * (2 * R + 1)> tp,
+                    const __grid_constant__ CUtensorMap tmap) {
+    constexpr int NT = 2 * R + 1;
+    using G = TileGeo<Tin, NT, PX>;
+    static_assert(PX == 4, "the t buffer is written and read as float4");
+    extern __shared__ __align__(128) uint8_t smem[];
+
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int bx = a.bx, by = a.by;
+    const int TW = bx * PX, TH = by * PY;
+    const int SW = TW + 2 * G::PAD, SH = TH + 2 * R;
+    const int stage_bytes = round_up(SW * SH * G::SZ, 128);
+    constexpr int kStages = LOAD == IMCL_LOAD_TMA ? 2 : (LOAD == IMCL_LOAD_SMEM ? 1 : 0);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+    float* tbuf = reinterpret_cast<float*>(smem + 128 + kStages * stage_bytes);
+    float* wsm = tbuf + SH * TW;
+
+    const Tin* in = static_cast<const Tin*>(a.in);
+    Tout* out = static_cast<Tout*>(a.out);
+    const Tin bv_t = border_pixel<Tin>(a);
+    const float bv = to_acc(bv_t);
+
+    if constexpr (FILT == IMCL_FILT_SMEM) {
+        if (a.taps_dev) {
+            const int orr = R - (a.kw - 1) / 2, orc = R - (a.kh - 1) / 2;
+            const float* rd = static_cast<const float*>(a.taps_dev);
+            const float* cd = static_cast<const float*>(a.taps2_dev);
+            for (int i = tid; i < NT; i += nth) {
+                wsm[i] = (i >= orr && i < orr + a.kw) ? rd[i - orr] : 0.f;
+                wsm[NT + i] = (i >= orc && i < orc + a.kh) ? cd[i - orc] : 0.f;
+            }
+        } else {
+            for (int i = tid; i < 2 * NT; i += nth) wsm[i] = tp.w[i];
+        }
+    }
+    const float* rw;
+    if constexpr (FILT == IMCL_FILT_SMEM) rw = wsm; else rw = tp.w;
+    const float* cw = rw + NT;
+
+    const int ntiles = a.tiles_x * a.tiles_y;
+    int t = blockIdx.x;
+    int s = 0;
+    uint32_t parity = 0;
+    if constexpr (LOAD == IMCL_LOAD_TMA) {
+        if (tid == 0) {
+            prefetch_tmap(&tmap);
+            mbar_init(&bar[0], 1);
+            mbar_init(&bar[1], 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        if (tid == 0 && t < ntiles) {
+            const int tx0 = (t % a.tiles_x) * TW, ty0 = (t / a.tiles_x) * TH;
+            mbar_arrive_expect_tx(&bar[0], (uint32_t)(SW * SH * G::SZ));
+            tma_load_2d(smem + 128, &tmap, tx0 - G::PAD, ty0 - R, &bar[0]);
+        }
+    } else {
+        __syncthreads();
+    }
+
+    for (; t < ntiles; t += gridDim.x) {
+        const int x0 = (t % a.tiles_x) * TW, y0 = (t / a.tiles_x) * TH;
+        const int gx0 = x0 - G::PAD, gy0 = y0 - R;
+        Tin* st = reinterpret_cast<Tin*>(smem + 128 + s * stage_bytes);
+
+        if constexpr (LOAD == IMCL_LOAD_TMA) {
+            const int tn = t + gridDim.x;
+            const bool prefetch = tn < ntiles;
+            if (tid == 0 && prefetch) {
+                const int nx0 = (tn % a.tiles_x) * TW, ny0 = (tn / a.tiles_x) * TH;
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&bar[s ^ 1], (uint32_t)(SW * SH * G::SZ));
+                tma_load_2d(smem + 128 + (s ^ 1) * stage_bytes, &tmap, nx0 - G::PAD, ny0 - R, &bar[s ^ 1]);
+            }
+            const bool ok = mbar_wait(&bar[s], (parity >> s) & 1u, a.status);
+            parity ^= (1u << s);
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0 && prefetch) mbar_wait(&bar[s ^ 1], (parity >> (s ^ 1)) & 1u, nullptr);
+                return;
+            }
+            if (!tile_inside(gx0, gy0, SW, SH, a.W, a.H))
+                patch_tile<Tin>(st, SW, SH, gx0, gy0, a.W, a.H, a.border, bv_t, tid, nth);
+        } else if constexpr (LOAD == IMCL_LOAD_SMEM) {
+            coop_load_tile<Tin>(st, in, a.in_pitch, SW, SH, gx0, gy0, a.W, a.H, a.border, bv_t, a.vec_in != 0,
+                                tid, nth);
+            __syncthreads();
+        }
+
+        // row pass: t for the SH staged rows, TW columns, PX per work item
+        const int nseg = TW / PX;
+        for (int it = tid; it < SH * nseg; it += nth) {
+            const int row = it / nseg, c0 = (it - row * nseg) * PX;
+            const int gy = gy0 + row;
+            float4 tv;
+            if (a.border == IMCL_BORDER_CONSTANT && (gy < 0 || gy >= a.H)) {
+                tv = make_float4(a.bv_f, a.bv_f, a.bv_f, a.bv_f);   // t is padded with the constant
+            } else {
+                float seg[G::SEG];
+                if constexpr (LOAD == IMCL_LOAD_GLOBAL)
+                    load_seg_global<Tin, G>(in, a.in_pitch, gy, x0 + c0 - G::PAD, a.W, a.H, a.border, bv,
+                                            a.vec_in != 0, seg);
+                else
+                    load_seg_smem<Tin, G>(st + row * SW + c0, seg);
+                float r4[PX];
+#pragma unroll
+                for (int ox = 0; ox < PX; ++ox) r4[ox] = 0.f;
+#pragma unroll
+                for (int i = 0; i < NT; ++i) {
+                    const float w = rw[i];
+#pragma unroll
+                    for (int ox = 0; ox < PX; ++ox) r4[ox] = __fmaf_rn(w, seg[G::LO + ox + i], r4[ox]);
+                }
+                tv = make_float4(r4[0], r4[1], r4[2], r4[3]);
+            }
+            *reinterpret_cast<float4*>(tbuf + row * TW + c0) = tv;
+        }
+        __syncthreads();
+
+        // column pass: PX x PY block per thread, sliding down the t buffer
+        {
+            const int tx = tid % bx, ty = tid / bx;
+            float acc[PY][PX];
+#pragma unroll
+            for (int oy = 0; oy < PY; ++oy)
+#pragma unroll
+                for (int ox = 0; ox < PX; ++ox) acc[oy][ox] = 0.f;
+#pragma unroll
+            for (int yy = 0; yy < PY + 2 * R; ++yy) {
+                const float4 v = *reinterpret_cast<const float4*>(tbuf + (ty * PY + yy) * TW + tx * PX);
+                const float tv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int oy = 0; oy < PY; ++oy) {
+                    const int j = yy - oy;
+                    if (j >= 0 && j < NT) {
+                        const float w = cw[j];
+#pragma unroll
+                        for (int ox = 0; ox < PX; ++ox) acc[oy][ox] = __fmaf_rn(w, tv[ox], acc[oy][ox]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int oy = 0; oy < PY; ++oy)
+                store_block_row<Tout, PX>(out, a.out_pitch, x0 + tx * PX, y0 + ty * PY + oy, a.W, a.H,
+                                          a.vec_out != 0, acc[oy]);
+        }
+        __syncthreads();   // t buffer and stage s may be refilled
+        if constexpr (LOAD == IMCL_LOAD_TMA) s ^= 1;
+    }
+}
+
+// ------------------------------------------------------------------ host launchers
+inline void fill_sep_taps(float* w, int R, const ConvCall& c) {
+    const int NT = 2 * R + 1;
+    for (int i = 0; i < 2 * NT; ++i) w[i] = 0.f;
+    if (c.taps_mem != IMCL_MEM_HOST) return;
+    const float* row = static_cast<const float*>(c.taps);
+    const float* col = static_cast<const float*>(c.taps2);
+    const int orr = R - (c.kw - 1) / 2, orc = R - (c.kh - 1) / 2;
+    for (int i = 0; i < c.kw; ++i) w[orr + i] = row[i];
+    for (int j = 0; j < c.kh; ++j) w[NT + orc + j] = col[j];
+}
+
+template <typename Tin, typename Tout>
+imcl_status launch_sep_plain(const ConvCall& c, const imcl_variant& v, cudaStream_t s) {
+    const size_t need = (size_t)c.W * c.H * sizeof(float);
+    if (!c.workspace || c.ws_bytes < need)
+        return fail(IMCL_ERR_INVALID, "the unfused separable kernels need a workspace of width*height*4 bytes");
+    const int bx = v.bx > 0 ? v.bx : 16, by = v.by > 0 ? v.by : 16;
+    if (bx * by > 256) return fail(IMCL_ERR_UNSUPPORTED, "plain kernel: bx*by must be <= 256");
+    ConvArgs a = make_conv_args(c, v, 1, 1);
+    TapsParam<float, 66> tp;
+    for (int i = 0; i < 66; ++i) tp.w[i] = 0.f;
+    if (c.taps_mem == IMCL_MEM_HOST) {
+        for (int i = 0; i < c.kw; ++i) tp.w[i] = static_cast<const float*>(c.taps)[i];
+        for (int j = 0; j < c.kh; ++j) tp.w[33 + j] = static_cast<const float*>(c.taps2)[j];
+    }
+    dim3 grid((c.W + bx - 1) / bx, (c.H + by - 1) / by), block(bx, by);
+    k_sep_row_plain<Tin><<<grid, block, 0, s>>>(a, tp);
+    k_sep_col_plain<Tout><<<grid, block, 0, s>>>(a, tp);
+    return cuda_fail(cudaGetLastError(), "sepconv plain launch");
+}
+
+template <typename Tin, typename Tout, int R, int PX, int PY, int LOAD, int FILT>
+imcl_status launch_sep_fused(const ConvCall& c, const imcl_variant& v, cudaStream_t s) {
+    constexpr int NT = 2 * R + 1;
+    using G = TileGeo<Tin, NT, PX>;
+    const int bx = v.bx, by = v.by, nth = bx * by;
+    if (bx <= 0 || by <= 0 || nth > 256 || nth % 32 != 0)
+        return fail(IMCL_ERR_UNSUPPORTED, "fused sepconv: bx*by must be a multiple of 32, at most 256");
+    if ((bx * PX) % G::CV != 0) return fail(IMCL_ERR_UNSUPPORTED, "fused sepconv: bx*px must be a multiple of 16 bytes");
+    if (std::max(c.kw, c.kh) != NT) return fail(IMCL_ERR_UNSUPPORTED, "fused sepconv: radius mismatch");
+    if (c.taps_mem == IMCL_MEM_DEVICE && FILT != IMCL_FILT_SMEM)
+        return fail(IMCL_ERR_UNSUPPORTED, "device-resident taps need a FILT_SMEM variant");
+    const int TW = bx * PX, TH = by * PY;
+    const int SW = TW + 2 * G::PAD, SH = TH + 2 * R;
+    if (LOAD == IMCL_LOAD_TMA && (SW > 256 || SH > 256))
+        return fail(IMCL_ERR_UNSUPPORTED, "fused sepconv: TMA box larger than 256 in a dimension");
+    const int stage_bytes = round_up(SW * SH * G::SZ, 128);
+    const int nstage = LOAD == IMCL_LOAD_TMA ? 2 : (LOAD == IMCL_LOAD_SMEM ? 1 : 0);
+    const int smem = 128 + nstage * stage_bytes + SH * TW * 4 + 2 * NT * 4;
+    if (smem > c.dev->max_smem_optin) return fail(IMCL_ERR_UNSUPPORTED, "fused sepconv: tile too large for shared memory");
+    auto kfn = k_sepconv_fused<Tin, Tout, R, PX, PY, LOAD, FILT>;
+    imcl_status st = set_smem_limit((const void*)kfn, smem);
+    if (st != IMCL_OK) return st;
+    const int in_align = (LOAD == IMCL_LOAD_GLOBAL) ? G::VB * G::SZ : 16;
+    ConvArgs a = make_conv_args(c, v, in_align, PX * (int)sizeof(Tout) > 16 ? 16 : PX * (int)sizeof(Tout));
+    a.tiles_x = (c.W + TW - 1) / TW;
+    a.tiles_y = (c.H + TH - 1) / TH;
+    const int ntiles = a.tiles_x * a.tiles_y;
+    CUtensorMap tmap;
+    memset(&tmap, 0, sizeof(tmap));
+    if (LOAD == IMCL_LOAD_TMA) {
+        if ((reinterpret_cast<uintptr_t>(c.in) & 15) || (c.in_pitch_b & 15))
+            return fail(IMCL_ERR_ALIGN, "TMA staging needs a 16-byte aligned input and pitch");
+        st = encode_tmap_2d(&tmap, c.in_dtype, c.in, c.W, c.H, c.in_pitch_b, SW, SH);
+        if (st != IMCL_OK) return st;
+    }
+    TapsParam<float, 2 * NT> tp;
+    fill_sep_taps(tp.w, R, c);
+    int grid = ntiles;
+    if (v.persistent || LOAD == IMCL_LOAD_TMA) {
+        const int occ = cached_occupancy((const void*)kfn, nth, smem);
+        if (occ <= 0) return fail(IMCL_ERR_UNSUPPORTED, "fused sepconv: kernel cannot be resident");
+        const int slots = occ * c.dev->sm_count;
+        grid = ntiles < slots ? ntiles : slots;
+    }
+    kfn<<<grid, nth, smem, s>>>(a, tp, tmap);
+    return cuda_fail(cudaGetLastError(), "sepconv fused launch");
+}
+
+template <typename Tin, typename Tout, int R, int PX, int PY, int LOAD, int FILT>
+inline ConvEntry sep_entry(int bx, int by, int persistent) {
+    imcl_variant v{};
+    v.kind = IMCL_KIND_TILED;
+    v.bx = bx;
+    v.by = by;
+    v.px = PX;
+    v.py = PY;
+    v.load = LOAD;
+    v.filt = FILT;
+    v.map = IMCL_MAP_BLOCKED;
+    v.unroll = 1;
+    v.persistent = persistent;
+    return ConvEntry{DtypeOf<Tin>::v, DtypeOf<Tout>::v, R, v, &launch_sep_fused<Tin, Tout, R, PX, PY, LOAD, FILT>};
+}
+
+}  // namespace imcl

@@ -104,6 +104,62 @@ def conv2d(x: torch.Tensor, taps, border: str = "clamp", border_value: float = 0
     return y
 
 
+def sepconv(x: torch.Tensor, row_taps, col_taps=None, border: str = "clamp",
+            border_value: float = 0.0, out=None, out_dtype=None, variant=None, workspace=None,
+            stream=None) -> torch.Tensor:
+    """Row pass with ``row_taps`` then column pass with ``col_taps`` (default: the same
+    taps), each applying the boundary rule to its own input; t is kept in f32."""
+    if x.dtype in (torch.uint8, torch.int32):
+        raise TypeError("sepconv takes f32, f16 or bf16 images")
+    rt = Taps(row_taps, False, ndim=1)
+    ct = Taps(row_taps if col_taps is None else col_taps, False, ndim=1)
+    if rt.mem != ct.mem:
+        raise ValueError("row and column taps must both be on the host or both on the device")
+    y = _out_like(x, out, out_dtype, False)
+    xi, yi = image(x), image(y)
+    vptr = _variant(variant)
+    need = lib().imagecl_sepconv_workspace_size(x.size(1), x.size(0), vptr)
+    ws_ptr, ws_bytes = None, 0
+    if need:
+        if workspace is None:
+            workspace = torch.empty(need, dtype=torch.uint8, device=x.device)
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    check(lib().imagecl_sepconv(ctypes.byref(xi), ctypes.byref(yi), ctypes.c_void_p(rt.ptr),
+                                rt.shape[0], ctypes.c_void_p(ct.ptr), ct.shape[0], rt.mem,
+                                BORDERS[border], float(border_value), vptr,
+                                ctypes.c_void_p(ws_ptr), ws_bytes,
+                                ctypes.c_void_p(stream_handle(stream))))
+    return y
+
+
+def harris(x: torch.Tensor, sobel_x, sobel_y, window, k: float = 0.04, out=None, variant=None,
+           workspace=None, stream=None) -> torch.Tensor:
+    """Harris response of the f32 image ``x`` with the given 3x3 Sobel taps and odd
+    window (clamped boundary on every stage)."""
+    if x.dtype != torch.float32:
+        raise TypeError("harris takes an f32 image")
+    sx, sy = Taps(sobel_x, False), Taps(sobel_y, False)
+    win = Taps(window, False)
+    if not (sx.mem == sy.mem == win.mem):
+        raise ValueError("all Harris taps must be on the host or all on the device")
+    if sx.shape != (3, 3) or sy.shape != (3, 3) or win.shape[0] != win.shape[1]:
+        raise ValueError("Sobel taps must be 3x3 and the window square")
+    y = out if out is not None else torch.empty_like(x)
+    xi, yi = image(x), image(y)
+    vptr = _variant(variant)
+    need = lib().imagecl_harris_workspace_size(x.size(1), x.size(0), vptr)
+    ws_ptr, ws_bytes = None, 0
+    if need:
+        if workspace is None:
+            workspace = torch.empty(need, dtype=torch.uint8, device=x.device)
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    check(lib().imagecl_harris(ctypes.byref(xi), ctypes.byref(yi), ctypes.c_void_p(sx.ptr),
+                               ctypes.c_void_p(sy.ptr), ctypes.c_void_p(win.ptr), win.shape[0],
+                               float(k), sx.mem, vptr, ctypes.c_void_p(ws_ptr), ws_bytes,
+                               ctypes.c_void_p(stream_handle(stream))))
+    return y
+
+
 def problem(op: int, in_dtype, out_dtype, kw: int, kh: int, width: int, height: int,
             border: str = "clamp", taps_mem: int = _abi.MEM_HOST) -> _abi.Problem:
     def dt(d):

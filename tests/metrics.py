@@ -76,3 +76,39 @@ def conv_reference(x, w, border="clamp", bv=0.0, rows=None, halo=None):
         return y64, None
     s = oracle.conv2d(np.abs(to_f64(x)), np.abs(to_f64(w)), border, abs(bv), rows=rows)
     return y64, s
+
+
+def sep_reference(x, row, col, border="clamp", bv=0.0, rows=None, halo=None):
+    """(y64, s) for sepconv; s = (|c| x |r|) applied to |x| (|bv| outside), the scale of
+    the summed terms of both passes."""
+    if rows is not None and halo is not None:
+        x, rows = band(x, rows, halo)
+    y64 = oracle.sepconv(x, row, col, border, bv, rows=rows)
+    s = oracle.sepconv(np.abs(to_f64(x)), np.abs(to_f64(row)), np.abs(to_f64(col)), border, abs(bv),
+                       rows=rows)
+    return y64, s
+
+
+TOL_HARRIS = 1e-5
+
+
+def harris_reference(img, sx, sy, win, k=0.04, rows=None, halo=None):
+    """(R64, scale) for Harris.  scale = T^2 with T = |G| (*) (Ax^2 + Ay^2) and
+    A = |S| (*) |I|: a bound on |Sxx|, |Syy|, |Sxy| that also covers the rounding of the
+    Sobel sums (|Ix| <= Ax), so e = |R - R64| / T^2 is the forward error of R relative
+    to the size of its terms."""
+    if rows is not None and halo is not None:
+        img, rows = band(img, rows, halo)
+    R = oracle.harris(img, sx, sy, win, k, rows=rows)
+    ai = np.abs(to_f64(img))
+    ax = oracle.conv2d(ai, np.abs(to_f64(sx)))
+    ay = oracle.conv2d(ai, np.abs(to_f64(sy)))
+    T = oracle.conv2d(ax * ax + ay * ay, np.abs(to_f64(win)), rows=rows)
+    return R, T * T
+
+
+def check_harris_output(gpu, R64, scale, what=""):
+    e = np.abs(to_f64(gpu) - R64) / np.maximum(scale, 1e-30)
+    emax = float(e.max()) if e.size else 0.0
+    assert emax <= TOL_HARRIS, f"{what}: max scaled error {emax:.3e} > {TOL_HARRIS}"
+    return emax

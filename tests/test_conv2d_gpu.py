@@ -4,6 +4,7 @@ import pytest
 import torch
 
 import oracle
+from gpu_util import empty_padded, padded
 from metrics import check_float_output, conv_reference, to_f64
 from paper_1605_06399_gb300 import ImclError, _abi, ops, synth
 
@@ -26,21 +27,6 @@ def _inputs(g, h, w, dt):
     if dt == "u8":
         return torch.from_numpy(synth.uniform_u8(g, h, w))
     return synth.to_storage(synth.uniform_f32(g, h, w), dt)
-
-
-def padded(t: torch.Tensor, device="cuda") -> torch.Tensor:
-    """A (h, w) view of a buffer whose rows are padded to a multiple of 128 bytes."""
-    h, w = t.shape
-    per = 128 // t.element_size()
-    buf = torch.zeros((h, (w + per - 1) // per * per), dtype=t.dtype, device=device)
-    v = buf[:, :w]
-    v.copy_(t.to(device))
-    return v
-
-
-def empty_padded(h, w, dtype):
-    per = 128 // torch.empty((), dtype=dtype).element_size()
-    return torch.empty((h, (w + per - 1) // per * per), dtype=dtype, device="cuda")[:, :w]
 
 
 def _variants_for(in_t, out_t, k, h, w, taps_mem, border):
