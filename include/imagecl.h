@@ -165,6 +165,36 @@ imcl_status imagecl_harris(const imcl_image *in, const imcl_image *out, const fl
 /* Workspace bytes imagecl_harris needs for `variant` (0 for fused variants and NULL). */
 size_t imagecl_harris_workspace_size(int32_t width, int32_t height, const imcl_variant *variant);
 
+/*
+ * imagecl_sepconv_noalloc -- the separable correlation for callers that may not
+ * allocate device memory.  The paper has no counterpart; this entry point exists for
+ * deployment.  Some callers cannot call cudaMalloc (or anything that allocates) while
+ * they run: code recording a stream into a CUDA graph, plugins whose host framework
+ * owns all device memory through its own allocator, loops that cannot take the
+ * synchronisation an allocation may cause.  They still pass their own input and output
+ * images; the one intermediate this operation needs (the f32 row pass) lives in a
+ * fixed array of IMAGECL_NOALLOC_SCRATCH_BYTES that the library declares in device
+ * memory.  Every GPU that loads the library holds that array until the process exits.
+ *
+ * Arguments and result are those of imagecl_sepconv run with the PLAIN variant (same
+ * kernels, same result bit for bit), without the variant and workspace arguments.
+ * Limits and behaviour:
+ *  - width * height * 4 must not exceed IMAGECL_NOALLOC_SCRATCH_BYTES (16 MiB, i.e.
+ *    4,194,304 pixels); larger images -> IMCL_ERR_UNSUPPORTED.
+ *  - No cudaMalloc, cudaFree or other allocating call is made.  The first call on each
+ *    device looks up the array's device address (cudaGetSymbolAddress) with that device
+ *    current and caches it; make that first call before any stream capture begins.
+ *  - All calls share the one array per device, which keeps the last call's contents.
+ *    Nothing in it needs clearing (the row pass writes every value the column pass
+ *    reads), but calls whose kernels overlap on the same GPU race on it: order them on
+ *    one stream or synchronise between them.
+ */
+#define IMAGECL_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+imcl_status imagecl_sepconv_noalloc(const imcl_image *in, const imcl_image *out,
+                                    const float *row_taps, int32_t nrow, const float *col_taps,
+                                    int32_t ncol, int32_t taps_mem, int32_t border,
+                                    double border_value, void *stream);
+
 /* ------------------------------------------------------------------ tuning */
 
 /* Number of compiled variants applicable to `problem` (0 if none), and the idx-th one.
