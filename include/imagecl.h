@@ -133,16 +133,18 @@ imcl_status imagecl_conv2d(const imcl_image *in, const imcl_image *out, const vo
  * The fused variants (the default) need no workspace.  The PLAIN variant runs the two
  * passes as two kernels with t in `workspace` (width*height*4 bytes, device memory the
  * caller owns; see imagecl_sepconv_workspace_size); a NULL or short workspace for it
- * -> IMCL_ERR_INVALID.
+ * -> IMCL_ERR_INVALID.  The default selection picks the two-kernel form only when no
+ * fused variant fits or the tuner found it fastest: ask imagecl_sepconv_workspace_size.
  */
 imcl_status imagecl_sepconv(const imcl_image *in, const imcl_image *out, const float *row_taps,
                             int32_t nrow, const float *col_taps, int32_t ncol, int32_t taps_mem,
                             int32_t border, double border_value, const imcl_variant *variant,
                             void *workspace, size_t workspace_bytes, void *stream);
 
-/* Workspace bytes imagecl_sepconv needs for `variant` on a width x height image (0 for
- * the fused variants and for NULL, the default). */
-size_t imagecl_sepconv_workspace_size(int32_t width, int32_t height, const imcl_variant *variant);
+/* Workspace bytes imagecl_sepconv needs for `problem` (op IMCL_OP_SEPCONV, sizes, tap
+ * counts, types, border, taps memory) run with `variant`: 0 for the fused variants.
+ * NULL: the variant a call with variant NULL would use now (the tuned one if cached). */
+size_t imagecl_sepconv_workspace_size(const imcl_problem *problem, const imcl_variant *variant);
 
 /*
  * Harris corner response (§6 corner-detection benchmark: a Sobel kernel then a Harris
@@ -162,8 +164,52 @@ imcl_status imagecl_harris(const imcl_image *in, const imcl_image *out, const fl
                            int32_t taps_mem, const imcl_variant *variant, void *workspace,
                            size_t workspace_bytes, void *stream);
 
-/* Workspace bytes imagecl_harris needs for `variant` (0 for fused variants and NULL). */
-size_t imagecl_harris_workspace_size(int32_t width, int32_t height, const imcl_variant *variant);
+/* Workspace bytes imagecl_harris needs for `problem` (op IMCL_OP_HARRIS, kw = window
+ * side) run with `variant`: 0 for fused variants; NULL as for imagecl_sepconv. */
+size_t imagecl_harris_workspace_size(const imcl_problem *problem, const imcl_variant *variant);
+
+/* ------------------------------------------------------------------ gradients */
+
+/*
+ * Adjoint (backward) passes.  The forward operators are linear in their input and in
+ * their taps (Harris: polynomial), so the gradients are the transposed maps:
+ *  - input gradient: correlation of grad_out with the flipped taps under a zero border,
+ *    plus, for the clamped rule, the contributions of taps that were clamped, summed
+ *    onto the first/last rows and columns (the transpose of the clamp);
+ *  - tap gradient: dtaps[o] = sum_p grad_out(p) * in_b(p + o), with in_b the boundary
+ *    rule's read, reduced per CTA and then over CTAs in a fixed order (deterministic);
+ *  - Harris: the chain rule R -> (Sxx, Syy, Sxy) -> products -> (Ix, Iy) -> image, and
+ *    the window and Sobel tap gradients on the way.
+ * grad_out is f32 with the size of `in`; in is f32, f16 or bf16 (Harris: f32).
+ * grad_in (f32, nullable: not computed) must not overlap grad_out or in.  The tap
+ * gradients (nullable) are device f32 arrays the caller owns, written (not accumulated).
+ * workspace: device memory the caller owns, at least the *_workspace_size bytes for the
+ * same sizes (always required).  Asynchronous on `stream`.
+ */
+imcl_status imagecl_conv2d_backward(const imcl_image *grad_out, const imcl_image *in,
+                                    const float *taps, int32_t kw, int32_t kh, int32_t taps_mem,
+                                    int32_t border, double border_value,
+                                    const imcl_image *grad_in, float *grad_taps,
+                                    void *workspace, size_t workspace_bytes, void *stream);
+size_t imagecl_conv2d_backward_workspace_size(int32_t width, int32_t height, int32_t kw,
+                                              int32_t kh);
+
+imcl_status imagecl_sepconv_backward(const imcl_image *grad_out, const imcl_image *in,
+                                     const float *row_taps, int32_t nrow, const float *col_taps,
+                                     int32_t ncol, int32_t taps_mem, int32_t border,
+                                     double border_value, const imcl_image *grad_in,
+                                     float *grad_row, float *grad_col, void *workspace,
+                                     size_t workspace_bytes, void *stream);
+size_t imagecl_sepconv_backward_workspace_size(int32_t width, int32_t height, int32_t nrow,
+                                               int32_t ncol);
+
+imcl_status imagecl_harris_backward(const imcl_image *grad_out, const imcl_image *in,
+                                    const float *sobel_x, const float *sobel_y,
+                                    const float *window, int32_t wk, float k, int32_t taps_mem,
+                                    const imcl_image *grad_in, float *grad_sobel_x,
+                                    float *grad_sobel_y, float *grad_window, void *workspace,
+                                    size_t workspace_bytes, void *stream);
+size_t imagecl_harris_backward_workspace_size(int32_t width, int32_t height, int32_t wk);
 
 /*
  * imagecl_sepconv_noalloc -- the separable correlation for callers that may not

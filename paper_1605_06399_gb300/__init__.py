@@ -7,6 +7,9 @@ with ``python -m paper_1605_06399_gb300.build``; calls fail loudly if it is miss
 from .ops import (conv2d, sepconv, harris, default_variant, device_status, image, problem, tune, tune_clear,
                   tune_load, tune_save, tune_set, variants, version)
 from ._abi import ImclError
+from . import autograd
+from .ops import conv2d_backward, harris_backward, sepconv_backward
 
 __all__ = ["conv2d", "sepconv", "harris", "default_variant", "device_status", "image", "problem", "tune", "tune_clear",
-           "tune_load", "tune_save", "tune_set", "variants", "version", "ImclError"]
+           "tune_load", "tune_save", "tune_set", "variants", "version", "ImclError", "autograd", "conv2d_backward",
+           "sepconv_backward", "harris_backward"]

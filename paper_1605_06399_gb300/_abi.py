@@ -77,13 +77,25 @@ SIGNATURES = {
                                  c_int32, c_double, P(Variant), c_void_p]),
     "imagecl_sepconv": (c_int32, [P(Image), P(Image), c_void_p, c_int32, c_void_p, c_int32, c_int32,
                                   c_int32, c_double, P(Variant), c_void_p, ctypes.c_size_t, c_void_p]),
-    "imagecl_sepconv_workspace_size": (ctypes.c_size_t, [c_int32, c_int32, P(Variant)]),
+    "imagecl_sepconv_workspace_size": (ctypes.c_size_t, [P(Problem), P(Variant)]),
     "imagecl_harris": (c_int32, [P(Image), P(Image), c_void_p, c_void_p, c_void_p, c_int32,
                                  ctypes.c_float, c_int32, P(Variant), c_void_p, ctypes.c_size_t,
                                  c_void_p]),
-    "imagecl_harris_workspace_size": (ctypes.c_size_t, [c_int32, c_int32, P(Variant)]),
+    "imagecl_harris_workspace_size": (ctypes.c_size_t, [P(Problem), P(Variant)]),
     "imagecl_sepconv_noalloc": (c_int32, [P(Image), P(Image), c_void_p, c_int32, c_void_p, c_int32,
                                           c_int32, c_int32, c_double, c_void_p]),
+    "imagecl_conv2d_backward": (c_int32, [P(Image), P(Image), c_void_p, c_int32, c_int32, c_int32,
+                                          c_int32, c_double, P(Image), c_void_p, c_void_p,
+                                          ctypes.c_size_t, c_void_p]),
+    "imagecl_conv2d_backward_workspace_size": (ctypes.c_size_t, [c_int32, c_int32, c_int32, c_int32]),
+    "imagecl_sepconv_backward": (c_int32, [P(Image), P(Image), c_void_p, c_int32, c_void_p, c_int32,
+                                           c_int32, c_int32, c_double, P(Image), c_void_p, c_void_p,
+                                           c_void_p, ctypes.c_size_t, c_void_p]),
+    "imagecl_sepconv_backward_workspace_size": (ctypes.c_size_t, [c_int32, c_int32, c_int32, c_int32]),
+    "imagecl_harris_backward": (c_int32, [P(Image), P(Image), c_void_p, c_void_p, c_void_p, c_int32,
+                                          ctypes.c_float, c_int32, P(Image), c_void_p, c_void_p,
+                                          c_void_p, c_void_p, ctypes.c_size_t, c_void_p]),
+    "imagecl_harris_backward_workspace_size": (ctypes.c_size_t, [c_int32, c_int32, c_int32]),
     "imagecl_variant_count": (c_int32, [P(Problem)]),
     "imagecl_variant_get": (c_int32, [P(Problem), c_int32, P(Variant)]),
     "imagecl_variant_default": (c_int32, [P(Problem), P(Variant)]),

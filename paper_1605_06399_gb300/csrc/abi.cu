@@ -132,20 +132,56 @@ const ConvEntry* conv_find(const ConvCall& c, const imcl_variant& v) {
     return nullptr;
 }
 
+imcl_variant pick_default(const std::vector<const ConvEntry*>& entries, int taps_mem, bool tma_ok, int want_px,
+                          int want_py) {
+    const int filt = taps_mem == IMCL_MEM_DEVICE ? IMCL_FILT_SMEM : IMCL_FILT_PARAM;
+    auto ok = [&](const ConvEntry* e) {
+        return e->v.kind == IMCL_KIND_TILED && e->v.filt == filt && e->v.map == IMCL_MAP_BLOCKED &&
+               (tma_ok || e->v.load != IMCL_LOAD_TMA);
+    };
+    const int first = tma_ok ? IMCL_LOAD_TMA : IMCL_LOAD_GLOBAL;
+    // the preferred coarsening with TMA staging when the buffers allow it, else the L1 path
+    for (const ConvEntry* e : entries)
+        if (ok(e) && e->v.py == want_py && (want_px <= 0 || e->v.px == want_px) && e->v.load == first) return e->v;
+    for (const ConvEntry* e : entries)
+        if (ok(e) && e->v.py == want_py && (want_px <= 0 || e->v.px == want_px)) return e->v;
+    // any feasible tiled variant, the L1 path before cooperative staging
+    for (int load : {first, (int)IMCL_LOAD_GLOBAL, (int)IMCL_LOAD_SMEM})
+        for (const ConvEntry* e : entries)
+            if (ok(e) && e->v.load == load) return e->v;
+    for (const ConvEntry* e : entries)
+        if (e->v.kind == IMCL_KIND_PLAIN) return e->v;
+    imcl_variant none{};
+    none.kind = -1;
+    return none;
+}
+
+ConvCall problem_call(const imcl_problem& p) {
+    ConvCall c;
+    c.in = reinterpret_cast<const void*>(uintptr_t(256));
+    c.out = reinterpret_cast<void*>(uintptr_t(512));
+    c.in_dtype = p.in_dtype;
+    c.out_dtype = p.out_dtype;
+    c.W = p.width;
+    c.H = p.height;
+    c.in_pitch_b = ((int64_t)p.width * dtype_size(p.in_dtype) + 127) / 128 * 128;
+    c.out_pitch_b = ((int64_t)p.width * dtype_size(p.out_dtype) + 127) / 128 * 128;
+    c.kw = p.kw;
+    c.kh = p.kh;
+    c.taps_mem = p.taps_mem;
+    c.border = p.border;
+    return c;
+}
+
+bool tma_aligned(const ConvCall& c) {
+    return (reinterpret_cast<uintptr_t>(c.in) % 16) == 0 && (c.in_pitch_b % 16) == 0;
+}
+
 imcl_variant conv_default_variant(const ConvCall& c) {
     imcl_variant v{};
     if (cache_lookup(conv_problem(c), &v)) return v;
-    const bool tma_ok = (reinterpret_cast<uintptr_t>(c.in) % 16) == 0 && (c.in_pitch_b % 16) == 0;
-    const int filt = c.taps_mem == IMCL_MEM_DEVICE ? IMCL_FILT_SMEM : IMCL_FILT_PARAM;
-    for (const ConvEntry* e : conv_entries_for(c.in_dtype, c.out_dtype, c.kw, c.kh, c.taps_mem)) {
-        if (e->v.kind != IMCL_KIND_TILED || e->v.filt != filt || e->v.map != IMCL_MAP_BLOCKED) continue;
-        if (e->v.px != 4 || e->v.py != 4) continue;
-        if (tma_ok ? e->v.load == IMCL_LOAD_TMA : e->v.load == IMCL_LOAD_GLOBAL) return e->v;
-    }
-    for (const ConvEntry* e : conv_entries_for(c.in_dtype, c.out_dtype, c.kw, c.kh, c.taps_mem))
-        if (e->v.kind == IMCL_KIND_PLAIN) return e->v;
-    v.kind = -1;
-    return v;
+    return pick_default(conv_entries_for(c.in_dtype, c.out_dtype, c.kw, c.kh, c.taps_mem), c.taps_mem,
+                        tma_aligned(c), 4, 4);
 }
 
 imcl_status conv_prepare(const imcl_image* in, const imcl_image* out, const void* taps, int taps_dtype,

@@ -33,19 +33,7 @@ static const ConvEntry* harris_find(const ConvCall& c, const imcl_variant& v) {
 imcl_variant harris_default_variant(const ConvCall& c) {
     imcl_variant v{};
     if (cache_lookup(harris_problem(c), &v)) return v;
-    const bool tma_ok = (reinterpret_cast<uintptr_t>(c.in) % 16) == 0 && (c.in_pitch_b % 16) == 0;
-    const int filt = c.taps_mem == IMCL_MEM_DEVICE ? IMCL_FILT_SMEM : IMCL_FILT_PARAM;
-    const auto entries = harris_entries_for(c.kw, c.taps_mem);
-    for (const ConvEntry* e : entries)
-        if (e->v.kind == IMCL_KIND_TILED && e->v.filt == filt && e->v.py == 2 &&
-            e->v.load == (tma_ok ? IMCL_LOAD_TMA : IMCL_LOAD_SMEM))
-            return e->v;
-    for (const ConvEntry* e : entries)
-        if (e->v.kind == IMCL_KIND_TILED && e->v.load == IMCL_LOAD_SMEM && e->v.filt == filt) return e->v;
-    for (const ConvEntry* e : entries)
-        if (e->v.kind == IMCL_KIND_PLAIN) return e->v;
-    v.kind = -1;
-    return v;
+    return pick_default(harris_entries_for(c.kw, c.taps_mem), c.taps_mem, tma_aligned(c), 4, 2);
 }
 
 imcl_status harris_prepare(const imcl_image* in, const imcl_image* out, const float* sx, const float* sy,
@@ -115,9 +103,12 @@ imcl_status imagecl_harris(const imcl_image* in, const imcl_image* out, const fl
     return harris_run(c, variant, static_cast<cudaStream_t>(stream));
 }
 
-size_t imagecl_harris_workspace_size(int32_t width, int32_t height, const imcl_variant* variant) {
-    if (width <= 0 || height <= 0) return 0;
-    if (variant && variant->kind == IMCL_KIND_PLAIN) return (size_t)2 * width * (size_t)height * sizeof(float);
+size_t imagecl_harris_workspace_size(const imcl_problem* problem, const imcl_variant* variant) {
+    if (!problem || problem->width <= 0 || problem->height <= 0) return 0;
+    imcl_problem q = *problem;
+    q.in_dtype = q.out_dtype = IMCL_F32;
+    const imcl_variant v = variant ? *variant : harris_default_variant(problem_call(q));
+    if (v.kind == IMCL_KIND_PLAIN) return (size_t)2 * problem->width * (size_t)problem->height * sizeof(float);
     return 0;
 }
 

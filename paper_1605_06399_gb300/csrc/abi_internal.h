@@ -18,6 +18,13 @@ bool cache_lookup(const imcl_problem& p, imcl_variant* v);
 void cache_store(const imcl_problem& p, const imcl_variant& v);
 
 imcl_problem conv_problem(const ConvCall& c);
+// The variant a call uses when none is given and none is cached: taps memory decides
+// where the taps live, TMA staging only on 16-byte aligned buffers, PLAIN last.
+imcl_variant pick_default(const std::vector<const ConvEntry*>& entries, int taps_mem, bool tma_ok, int want_px,
+                          int want_py);
+bool tma_aligned(const ConvCall& c);
+// A ConvCall describing `p` on hypothetical, fully aligned buffers (no device).
+ConvCall problem_call(const imcl_problem& p);
 std::vector<const ConvEntry*> conv_entries_for(int in_dt, int out_dt, int kw, int kh, int taps_mem);
 const ConvEntry* conv_find(const ConvCall& c, const imcl_variant& v);
 imcl_variant conv_default_variant(const ConvCall& c);

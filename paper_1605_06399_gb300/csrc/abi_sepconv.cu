@@ -15,7 +15,8 @@ imcl_problem sep_problem(const ConvCall& c) {
 
 std::vector<const ConvEntry*> sep_entries_for(int in_dt, int out_dt, int nr, int nc, int taps_mem) {
     std::vector<const ConvEntry*> r;
-    const int R = (std::max(nr, nc) - 1) / 2;
+    // a single-tap pass on both axes (radius 0) runs on the radius-1 kernels, zero-padded
+    const int R = std::max(1, (std::max(nr, nc) - 1) / 2);
     for (const ConvEntry& e : sep_table()) {
         if (e.in_dtype != in_dt || e.out_dtype != out_dt) continue;
         if (e.v.kind == IMCL_KIND_PLAIN) { r.push_back(&e); continue; }
@@ -39,19 +40,8 @@ static const ConvEntry* sep_find(const ConvCall& c, const imcl_variant& v) {
 imcl_variant sep_default_variant(const ConvCall& c) {
     imcl_variant v{};
     if (cache_lookup(sep_problem(c), &v)) return v;
-    const bool tma_ok = (reinterpret_cast<uintptr_t>(c.in) % 16) == 0 && (c.in_pitch_b % 16) == 0;
-    const int filt = c.taps_mem == IMCL_MEM_DEVICE ? IMCL_FILT_SMEM : IMCL_FILT_PARAM;
-    const auto entries = sep_entries_for(c.in_dtype, c.out_dtype, c.kw, c.kh, c.taps_mem);
-    for (int pass = 0; pass < 2; ++pass)
-        for (const ConvEntry* e : entries) {
-            if (e->v.kind != IMCL_KIND_TILED || e->v.filt != filt || e->v.py != 8) continue;
-            const int want = pass == 0 ? (tma_ok ? IMCL_LOAD_TMA : IMCL_LOAD_GLOBAL) : IMCL_LOAD_SMEM;
-            if (e->v.load == want) return e->v;
-        }
-    for (const ConvEntry* e : entries)
-        if (e->v.kind == IMCL_KIND_PLAIN) return e->v;
-    v.kind = -1;
-    return v;
+    return pick_default(sep_entries_for(c.in_dtype, c.out_dtype, c.kw, c.kh, c.taps_mem), c.taps_mem,
+                        tma_aligned(c), 4, 8);
 }
 
 imcl_status sep_prepare(const imcl_image* in, const imcl_image* out, const float* row, int nr, const float* col,
@@ -121,9 +111,10 @@ imcl_status imagecl_sepconv(const imcl_image* in, const imcl_image* out, const f
     return sep_run(c, variant, static_cast<cudaStream_t>(stream));
 }
 
-size_t imagecl_sepconv_workspace_size(int32_t width, int32_t height, const imcl_variant* variant) {
-    if (width <= 0 || height <= 0) return 0;
-    if (variant && variant->kind == IMCL_KIND_PLAIN) return (size_t)width * (size_t)height * sizeof(float);
+size_t imagecl_sepconv_workspace_size(const imcl_problem* problem, const imcl_variant* variant) {
+    if (!problem || problem->width <= 0 || problem->height <= 0) return 0;
+    const imcl_variant v = variant ? *variant : sep_default_variant(problem_call(*problem));
+    if (v.kind == IMCL_KIND_PLAIN) return (size_t)problem->width * (size_t)problem->height * sizeof(float);
     return 0;
 }
 

@@ -1,0 +1,342 @@
+// backward.cu -- the adjoint passes of conv2d, sepconv and Harris, composed from the
+// forward kernels (zero-border correlations with flipped taps) and the building blocks
+// of backward_kernels.cuh.  Every launch goes on the caller's stream; intermediate planes
+// and partial sums live in the caller's workspace.
+#include <algorithm>
+#include <vector>
+
+#include "abi_internal.h"
+#include "backward_internal.h"
+#include "backward_kernels.cuh"
+
+namespace imcl {
+
+static size_t plane_pitch(int W) { return (size_t)round_up(W, 32); }              // floats (128 B)
+static size_t plane_floats(int W, int H) { return plane_pitch(W) * (size_t)H; }
+static int wgrad_grid(int W, int H) {
+    const int tiles = ((W + kWgTileW - 1) / kWgTileW) * ((H + kWgTileH - 1) / kWgTileH);
+    return std::min(tiles, kWgMaxParts);
+}
+constexpr size_t kTapScratch = 4 * kMaxAdjTaps + 64;                                // floats
+
+size_t conv2d_backward_ws(int W, int H, int kw, int kh) {
+    return (kTapScratch + (size_t)wgrad_grid(W, H) * kw * kh) * sizeof(float);
+}
+size_t sepconv_backward_ws(int W, int H, int nr, int nc) {
+    return (2 * plane_floats(W, H) + kTapScratch + (size_t)wgrad_grid(W, H) * std::max(nr, nc)) * sizeof(float);
+}
+size_t harris_backward_ws(int W, int H, int wk) {
+    return (9 * plane_floats(W, H) + kTapScratch + (size_t)3 * wgrad_grid(W, H) * wk * wk) * sizeof(float);
+}
+
+// ------------------------------------------------------------------ helpers
+// A ConvCall for an f32 -> f32 correlation of workspace / user planes.
+static ConvCall f32_call(const ConvCall& base, const float* in, int64_t in_pitch_b, float* out, int64_t out_pitch_b) {
+    ConvCall c = base;
+    c.in = in;
+    c.out = out;
+    c.in_dtype = IMCL_F32;
+    c.out_dtype = IMCL_F32;
+    c.in_pitch_b = in_pitch_b;
+    c.out_pitch_b = out_pitch_b;
+    c.workspace = nullptr;
+    c.ws_bytes = 0;
+    return c;
+}
+
+// Taps of one operand: host vectors, or device pointers into the workspace.
+struct TapSet {
+    const float* orig = nullptr;       // as given (host or device)
+    const float* flipped = nullptr;    // flip(w) (host or device)
+    std::vector<float> host_flip;
+};
+
+static imcl_status make_taps(const float* taps, int n, int taps_mem, float* dev_slot, cudaStream_t s, TapSet* t) {
+    t->orig = taps;
+    if (taps_mem == IMCL_MEM_HOST) {
+        t->host_flip.assign(taps, taps + n);
+        std::reverse(t->host_flip.begin(), t->host_flip.end());
+        t->flipped = t->host_flip.data();
+        return IMCL_OK;
+    }
+    k_flip_taps<<<(n + 255) / 256, 256, 0, s>>>(taps, n, 1, dev_slot, nullptr);
+    t->flipped = dev_slot;
+    return cuda_fail(cudaGetLastError(), "flip taps");
+}
+
+// the single unit tap (row or column pass that leaves its axis alone)
+static const float kOne = 1.0f;
+static imcl_status unit_tap(int taps_mem, float* dev_slot, cudaStream_t s, const float** out) {
+    if (taps_mem == IMCL_MEM_HOST) { *out = &kOne; return IMCL_OK; }
+    k_flip_taps<<<1, 32, 0, s>>>(nullptr, 0, 0, nullptr, dev_slot);
+    *out = dev_slot;
+    return cuda_fail(cudaGetLastError(), "unit tap");
+}
+
+static imcl_status edges_2d(float* dx, int64_t dx_pitch, const float* g1, int64_t g1_pitch, const float* w1,
+                            const float* g2, int64_t g2_pitch, const float* w2, int W, int H, int kw, int kh,
+                            int taps_mem, cudaStream_t s) {
+    AdjTaps tp;
+    memset(&tp, 0, sizeof tp);
+    const float *w1d = nullptr, *w2d = nullptr;
+    if (taps_mem == IMCL_MEM_HOST) {
+        memcpy(tp.w1, w1, sizeof(float) * kw * kh);
+        if (w2) memcpy(tp.w2, w2, sizeof(float) * kw * kh);
+    } else {
+        w1d = w1;
+        w2d = w2;
+    }
+    const int nedge = (H > 1 ? 2 * W : W) + (W > 1 ? 2 : 1) * std::max(H - 2, 0);
+    k_adjoint_edges_2d<<<(nedge + 255) / 256, 256, 0, s>>>(dx, dx_pitch, g1, g1_pitch, g2, g2_pitch, W, H, kw, kh,
+                                                            w1d, w2d, tp);
+    return cuda_fail(cudaGetLastError(), "adjoint edges");
+}
+
+static imcl_status fold_1d(float* dst, int64_t dst_pitch, const float* g, int64_t g_pitch, int W, int H, int n,
+                           int axis, const float* w, int taps_mem, cudaStream_t s) {
+    TapsParam<float, 33> tp;
+    for (int i = 0; i < 33; ++i) tp.w[i] = 0.f;
+    const float* wd = nullptr;
+    if (taps_mem == IMCL_MEM_HOST) for (int i = 0; i < n; ++i) tp.w[i] = w[i];
+    else wd = w;
+    const int lines = axis == 0 ? H : W;
+    k_fold_1d<<<(lines + 255) / 256, 256, 0, s>>>(dst, dst_pitch, g, g_pitch, W, H, n, axis, wd, tp);
+    return cuda_fail(cudaGetLastError(), "fold 1d");
+}
+
+template <typename Tx>
+static imcl_status wgrad_partials(const float* g, int64_t g_pitch, const Tx* x, int64_t x_pitch, int W, int H, int kw,
+                                  int kh, int border, float bv, float* partials, cudaStream_t s) {
+    const int grid = wgrad_grid(W, H);
+    const int smem = (kWgTileW * kWgTileH + (kWgTileW + kw - 1) * (kWgTileH + kh - 1) + 256 * 4) * 4;
+    if (kh * ((kw + 3) / 4) > 256) return fail(IMCL_ERR_UNSUPPORTED, "tap gradient: too many taps");
+    k_wgrad_partial<Tx><<<grid, 256, smem, s>>>(g, g_pitch, x, x_pitch, W, H, kw, kh, border, bv, partials);
+    return cuda_fail(cudaGetLastError(), "tap gradient partials");
+}
+
+static imcl_status wgrad_any(const float* g, int64_t g_pitch, const void* x, int x_dtype, int64_t x_pitch_b, int W,
+                             int H, int kw, int kh, int border, float bv, float* partials, cudaStream_t s) {
+    switch (x_dtype) {
+        case IMCL_F32:
+            return wgrad_partials<float>(g, g_pitch, static_cast<const float*>(x), x_pitch_b / 4, W, H, kw, kh, border,
+                                         bv, partials, s);
+        case IMCL_F16:
+            return wgrad_partials<__half>(g, g_pitch, static_cast<const __half*>(x), x_pitch_b / 2, W, H, kw, kh, border,
+                                          bv, partials, s);
+        case IMCL_BF16:
+            return wgrad_partials<__nv_bfloat16>(g, g_pitch, static_cast<const __nv_bfloat16*>(x), x_pitch_b / 2, W, H,
+                                                 kw, kh, border, bv, partials, s);
+        default: return fail(IMCL_ERR_UNSUPPORTED, "tap gradient: pixel type");
+    }
+}
+
+static imcl_status finalize(const float* partials, int nparts, int ntaps, float* out, cudaStream_t s) {
+    k_wgrad_finalize<<<ntaps, 256, 0, s>>>(partials, nparts, ntaps, out, 0);
+    return cuda_fail(cudaGetLastError(), "tap gradient finalize");
+}
+
+// A separable pass inside the backward runs a fused variant: the tuned one unless the
+// tuning cache chose the two-kernel form (which needs a workspace these passes do not
+// have), then the built-in fused default.
+static imcl_status sep_run_fused(const ConvCall& c, cudaStream_t s) {
+    imcl_variant v = sep_default_variant(c);
+    if (v.kind != IMCL_KIND_TILED)
+        v = pick_default(sep_entries_for(c.in_dtype, c.out_dtype, c.kw, c.kh, c.taps_mem), c.taps_mem,
+                         tma_aligned(c), 4, 8);
+    if (v.kind != IMCL_KIND_TILED) return fail(IMCL_ERR_UNSUPPORTED, "no fused separable variant for a backward pass");
+    return sep_run(c, &v, s);
+}
+
+#define IMCL_TRY(x)                          \
+    do {                                     \
+        imcl_status _st = (x);               \
+        if (_st != IMCL_OK) return _st;      \
+    } while (0)
+
+// ------------------------------------------------------------------ conv2d
+imcl_status conv2d_backward_run(const BwdArgs& b, cudaStream_t s) {
+    const ConvCall& f = b.fwd;
+    const int W = f.W, H = f.H, n = f.kw * f.kh;
+    float* ws = static_cast<float*>(b.workspace);
+    float* tap_slot = ws;
+    float* partials = ws + kTapScratch;
+    if (b.dx) {
+        TapSet t;
+        IMCL_TRY(make_taps(static_cast<const float*>(f.taps), n, f.taps_mem, tap_slot, s, &t));
+        ConvCall c = f32_call(f, b.g, b.g_pitch_b, b.dx, b.dx_pitch_b);
+        c.taps = t.flipped;
+        c.border = IMCL_BORDER_CONSTANT;
+        c.border_value = 0.0;
+        IMCL_TRY(conv_run(c, nullptr, s));
+        if (f.border == IMCL_BORDER_CLAMP)
+            IMCL_TRY(edges_2d(b.dx, b.dx_pitch_b / 4, b.g, b.g_pitch_b / 4, static_cast<const float*>(f.taps), nullptr, 0,
+                              nullptr, W, H, f.kw, f.kh, f.taps_mem, s));
+    }
+    if (b.dw0) {
+        IMCL_TRY(wgrad_any(b.g, b.g_pitch_b / 4, f.in, f.in_dtype, f.in_pitch_b, W, H, f.kw, f.kh, f.border,
+                           (float)f.border_value, partials, s));
+        IMCL_TRY(finalize(partials, wgrad_grid(W, H), n, b.dw0, s));
+    }
+    return IMCL_OK;
+}
+
+// ------------------------------------------------------------------ sepconv
+imcl_status sepconv_backward_run(const BwdArgs& b, cudaStream_t s) {
+    const ConvCall& f = b.fwd;
+    const int W = f.W, H = f.H, nr = f.kw, nc = f.kh;
+    const size_t pf = plane_floats(W, H);
+    const int64_t pp_b = (int64_t)plane_pitch(W) * 4;
+    float* ws = static_cast<float*>(b.workspace);
+    float* T = ws;
+    float* DT = ws + pf;
+    float* tap_slot = ws + 2 * pf;
+    float* partials = tap_slot + kTapScratch;
+    const float* one = nullptr;
+    IMCL_TRY(unit_tap(f.taps_mem, tap_slot + 4 * kMaxAdjTaps, s, &one));
+    TapSet tr, tc;
+    IMCL_TRY(make_taps(static_cast<const float*>(f.taps), nr, f.taps_mem, tap_slot, s, &tr));
+    IMCL_TRY(make_taps(static_cast<const float*>(f.taps2), nc, f.taps_mem, tap_slot + 64, s, &tc));
+
+    // dt = C^T g: zero-border column correlation with the flipped column taps, then fold
+    ConvCall c = f32_call(f, b.g, b.g_pitch_b, DT, pp_b);
+    c.kw = 1;
+    c.kh = nc;
+    c.taps = one;
+    c.taps2 = tc.flipped;
+    c.border = IMCL_BORDER_CONSTANT;
+    c.border_value = 0.0;
+    IMCL_TRY(sep_run_fused(c, s));
+    if (f.border == IMCL_BORDER_CLAMP)
+        IMCL_TRY(fold_1d(DT, pp_b / 4, b.g, b.g_pitch_b / 4, W, H, nc, 1, static_cast<const float*>(f.taps2),
+                         f.taps_mem, s));
+    if (b.dx) {   // dx = R^T dt
+        ConvCall r = f32_call(f, DT, pp_b, b.dx, b.dx_pitch_b);
+        r.kw = nr;
+        r.kh = 1;
+        r.taps = tr.flipped;
+        r.taps2 = one;
+        r.border = IMCL_BORDER_CONSTANT;
+        r.border_value = 0.0;
+        IMCL_TRY(sep_run_fused(r, s));
+        if (f.border == IMCL_BORDER_CLAMP)
+            IMCL_TRY(fold_1d(b.dx, b.dx_pitch_b / 4, DT, pp_b / 4, W, H, nr, 0, static_cast<const float*>(f.taps),
+                             f.taps_mem, s));
+    }
+    if (b.dw0) {  // drow[i] = sum dt(p) x_b(p + i - rr)
+        IMCL_TRY(wgrad_any(DT, pp_b / 4, f.in, f.in_dtype, f.in_pitch_b, W, H, nr, 1, f.border,
+                           (float)f.border_value, partials, s));
+        IMCL_TRY(finalize(partials, wgrad_grid(W, H), nr, b.dw0, s));
+    }
+    if (b.dw1) {  // dcol[j] = sum g(p) t_b(p + j - rc), t the forward row pass
+        ConvCall t = f;
+        t.out = T;
+        t.out_dtype = IMCL_F32;
+        t.out_pitch_b = pp_b;
+        t.kh = 1;
+        t.taps2 = one;
+        t.workspace = nullptr;
+        t.ws_bytes = 0;
+        IMCL_TRY(sep_run_fused(t, s));
+        IMCL_TRY(wgrad_any(b.g, b.g_pitch_b / 4, T, IMCL_F32, pp_b, W, H, 1, nc, f.border, (float)f.border_value,
+                           partials, s));
+        IMCL_TRY(finalize(partials, wgrad_grid(W, H), nc, b.dw1, s));
+    }
+    return IMCL_OK;
+}
+
+// ------------------------------------------------------------------ Harris
+imcl_status harris_backward_run(const BwdArgs& b, cudaStream_t s) {
+    const ConvCall& f = b.fwd;
+    const int W = f.W, H = f.H, wk = f.kw;
+    const size_t pf = plane_floats(W, H);
+    const int64_t pp = (int64_t)plane_pitch(W), pp_b = pp * 4;
+    float* ws = static_cast<float*>(b.workspace);
+    float* IX = ws;
+    float* IY = ws + pf;
+    float* P[3] = {ws + 2 * pf, ws + 3 * pf, ws + 4 * pf};
+    float* S[3] = {ws + 5 * pf, ws + 6 * pf, ws + 7 * pf};
+    float* TMP = ws + 8 * pf;
+    float* tap_slot = ws + 9 * pf;
+    float* partials = tap_slot + kTapScratch;
+    const float* sx = static_cast<const float*>(f.taps);
+    const float* sy = static_cast<const float*>(f.taps2);
+    const float* gw = static_cast<const float*>(f.taps3);
+    const int grid = wgrad_grid(W, H);
+    dim3 eg((W + 255) / 256, H);
+
+    // forward intermediates: Ix, Iy, P, S
+    ConvCall base = f;
+    base.kw = base.kh = 3;
+    ConvCall c = f32_call(base, static_cast<const float*>(f.in), f.in_pitch_b, IX, pp_b);
+    c.taps = sx;
+    c.border = IMCL_BORDER_CLAMP;
+    IMCL_TRY(conv_run(c, nullptr, s));
+    c.out = IY;
+    c.taps = sy;
+    IMCL_TRY(conv_run(c, nullptr, s));
+    k_harris_products<<<eg, 256, 0, s>>>(IX, IY, P[0], P[1], P[2], pp, W, H);
+    IMCL_TRY(cuda_fail(cudaGetLastError(), "harris products"));
+    ConvCall cw = f;
+    cw.kw = cw.kh = wk;
+    for (int ch = 0; ch < 3; ++ch) {
+        ConvCall w = f32_call(cw, P[ch], pp_b, S[ch], pp_b);
+        w.taps = gw;
+        w.border = IMCL_BORDER_CLAMP;
+        IMCL_TRY(conv_run(w, nullptr, s));
+    }
+    // dR/dS in place
+    k_harris_gs<<<eg, 256, 0, s>>>(b.g, b.g_pitch_b / 4, S[0], S[1], S[2], pp, W, H, f.hk);
+    IMCL_TRY(cuda_fail(cudaGetLastError(), "harris dR/dS"));
+    // window gradient: sum over the three channels
+    if (b.dw2) {
+        for (int ch = 0; ch < 3; ++ch)
+            IMCL_TRY(wgrad_partials<float>(S[ch], pp, P[ch], pp, W, H, wk, wk, IMCL_BORDER_CLAMP, 0.f,
+                                           partials + (size_t)ch * grid * wk * wk, s));
+        IMCL_TRY(finalize(partials, 3 * grid, wk * wk, b.dw2, s));
+    }
+    // gP = window adjoint of gS (into the P planes)
+    TapSet tg;
+    IMCL_TRY(make_taps(gw, wk * wk, f.taps_mem, tap_slot, s, &tg));
+    for (int ch = 0; ch < 3; ++ch) {
+        ConvCall w = f32_call(cw, S[ch], pp_b, P[ch], pp_b);
+        w.taps = tg.flipped;
+        w.border = IMCL_BORDER_CONSTANT;
+        w.border_value = 0.0;
+        IMCL_TRY(conv_run(w, nullptr, s));
+        IMCL_TRY(edges_2d(P[ch], pp, S[ch], pp, gw, nullptr, 0, nullptr, W, H, wk, wk, f.taps_mem, s));
+    }
+    // through the products: gIx -> S0, gIy -> S1
+    k_harris_gi<<<eg, 256, 0, s>>>(IX, IY, P[0], P[1], P[2], S[0], S[1], pp, W, H);
+    IMCL_TRY(cuda_fail(cudaGetLastError(), "harris dIx dIy"));
+    if (b.dx) {   // Sobel adjoints, summed, then the folded edges of both
+        TapSet tx, ty;
+        IMCL_TRY(make_taps(sx, 9, f.taps_mem, tap_slot + 64, s, &tx));
+        IMCL_TRY(make_taps(sy, 9, f.taps_mem, tap_slot + 128, s, &ty));
+        ConvCall a = f32_call(base, S[0], pp_b, b.dx, b.dx_pitch_b);
+        a.taps = tx.flipped;
+        a.border = IMCL_BORDER_CONSTANT;
+        a.border_value = 0.0;
+        IMCL_TRY(conv_run(a, nullptr, s));
+        ConvCall a2 = f32_call(base, S[1], pp_b, TMP, pp_b);
+        a2.taps = ty.flipped;
+        a2.border = IMCL_BORDER_CONSTANT;
+        a2.border_value = 0.0;
+        IMCL_TRY(conv_run(a2, nullptr, s));
+        k_add_plane<<<eg, 256, 0, s>>>(b.dx, b.dx_pitch_b / 4, TMP, pp, W, H);
+        IMCL_TRY(cuda_fail(cudaGetLastError(), "harris dI sum"));
+        IMCL_TRY(edges_2d(b.dx, b.dx_pitch_b / 4, S[0], pp, sx, S[1], pp, sy, W, H, 3, 3, f.taps_mem, s));
+    }
+    if (b.dw0) {
+        IMCL_TRY(wgrad_partials<float>(S[0], pp, static_cast<const float*>(f.in), f.in_pitch_b / 4, W, H, 3, 3,
+                                       IMCL_BORDER_CLAMP, 0.f, partials, s));
+        IMCL_TRY(finalize(partials, grid, 9, b.dw0, s));
+    }
+    if (b.dw1) {
+        IMCL_TRY(wgrad_partials<float>(S[1], pp, static_cast<const float*>(f.in), f.in_pitch_b / 4, W, H, 3, 3,
+                                       IMCL_BORDER_CLAMP, 0.f, partials, s));
+        IMCL_TRY(finalize(partials, grid, 9, b.dw1, s));
+    }
+    return IMCL_OK;
+}
+
+}  // namespace imcl

@@ -1,0 +1,240 @@
+// backward_kernels.cuh -- building blocks of the adjoint (backward) passes.
+//
+// A forward correlation with the clamped rule reads in(clamp(p + o)).  Write it as a
+// correlation on the image extended by clamping, E in.  Its adjoint applied to an
+// upstream gradient g is then
+//     dx = E^T ( corr(g0, flip(w)) on the extended domain ),
+// g0 being g with zeros outside the image and flip(w)[m] = w[K-1-m].  Inside the image
+// (away from the first and last row and column) E^T is the identity, so the bulk of dx
+// is a correlation of g with the flipped taps under a zero border: the forward kernels
+// compute it.  E^T sums every extended position onto the pixel it clamps to, which only
+// touches the first and last rows and columns; the edge kernels below recompute those
+// pixels with the folded sums.  Under the constant rule outside reads carry no input,
+// so the zero-border correlation is the whole input gradient.
+//
+// The tap gradient dw[o] = sum_p g(p) in_b(p + o) is reduced in two fixed-order stages
+// (per-CTA partials over a static tile assignment, then a tree per tap), so results are
+// deterministic run to run.
+#pragma once
+
+#include "tile_common.cuh"
+
+namespace imcl {
+
+constexpr int kWgTileW = 64, kWgTileH = 32;   // tile of the tap-gradient reduction
+constexpr int kWgMaxParts = 1024;             // CTAs (partial sums per tap) at most
+constexpr int kMaxAdjTaps = 33 * 33;
+
+struct AdjTaps {                  // taps of up to two channels for the edge kernels
+    float w1[kMaxK * kMaxK];
+    float w2[kMaxK * kMaxK];
+};
+
+__device__ __forceinline__ float g0_at(const float* g, long long pitch, int x, int y, int W, int H) {
+    return (x >= 0 && x < W && y >= 0 && y < H) ? g[(long long)y * pitch + x] : 0.f;
+}
+
+// Recompute dx at every pixel of the first/last row and column: the folded adjoint of
+// one or two clamped correlations (kw x kh taps each, kw, kh <= 15).  Overwrites.
+__global__ void __launch_bounds__(256)
+    k_adjoint_edges_2d(float* dx, long long dx_pitch, const float* g1, long long g1_pitch, const float* g2,
+                       long long g2_pitch, int W, int H, int kw, int kh, const float* w1_dev, const float* w2_dev,
+                       const __grid_constant__ AdjTaps tp) {
+    const int ntop = W, nside = H > 2 ? H - 2 : 0;
+    const int nedge = (H > 1 ? 2 * ntop : ntop) + (W > 1 ? 2 * nside : nside);
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nedge) return;
+    int qx, qy;
+    const int rows = H > 1 ? 2 * ntop : ntop;
+    if (e < rows) {
+        qx = e % W;
+        qy = e < ntop ? 0 : H - 1;
+    } else {
+        const int k = e - rows;
+        qy = 1 + (k % nside);
+        qx = k < nside ? 0 : W - 1;
+    }
+    const int rx = (kw - 1) / 2, ry = (kh - 1) / 2;
+    const int xlo = qx == 0 ? -rx : qx, xhi = qx == W - 1 ? W - 1 + rx : qx;
+    const int ylo = qy == 0 ? -ry : qy, yhi = qy == H - 1 ? H - 1 + ry : qy;
+    const float* w1 = w1_dev ? w1_dev : tp.w1;
+    const float* w2 = w2_dev ? w2_dev : tp.w2;
+    float acc = 0.f;
+    for (int ey = ylo; ey <= yhi; ++ey)
+        for (int ex = xlo; ex <= xhi; ++ex)
+            for (int j = 0; j < kh; ++j)
+                for (int i = 0; i < kw; ++i) {
+                    const int sx = ex - i + rx, sy = ey - j + ry;
+                    acc = __fmaf_rn(w1[j * kw + i], g0_at(g1, g1_pitch, sx, sy, W, H), acc);
+                    if (g2) acc = __fmaf_rn(w2[j * kw + i], g0_at(g2, g2_pitch, sx, sy, W, H), acc);
+                }
+    dx[(long long)qy * dx_pitch + qx] = acc;
+}
+
+// Add the folded contributions of a clamped 1D correlation along one axis (axis 0: x,
+// axis 1: y) to the first and last column / row of dst (dst already holds the
+// zero-border adjoint).  n taps, n <= 33.
+__global__ void __launch_bounds__(256)
+    k_fold_1d(float* dst, long long dst_pitch, const float* g, long long g_pitch, int W, int H, int n, int axis,
+              const float* w_dev, const __grid_constant__ TapsParam<float, 33> tp) {
+    const int L = axis == 0 ? W : H;        // length along the folded axis
+    const int M = axis == 0 ? H : W;        // lines to treat
+    const int line = blockIdx.x * blockDim.x + threadIdx.x;
+    if (line >= M) return;
+    const float* w = w_dev ? w_dev : tp.w;
+    const int r = (n - 1) / 2;
+    auto gat = [&](int along) -> float {
+        if (along < 0 || along >= L) return 0.f;
+        return axis == 0 ? g[(long long)line * g_pitch + along] : g[(long long)along * g_pitch + line];
+    };
+    float lo = 0.f, hi = 0.f;
+    for (int e = -r; e <= -1; ++e)
+        for (int j = 0; j < n; ++j) lo = __fmaf_rn(w[j], gat(e - j + r), lo);
+    for (int e = L; e <= L - 1 + r; ++e)
+        for (int j = 0; j < n; ++j) hi = __fmaf_rn(w[j], gat(e - j + r), hi);
+    float* d0 = axis == 0 ? dst + (long long)line * dst_pitch : dst + line;
+    const long long step = axis == 0 ? 1 : dst_pitch;
+    if (L == 1) {
+        d0[0] += lo + hi;
+    } else {
+        d0[0] += lo;
+        d0[(long long)(L - 1) * step] += hi;
+    }
+}
+
+// Per-CTA partial sums of dw[j][i] = sum_p g(p) x_b(p + (i - rx, j - ry)) (kw, kh <= 33,
+// kw*kh <= 1089) over the CTA's tiles (static assignment t = blockIdx.x + k gridDim.x).
+// partials[blockIdx.x * kw*kh + tap].
+template <typename Tx>
+__global__ void __launch_bounds__(256)
+    k_wgrad_partial(const float* g, long long g_pitch, const Tx* x, long long x_pitch, int W, int H, int kw, int kh,
+                    int border, float bv, float* partials) {
+    extern __shared__ __align__(16) float wsm[];
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int rx = (kw - 1) / 2, ry = (kh - 1) / 2;
+    const int XW = kWgTileW + kw - 1, XH = kWgTileH + kh - 1;
+    float* gs = wsm;                                  // kWgTileH x kWgTileW
+    float* xs = gs + kWgTileW * kWgTileH;             // XH x XW
+    float* red = xs + XW * XH;                        // reduction scratch, nth * 4
+    const int cw = (kw + 3) / 4;                      // groups of 4 taps per tap row
+    const int ngroups = kh * cw;
+    const int reps = nth / ngroups > 0 ? nth / ngroups : 1;
+    const int gi = tid % ngroups, rep = tid / ngroups;
+    const bool active = rep < reps && tid < ngroups * reps;
+    const int j = gi / cw, i0 = (gi % cw) * 4;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const int tiles_x = (W + kWgTileW - 1) / kWgTileW, tiles_y = (H + kWgTileH - 1) / kWgTileH;
+    const Tx bvt = Store<Tx, float>::cvt(bv);
+    for (int t = blockIdx.x; t < tiles_x * tiles_y; t += gridDim.x) {
+        const int x0 = (t % tiles_x) * kWgTileW, y0 = (t / tiles_x) * kWgTileH;
+        __syncthreads();
+        for (int k = tid; k < kWgTileW * kWgTileH; k += nth) {
+            const int r = k / kWgTileW, c = k % kWgTileW;
+            gs[k] = (x0 + c < W && y0 + r < H) ? g[(long long)(y0 + r) * g_pitch + x0 + c] : 0.f;
+        }
+        for (int k = tid; k < XW * XH; k += nth) {
+            const int r = k / XW, c = k % XW;
+            const int gx = x0 - rx + c, gy = y0 - ry + r;
+            float v;
+            if (gx >= 0 && gx < W && gy >= 0 && gy < H) v = to_acc(x[(long long)gy * x_pitch + gx]);
+            else if (border == IMCL_BORDER_CONSTANT) v = to_acc(bvt);
+            else v = to_acc(x[(long long)clampi(gy, 0, H - 1) * x_pitch + clampi(gx, 0, W - 1)]);
+            xs[k] = v;
+        }
+        __syncthreads();
+        if (active) {
+            for (int py = rep; py < kWgTileH; py += reps) {
+                const float* xr = xs + (py + j) * XW + i0;
+                const float* gr = gs + py * kWgTileW;
+#pragma unroll 4
+                for (int px = 0; px < kWgTileW; ++px) {
+                    const float gv = gr[px];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (i0 + k < kw) acc[k] = __fmaf_rn(gv, xr[px + k], acc[k]);
+                }
+            }
+        }
+    }
+    // combine the replicas of each tap group in a fixed order
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) red[tid * 4 + k] = acc[k];
+    __syncthreads();
+    for (int q = tid; q < kw * kh; q += nth) {
+        const int jj = q / kw, ii = q % kw;
+        const int grp = jj * cw + ii / 4, lane = ii % 4;
+        float s = 0.f;
+        for (int r = 0; r < reps; ++r) s += red[(r * ngroups + grp) * 4 + lane];
+        partials[(long long)blockIdx.x * kw * kh + q] = s;
+    }
+}
+
+// out[tap] = (accumulate ? out[tap] : 0) + sum over nparts partial sums, as a fixed tree.
+__global__ void __launch_bounds__(256)
+    k_wgrad_finalize(const float* partials, int nparts, int ntaps, float* out, int accumulate) {
+    __shared__ float sh[256];
+    const int tap = blockIdx.x, tid = threadIdx.x;
+    float s = 0.f;
+    for (int p = tid; p < nparts; p += 256) s += partials[(long long)p * ntaps + tap];
+    sh[tid] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (tid < w) sh[tid] += sh[tid + w];
+        __syncthreads();
+    }
+    if (tid == 0) out[tap] = accumulate ? out[tap] + sh[0] : sh[0];
+}
+
+// flipped copies of device taps (and a single 1.0 tap) into dst
+__global__ void k_flip_taps(const float* src, int kw, int kh, float* dst, float* one) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < kw * kh) dst[k] = src[kw * kh - 1 - k];
+    if (k == 0 && one) *one = 1.f;
+}
+
+// ------------------------------------------------------------------ Harris elementwise steps
+// products of the gradients: P = (Ix^2, Iy^2, Ix Iy), planes of pitch `pitch`
+__global__ void k_harris_products(const float* ix, const float* iy, float* p0, float* p1, float* p2, long long pitch,
+                                  int W, int H) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= W || y >= H) return;
+    const long long o = (long long)y * pitch + x;
+    const float a = ix[o], b = iy[o];
+    p0[o] = a * a;
+    p1[o] = b * b;
+    p2[o] = a * b;
+}
+
+// dR/dS: gSxx = gR (Syy - 2k tr), gSyy = gR (Sxx - 2k tr), gSxy = -2 gR Sxy (in place)
+__global__ void k_harris_gs(const float* gR, long long gR_pitch, float* s0, float* s1, float* s2, long long pitch,
+                            int W, int H, float k) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= W || y >= H) return;
+    const long long o = (long long)y * pitch + x;
+    const float g = gR[(long long)y * gR_pitch + x];
+    const float sxx = s0[o], syy = s1[o], sxy = s2[o], tr = sxx + syy;
+    s0[o] = g * (syy - 2.f * k * tr);
+    s1[o] = g * (sxx - 2.f * k * tr);
+    s2[o] = -2.f * g * sxy;
+}
+
+// chain rule through the products: gIx = 2 Ix gPxx + Iy gPxy, gIy = 2 Iy gPyy + Ix gPxy
+__global__ void k_harris_gi(const float* ix, const float* iy, const float* gp0, const float* gp1, const float* gp2,
+                            float* gix, float* giy, long long pitch, int W, int H) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= W || y >= H) return;
+    const long long o = (long long)y * pitch + x;
+    const float a = ix[o], b = iy[o], pxx = gp0[o], pyy = gp1[o], pxy = gp2[o];
+    gix[o] = __fmaf_rn(2.f * a, pxx, b * pxy);
+    giy[o] = __fmaf_rn(2.f * b, pyy, a * pxy);
+}
+
+// dst += src (planes)
+__global__ void k_add_plane(float* dst, long long dst_pitch, const float* src, long long src_pitch, int W, int H) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= W || y >= H) return;
+    dst[(long long)y * dst_pitch + x] += src[(long long)y * src_pitch + x];
+}
+
+}  // namespace imcl

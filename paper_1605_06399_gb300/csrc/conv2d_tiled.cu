@@ -28,6 +28,7 @@ template <typename Tin, typename Tout>
 static void add_16bit(std::vector<ConvEntry>& t) {
     t.push_back(conv_entry<Tin, Tout, K, 4, 4, TMA, PARAM, BLK>(32, 8, 1));
     t.push_back(conv_entry<Tin, Tout, K, 4, 4, TMA, SFILT, BLK>(32, 8, 1));
+    t.push_back(conv_entry<Tin, Tout, K, 4, 4, GLB, SFILT, BLK>(32, 8, 0));
     if constexpr (K <= 7) {
         t.push_back(conv_entry<Tin, Tout, K, 4, 8, TMA, PARAM, BLK>(32, 4, 1));
         t.push_back(conv_entry<Tin, Tout, K, 4, 4, GLB, PARAM, BLK>(32, 8, 0));
@@ -40,6 +41,7 @@ void IMCL_REG_NAME(std::vector<ConvEntry>& t) {
     t.push_back(conv_entry<float, float, K, 4, 8, TMA, PARAM, BLK>(32, 4, 1));
     t.push_back(conv_entry<float, float, K, 4, 4, TMA, SFILT, BLK>(32, 8, 1));
     t.push_back(conv_entry<float, float, K, 4, 4, GLB, PARAM, BLK>(32, 8, 0));
+    t.push_back(conv_entry<float, float, K, 4, 4, GLB, SFILT, BLK>(32, 8, 0));
     if constexpr (kFullSpace) {
         t.push_back(conv_entry<float, float, K, 4, 2, TMA, PARAM, BLK>(32, 8, 1));
         t.push_back(conv_entry<float, float, K, 8, 2, TMA, PARAM, BLK>(16, 8, 1));

@@ -41,9 +41,11 @@ const std::vector<ConvEntry>& harris_table() {
         t->push_back(harris_entry<5, 2, SMEM, PARAM>(16, 16, 0));
         t->push_back(harris_entry<5, 2, TMA, SFILT>(16, 16, 1));
         t->push_back(harris_entry<5, 4, TMA, SFILT>(16, 8, 1));
+        t->push_back(harris_entry<5, 2, SMEM, SFILT>(16, 16, 0));
         t->push_back(harris_entry<3, 2, TMA, PARAM>(16, 16, 1));
         t->push_back(harris_entry<3, 2, TMA, SFILT>(16, 16, 1));
         t->push_back(harris_entry<3, 2, SMEM, PARAM>(16, 16, 0));
+        t->push_back(harris_entry<3, 2, SMEM, SFILT>(16, 16, 0));
         return t;
     }();
     return *table;

@@ -24,16 +24,25 @@ static void add_radius(std::vector<ConvEntry>& t) {
     t.push_back(sep_entry<float, float, R, 4, 8, SMEM, PARAM>(32, 8, 0));
     t.push_back(sep_entry<float, float, R, 4, 8, GLB, PARAM>(32, 8, 0));
     t.push_back(sep_entry<float, float, R, 4, 8, TMA, SFILT>(32, 8, 1));
+    t.push_back(sep_entry<float, float, R, 4, 8, GLB, SFILT>(32, 8, 0));
 #elif IMCL_SEP_GROUP == 1
     t.push_back(sep_entry<__half, float, R, 4, 8, TMA, PARAM>(32, 8, 1));
     t.push_back(sep_entry<__half, float, R, 4, 8, TMA, SFILT>(32, 8, 1));
+    t.push_back(sep_entry<__half, float, R, 4, 8, GLB, PARAM>(32, 8, 0));
+    t.push_back(sep_entry<__half, float, R, 4, 8, GLB, SFILT>(32, 8, 0));
     t.push_back(sep_entry<__half, __half, R, 4, 8, TMA, PARAM>(32, 8, 1));
     t.push_back(sep_entry<__half, __half, R, 4, 8, TMA, SFILT>(32, 8, 1));
+    t.push_back(sep_entry<__half, __half, R, 4, 8, GLB, PARAM>(32, 8, 0));
+    t.push_back(sep_entry<__half, __half, R, 4, 8, GLB, SFILT>(32, 8, 0));
 #else
     t.push_back(sep_entry<__nv_bfloat16, float, R, 4, 8, TMA, PARAM>(32, 8, 1));
     t.push_back(sep_entry<__nv_bfloat16, float, R, 4, 8, TMA, SFILT>(32, 8, 1));
+    t.push_back(sep_entry<__nv_bfloat16, float, R, 4, 8, GLB, PARAM>(32, 8, 0));
+    t.push_back(sep_entry<__nv_bfloat16, float, R, 4, 8, GLB, SFILT>(32, 8, 0));
     t.push_back(sep_entry<__nv_bfloat16, __nv_bfloat16, R, 4, 8, TMA, PARAM>(32, 8, 1));
     t.push_back(sep_entry<__nv_bfloat16, __nv_bfloat16, R, 4, 8, TMA, SFILT>(32, 8, 1));
+    t.push_back(sep_entry<__nv_bfloat16, __nv_bfloat16, R, 4, 8, GLB, PARAM>(32, 8, 0));
+    t.push_back(sep_entry<__nv_bfloat16, __nv_bfloat16, R, 4, 8, GLB, SFILT>(32, 8, 0));
 #endif
 }
 

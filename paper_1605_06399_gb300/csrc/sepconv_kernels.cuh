@@ -260,7 +260,8 @@ imcl_status launch_sep_fused(const ConvCall& c, const imcl_variant& v, cudaStrea
     if (bx <= 0 || by <= 0 || nth > 256 || nth % 32 != 0)
         return fail(IMCL_ERR_UNSUPPORTED, "fused sepconv: bx*by must be a multiple of 32, at most 256");
     if ((bx * PX) % G::CV != 0) return fail(IMCL_ERR_UNSUPPORTED, "fused sepconv: bx*px must be a multiple of 16 bytes");
-    if (std::max(c.kw, c.kh) != NT) return fail(IMCL_ERR_UNSUPPORTED, "fused sepconv: radius mismatch");
+    if (std::max(1, (std::max(c.kw, c.kh) - 1) / 2) != R)
+        return fail(IMCL_ERR_UNSUPPORTED, "fused sepconv: radius mismatch");
     if (c.taps_mem == IMCL_MEM_DEVICE && FILT != IMCL_FILT_SMEM)
         return fail(IMCL_ERR_UNSUPPORTED, "device-resident taps need a FILT_SMEM variant");
     const int TW = bx * PX, TH = by * PY;

@@ -7,21 +7,8 @@
 
 namespace imcl {
 
-// A ConvCall describing `p` on hypothetical, fully aligned buffers.
 static ConvCall conv_call_for(const imcl_problem& p, const DeviceInfo* dev) {
-    ConvCall c;
-    c.in = reinterpret_cast<const void*>(uintptr_t(256));
-    c.out = reinterpret_cast<void*>(uintptr_t(512));
-    c.in_dtype = p.in_dtype;
-    c.out_dtype = p.out_dtype;
-    c.W = p.width;
-    c.H = p.height;
-    c.in_pitch_b = ((int64_t)p.width * dtype_size(p.in_dtype) + 127) / 128 * 128;
-    c.out_pitch_b = ((int64_t)p.width * dtype_size(p.out_dtype) + 127) / 128 * 128;
-    c.kw = p.kw;
-    c.kh = p.kh;
-    c.taps_mem = p.taps_mem;
-    c.border = p.border;
+    ConvCall c = problem_call(p);
     c.dev = dev;
     c.status = dev ? dev->status : nullptr;
     return c;

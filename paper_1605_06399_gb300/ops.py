@@ -118,7 +118,9 @@ def sepconv(x: torch.Tensor, row_taps, col_taps=None, border: str = "clamp",
     y = _out_like(x, out, out_dtype, False)
     xi, yi = image(x), image(y)
     vptr = _variant(variant)
-    need = lib().imagecl_sepconv_workspace_size(x.size(1), x.size(0), vptr)
+    prob = problem(_abi.OP_SEPCONV, x.dtype, y.dtype, rt.shape[0], ct.shape[0], x.size(1), x.size(0), border,
+                   rt.mem)
+    need = lib().imagecl_sepconv_workspace_size(ctypes.byref(prob), vptr)
     ws_ptr, ws_bytes = None, 0
     if need:
         if workspace is None:
@@ -147,7 +149,9 @@ def harris(x: torch.Tensor, sobel_x, sobel_y, window, k: float = 0.04, out=None,
     y = out if out is not None else torch.empty_like(x)
     xi, yi = image(x), image(y)
     vptr = _variant(variant)
-    need = lib().imagecl_harris_workspace_size(x.size(1), x.size(0), vptr)
+    prob = problem(_abi.OP_HARRIS, torch.float32, torch.float32, win.shape[0], win.shape[0], x.size(1),
+                   x.size(0), "clamp", sx.mem)
+    need = lib().imagecl_harris_workspace_size(ctypes.byref(prob), vptr)
     ws_ptr, ws_bytes = None, 0
     if need:
         if workspace is None:
@@ -158,6 +162,79 @@ def harris(x: torch.Tensor, sobel_x, sobel_y, window, k: float = 0.04, out=None,
                                float(k), sx.mem, vptr, ctypes.c_void_p(ws_ptr), ws_bytes,
                                ctypes.c_void_p(stream_handle(stream))))
     return y
+
+
+def _grad_buffers(x, need_dx):
+    dx = torch.empty(x.shape, dtype=torch.float32, device=x.device) if need_dx else None
+    return dx, (ctypes.byref(image(dx)) if dx is not None else None)
+
+
+def _ws(nbytes, device):
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+def _f32_grad(g):
+    return g.detach().to(torch.float32).contiguous()
+
+
+def conv2d_backward(g, x, taps, border="clamp", border_value=0.0, need_dx=True, need_dw=True,
+                    stream=None):
+    """(dx, dtaps) of ``conv2d(x, taps)`` for the upstream gradient ``g`` (f32 results;
+    None for what is not requested)."""
+    g = _f32_grad(g)
+    tp = Taps(taps, False)
+    kh, kw = tp.shape
+    dx, dx_ref = _grad_buffers(x, need_dx)
+    dw = torch.empty((kh, kw), dtype=torch.float32, device=x.device) if need_dw else None
+    ws = _ws(lib().imagecl_conv2d_backward_workspace_size(x.size(1), x.size(0), kw, kh), x.device)
+    gi, xi = image(g), image(x)
+    check(lib().imagecl_conv2d_backward(ctypes.byref(gi), ctypes.byref(xi), ctypes.c_void_p(tp.ptr), kw, kh,
+                                        tp.mem, BORDERS[border], float(border_value), dx_ref,
+                                        ctypes.c_void_p(dw.data_ptr() if dw is not None else None),
+                                        ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                        ctypes.c_void_p(stream_handle(stream))))
+    return dx, dw
+
+
+def sepconv_backward(g, x, row_taps, col_taps=None, border="clamp", border_value=0.0, need_dx=True,
+                     need_drow=True, need_dcol=True, stream=None):
+    """(dx, drow, dcol) of ``sepconv(x, row_taps, col_taps)`` for the upstream ``g``."""
+    g = _f32_grad(g)
+    rt = Taps(row_taps, False, ndim=1)
+    ct = Taps(row_taps if col_taps is None else col_taps, False, ndim=1)
+    nr, nc = rt.shape[0], ct.shape[0]
+    dx, dx_ref = _grad_buffers(x, need_dx)
+    drow = torch.empty(nr, dtype=torch.float32, device=x.device) if need_drow else None
+    dcol = torch.empty(nc, dtype=torch.float32, device=x.device) if need_dcol else None
+    ws = _ws(lib().imagecl_sepconv_backward_workspace_size(x.size(1), x.size(0), nr, nc), x.device)
+    gi, xi = image(g), image(x)
+    check(lib().imagecl_sepconv_backward(ctypes.byref(gi), ctypes.byref(xi), ctypes.c_void_p(rt.ptr), nr,
+                                         ctypes.c_void_p(ct.ptr), nc, rt.mem, BORDERS[border],
+                                         float(border_value), dx_ref,
+                                         ctypes.c_void_p(drow.data_ptr() if drow is not None else None),
+                                         ctypes.c_void_p(dcol.data_ptr() if dcol is not None else None),
+                                         ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                         ctypes.c_void_p(stream_handle(stream))))
+    return dx, drow, dcol
+
+
+def harris_backward(g, x, sobel_x, sobel_y, window, k=0.04, need_dx=True, need_taps=True, stream=None):
+    """(dI, dsobel_x, dsobel_y, dwindow) of ``harris`` for the upstream gradient ``g``."""
+    g = _f32_grad(g)
+    sx, sy, win = Taps(sobel_x, False), Taps(sobel_y, False), Taps(window, False)
+    wk = win.shape[0]
+    dx, dx_ref = _grad_buffers(x, need_dx)
+    mk = (lambda shape: torch.empty(shape, dtype=torch.float32, device=x.device) if need_taps else None)
+    dsx, dsy, dwin = mk((3, 3)), mk((3, 3)), mk((wk, wk))
+    ws = _ws(lib().imagecl_harris_backward_workspace_size(x.size(1), x.size(0), wk), x.device)
+    gi, xi = image(g), image(x)
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr() if t is not None else None)
+    check(lib().imagecl_harris_backward(ctypes.byref(gi), ctypes.byref(xi), ctypes.c_void_p(sx.ptr),
+                                        ctypes.c_void_p(sy.ptr), ctypes.c_void_p(win.ptr), wk, float(k),
+                                        sx.mem, dx_ref, ptr(dsx), ptr(dsy), ptr(dwin),
+                                        ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                        ctypes.c_void_p(stream_handle(stream))))
+    return dx, dsx, dsy, dwin
 
 
 def problem(op: int, in_dtype, out_dtype, kw: int, kh: int, width: int, height: int,

@@ -37,7 +37,7 @@ def _variants_for(in_t, out_t, k, h, w, taps_mem, border):
         if v["kind"] == _abi.KIND_TILED and v["load"] == _abi.LOAD_TMA and v["py"] == 4:
             for bx, by in EXTRA_SHAPES:
                 extra.append(dict(v, bx=bx, by=by))
-    return vs + extra
+    return [None] + vs + extra
 
 
 def _run_all(x_cpu, taps, out_dtype, border, bv, taps_mem, layout):
@@ -73,7 +73,7 @@ def test_conv2d_every_variant_matches_oracle(dt, out_dtype, k):
         for border, bv in (("clamp", 0.0), ("constant", 3.0 if dt == "u8" else 0.375)):
             ref, s = conv_reference(x, taps, border, bv)
             for mem, layout in ((_abi.MEM_HOST, "dense"), (_abi.MEM_HOST, "padded"),
-                                (_abi.MEM_DEVICE, "padded")):
+                                (_abi.MEM_DEVICE, "padded"), (_abi.MEM_DEVICE, "dense")):
                 for v, y in _run_all(x, taps, out_dtype, border, bv, mem, layout):
                     what = f"{dt}->{out_dtype} k={k} {h}x{w} {border} mem={mem} {layout} {v}"
                     if dt == "u8":

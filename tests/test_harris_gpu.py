@@ -25,7 +25,7 @@ def _variants(wk, w, h, mem):
     vs = ops.variants(prob)
     extra = [dict(v, bx=bx, by=by) for v in vs if v["kind"] == _abi.KIND_TILED and v["load"] == _abi.LOAD_TMA
              for bx, by in ((32, 8), (8, 32), (16, 8))]
-    return vs + extra
+    return [None] + vs + extra
 
 
 @pytest.mark.parametrize("wk", [1, 3, 5, 7])
@@ -39,7 +39,8 @@ def test_harris_every_variant_matches_oracle(wk):
         img = synth.rectangles_image(g, h, w, n_rect=12, side_lo=2, side_hi=max(3, min(h, w)))
         R64, sc = harris_reference(img, sx, sy, win)
         x = torch.from_numpy(img)
-        for mem, layout in ((_abi.MEM_HOST, "dense"), (_abi.MEM_HOST, "padded"), (_abi.MEM_DEVICE, "padded")):
+        for mem, layout in ((_abi.MEM_HOST, "dense"), (_abi.MEM_HOST, "padded"), (_abi.MEM_DEVICE, "padded"),
+                            (_abi.MEM_DEVICE, "dense")):
             xd = place(x, layout)
             taps = [torch.from_numpy(np.ascontiguousarray(t)).cuda() if mem == _abi.MEM_DEVICE else t
                     for t in (sx, sy, win)]

@@ -27,7 +27,7 @@ def _all_variants(dt, out_dtype, nr, nc, w, h, mem):
     vs = ops.variants(prob)
     extra = [dict(v, bx=bx, by=by) for v in vs if v["kind"] == _abi.KIND_TILED and v["load"] == _abi.LOAD_TMA
              for bx, by in ((16, 8), (8, 16), (32, 4))]
-    return vs + extra
+    return [None] + vs + extra
 
 
 @pytest.mark.parametrize("radius", list(range(1, 17)))
@@ -42,7 +42,7 @@ def test_sepconv_every_variant_matches_oracle(dt, out_dtype, radius):
         for border, bv in (("clamp", 0.0), ("constant", 0.375)):
             ref, s = sep_reference(x, row, col, border, bv)
             for mem, layout in ((_abi.MEM_HOST, "dense"), (_abi.MEM_HOST, "padded"),
-                                (_abi.MEM_DEVICE, "padded")):
+                                (_abi.MEM_DEVICE, "padded"), (_abi.MEM_DEVICE, "dense")):
                 xd = place(x, layout)
                 r_arg = torch.from_numpy(row).cuda() if mem == _abi.MEM_DEVICE else row
                 c_arg = torch.from_numpy(col).cuda() if mem == _abi.MEM_DEVICE else col
@@ -60,7 +60,7 @@ def test_sepconv_every_variant_matches_oracle(dt, out_dtype, radius):
     assert n > 0
 
 
-@pytest.mark.parametrize("nr,nc", [(5, 9), (9, 5), (1, 33), (33, 1), (3, 1)])
+@pytest.mark.parametrize("nr,nc", [(5, 9), (9, 5), (1, 33), (33, 1), (3, 1), (1, 1)])
 def test_unequal_tap_counts(nr, nc):
     g = np.random.default_rng(nr * 100 + nc)
     x = synth.to_storage(synth.uniform_f32(g, 77, 140), "f32")
