@@ -211,6 +211,52 @@ imcl_status imagecl_harris_backward(const imcl_image *grad_out, const imcl_image
                                     size_t workspace_bytes, void *stream);
 size_t imagecl_harris_backward_workspace_size(int32_t width, int32_t height, int32_t wk);
 
+/* ------------------------------------------------------------------ ragged batch */
+
+/*
+ * A batch of independent image operations of uneven sizes (each image with its own
+ * conv2d filter or separable pair) run by one persistent kernel: every tile of every
+ * image goes into one work list, costliest first, that a grid of resident CTAs drains
+ * with an atomic counter.  imagecl_batch_create validates the items, times a few tile
+ * shapes on the whole batch (up to tune_budget_s) and keeps the fastest, and records the
+ * launch in a CUDA graph; imagecl_batch_run replays it.  The plan stores the pointers it
+ * was given: keep every buffer alive and in place while the handle lives, and change
+ * pixel or tap values in place between runs as you like.
+ * Per item: in f32/f16/bf16, out f32 or the input's type, same size, no overlap; conv2d
+ * sides / separable tap counts odd, at most 15; taps are DEVICE f32 arrays.  The
+ * gradient fields are used by imagecl_batch_backward (NULL data / pointers: skipped).
+ */
+typedef struct {
+    int32_t op;            /* IMCL_OP_CONV2D or IMCL_OP_SEPCONV                              */
+    int32_t border;        /* imcl_border                                                    */
+    int32_t kw, kh;        /* conv2d: filter sides; sepconv: row / column tap counts         */
+    double border_value;
+    imcl_image in, out;
+    const float *taps;     /* conv2d: kw*kh taps; sepconv: row taps (device)                 */
+    const float *taps2;    /* sepconv: column taps (device); NULL for conv2d                 */
+    imcl_image grad_out;   /* f32 upstream gradient (for imagecl_batch_backward)              */
+    imcl_image grad_in;    /* f32 input gradient, written by imagecl_batch_backward           */
+    float *grad_taps;      /* conv2d taps / sepconv row taps gradient (device), written       */
+    float *grad_taps2;     /* sepconv column taps gradient (device), written                  */
+} imcl_batch_item;
+
+typedef struct imcl_batch imcl_batch;   /* opaque plan */
+
+typedef struct {
+    int32_t images, tiles, tile_w, tile_h;
+    double pixels;             /* output pixels of one forward run                        */
+    double fwd_ms_at_create;   /* forward time of the chosen shape when it was tuned      */
+    double shape_ms[4];        /* forward time of each tile shape tried (0: not tried)    */
+    int32_t has_backward;
+} imcl_batch_info_t;
+
+imcl_status imagecl_batch_create(const imcl_batch_item *items, int32_t n, double tune_budget_s,
+                                 imcl_batch **out);
+/* Forward over the whole batch: one graph launch on `stream`. */
+imcl_status imagecl_batch_run(imcl_batch *batch, void *stream);
+imcl_status imagecl_batch_info(const imcl_batch *batch, imcl_batch_info_t *info);
+void imagecl_batch_destroy(imcl_batch *batch);
+
 /*
  * imagecl_sepconv_noalloc -- the separable correlation for callers that may not
  * allocate device memory.  The paper has no counterpart; this entry point exists for

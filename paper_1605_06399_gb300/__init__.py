@@ -8,8 +8,8 @@ from .ops import (conv2d, sepconv, harris, default_variant, device_status, image
                   tune_load, tune_save, tune_set, variants, version)
 from ._abi import ImclError
 from . import autograd
-from .ops import conv2d_backward, harris_backward, sepconv_backward
+from .ops import Batch, conv2d_backward, harris_backward, sepconv_backward
 
 __all__ = ["conv2d", "sepconv", "harris", "default_variant", "device_status", "image", "problem", "tune", "tune_clear",
            "tune_load", "tune_save", "tune_set", "variants", "version", "ImclError", "autograd", "conv2d_backward",
-           "sepconv_backward", "harris_backward"]
+           "sepconv_backward", "harris_backward", "Batch"]

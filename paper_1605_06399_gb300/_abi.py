@@ -63,6 +63,19 @@ class Problem(ctypes.Structure):
     _fields_ = [(n, c_int32) for n in PROBLEM_FIELDS]
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("op", c_int32), ("border", c_int32), ("kw", c_int32), ("kh", c_int32),
+                ("border_value", c_double), ("in_", Image), ("out", Image), ("taps", c_void_p),
+                ("taps2", c_void_p), ("grad_out", Image), ("grad_in", Image), ("grad_taps", c_void_p),
+                ("grad_taps2", c_void_p)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("images", c_int32), ("tiles", c_int32), ("tile_w", c_int32), ("tile_h", c_int32),
+                ("pixels", c_double), ("fwd_ms_at_create", c_double), ("shape_ms", c_double * 4),
+                ("has_backward", c_int32)]
+
+
 class ImclError(RuntimeError):
     def __init__(self, status: int, message: str):
         self.status = status
@@ -96,6 +109,10 @@ SIGNATURES = {
                                           ctypes.c_float, c_int32, P(Image), c_void_p, c_void_p,
                                           c_void_p, c_void_p, ctypes.c_size_t, c_void_p]),
     "imagecl_harris_backward_workspace_size": (ctypes.c_size_t, [c_int32, c_int32, c_int32]),
+    "imagecl_batch_create": (c_int32, [P(BatchItem), c_int32, c_double, P(c_void_p)]),
+    "imagecl_batch_run": (c_int32, [c_void_p, c_void_p]),
+    "imagecl_batch_info": (c_int32, [c_void_p, P(BatchInfo)]),
+    "imagecl_batch_destroy": (None, [c_void_p]),
     "imagecl_variant_count": (c_int32, [P(Problem)]),
     "imagecl_variant_get": (c_int32, [P(Problem), c_int32, P(Variant)]),
     "imagecl_variant_default": (c_int32, [P(Problem), P(Variant)]),

@@ -302,3 +302,86 @@ def device_status(stream=None) -> int:
 
 def version() -> str:
     return lib().imagecl_version().decode()
+
+
+class Batch:
+    """A ragged batch plan: one persistent, graph-replayed launch over many images.
+
+    ``items`` is a list of dicts with keys ``op`` ('conv' or 'sep'), ``x`` (CUDA tensor),
+    ``taps`` (CUDA tensor: conv (kh, kw), sep row taps), ``col_taps`` (sep, CUDA tensor),
+    optional ``out`` / ``out_dtype``, ``border``, ``border_value``, and for the backward
+    ``grad_out`` (f32 CUDA tensor).  The plan keeps references to every tensor it uses."""
+
+    def __init__(self, items, tune_budget_s: float = 2.0):
+        self.keep = []
+        arr = (_abi.BatchItem * len(items))()
+        self.outputs = []
+        self.grad_in, self.grad_taps, self.grad_taps2 = [], [], []
+        for i, it in enumerate(items):
+            x = it["x"]
+            op = _abi.OP_CONV2D if it["op"] == "conv" else _abi.OP_SEPCONV
+            taps = it["taps"].detach().to(torch.float32).contiguous()
+            col = it.get("col_taps")
+            col = col.detach().to(torch.float32).contiguous() if col is not None else None
+            if not taps.is_cuda or (col is not None and not col.is_cuda):
+                raise ValueError("batch taps must be CUDA tensors")
+            out = it.get("out")
+            if out is None:
+                od = it.get("out_dtype", x.dtype)
+                out = torch.empty(x.shape, dtype=od, device=x.device)
+            a = arr[i]
+            a.op = op
+            a.border = BORDERS[it.get("border", "clamp")]
+            if op == _abi.OP_CONV2D:
+                a.kh, a.kw = taps.shape
+            else:
+                a.kw, a.kh = taps.numel(), col.numel()
+            a.border_value = float(it.get("border_value", 0.0))
+            a.in_ = image(x)
+            a.out = image(out)
+            a.taps = taps.data_ptr()
+            a.taps2 = col.data_ptr() if col is not None else None
+            g = it.get("grad_out")
+            if g is not None:
+                g = g.detach().to(torch.float32).contiguous()
+                gi = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+                gt = torch.empty(taps.shape, dtype=torch.float32, device=x.device)
+                gt2 = torch.empty(col.shape, dtype=torch.float32, device=x.device) if col is not None else None
+                a.grad_out = image(g)
+                a.grad_in = image(gi)
+                a.grad_taps = gt.data_ptr()
+                a.grad_taps2 = gt2.data_ptr() if gt2 is not None else None
+                self.keep += [g]
+            else:
+                gi = gt = gt2 = None
+            self.grad_in.append(gi)
+            self.grad_taps.append(gt)
+            self.grad_taps2.append(gt2)
+            self.keep += [x, taps, col, out, gi, gt, gt2]
+            self.outputs.append(out)
+        h = ctypes.c_void_p()
+        check(lib().imagecl_batch_create(arr, len(items), float(tune_budget_s), ctypes.byref(h)))
+        self.handle = h
+        self._items = arr
+
+    def run(self, stream=None):
+        check(lib().imagecl_batch_run(self.handle, ctypes.c_void_p(stream_handle(stream))))
+        return self.outputs
+
+    def info(self) -> dict:
+        i = _abi.BatchInfo()
+        check(lib().imagecl_batch_info(self.handle, ctypes.byref(i)))
+        return {"images": i.images, "tiles": i.tiles, "tile": (i.tile_w, i.tile_h), "pixels": i.pixels,
+                "fwd_ms_at_create": i.fwd_ms_at_create, "shape_ms": list(i.shape_ms),
+                "has_backward": bool(i.has_backward)}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().imagecl_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
