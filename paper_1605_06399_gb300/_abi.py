@@ -111,6 +111,7 @@ SIGNATURES = {
     "imagecl_harris_backward_workspace_size": (ctypes.c_size_t, [c_int32, c_int32, c_int32]),
     "imagecl_batch_create": (c_int32, [P(BatchItem), c_int32, c_double, P(c_void_p)]),
     "imagecl_batch_run": (c_int32, [c_void_p, c_void_p]),
+    "imagecl_batch_backward": (c_int32, [c_void_p, c_void_p]),
     "imagecl_batch_info": (c_int32, [c_void_p, P(BatchInfo)]),
     "imagecl_batch_destroy": (None, [c_void_p]),
     "imagecl_variant_count": (c_int32, [P(Problem)]),

@@ -82,6 +82,125 @@ static imcl_status launch_fwd(const Batch& b, const BTile* tiles, int ntiles, in
     return cuda_fail(cudaGetLastError(), "batch forward launch");
 }
 
+static const void* bwd_kernel(int py) {
+    return py == 4 ? (const void*)k_batch_bwd<4> : (const void*)k_batch_bwd<2>;
+}
+
+size_t batch_bwd_smem_bytes(int py, int bx, int by) {
+    const size_t TW = 4 * bx, TH = (size_t)py * by, K = kBatchMaxK, R = kBatchMaxR;
+    const size_t conv_dx = (TW + 16) * (TH + K - 1) + K * K;
+    const size_t conv_wg = TW * TH + (TW + K - 1) * (TH + K - 1) + 1024;
+    const size_t HH = TH + 2 * R, XW = TW + 16;
+    const size_t sep_dt = 2 * TW * HH + XW * HH + 32 + 1024;
+    const size_t sep_dx = 2 * XW * TH + 16 + 1024;
+    return std::max(std::max(conv_dx, conv_wg), std::max(sep_dt, sep_dx)) * sizeof(float);
+}
+
+// Backward plan: gradient pointers into the image descriptors, intermediate planes and
+// partial-sum buffers, three work lists, and the graph that runs them in order.
+static imcl_status plan_backward(Batch* b) {
+    const int TW = 4 * b->bx, TH = b->py * b->by;
+    std::vector<BTile> l1, l2, l3;
+    bool any = false;
+    for (int i = 0; i < (int)b->items.size(); ++i) {
+        const imcl_batch_item& it = b->items[i];
+        BImg& im = b->himgs[i];
+        const bool has_g = it.grad_out.data != nullptr;
+        if (!has_g) continue;
+        imcl_status st;
+        if ((st = check_image(&it.grad_out, "grad_out")) != IMCL_OK) return st;
+        if (it.grad_out.dtype != IMCL_F32 || it.grad_out.width != im.W || it.grad_out.height != im.H)
+            return fail(IMCL_ERR_INVALID, "item " + std::to_string(i) + ": grad_out must be f32 of the image's size");
+        im.g = static_cast<const float*>(it.grad_out.data);
+        im.g_pitch = it.grad_out.pitch_bytes / 4;
+        if (it.grad_in.data) {
+            if ((st = check_image(&it.grad_in, "grad_in")) != IMCL_OK) return st;
+            if (it.grad_in.dtype != IMCL_F32 || it.grad_in.width != im.W || it.grad_in.height != im.H)
+                return fail(IMCL_ERR_INVALID, "item " + std::to_string(i) + ": grad_in must be f32 of the image's size");
+            im.gin = static_cast<float*>(it.grad_in.data);
+            im.gin_pitch = it.grad_in.pitch_bytes / 4;
+        }
+        im.gtaps = it.grad_taps;
+        im.gtaps2 = it.op == IMCL_OP_SEPCONV ? it.grad_taps2 : nullptr;
+        if (!im.gin && !im.gtaps && !im.gtaps2) continue;
+        any = true;
+        im.tiles_x = (im.W + TW - 1) / TW;
+        im.tiles_y = (im.H + TH - 1) / TH;
+        const int nt = im.tiles_x * im.tiles_y;
+        const size_t nparts = it.op == IMCL_OP_CONV2D ? (size_t)nt * im.kw * im.kh : (size_t)nt * (im.kw + im.kh);
+        if (im.gtaps || im.gtaps2) {
+            cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&im.part), nparts * sizeof(float));
+            if (e != cudaSuccess) return cuda_fail(e, "batch partial sums");
+            b->owned.push_back(im.part);
+        }
+        if (it.op == IMCL_OP_SEPCONV && (im.gin || im.gtaps)) {
+            im.dt_pitch = ((long long)im.W + 31) / 32 * 32;
+            cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&im.dt), (size_t)im.dt_pitch * im.H * sizeof(float));
+            if (e != cudaSuccess) return cuda_fail(e, "batch intermediate plane");
+            b->owned.push_back(im.dt);
+        }
+        for (int y = 0; y < im.H; y += TH)
+            for (int x = 0; x < im.W; x += TW) {
+                if (it.op == IMCL_OP_CONV2D) {
+                    l1.push_back(BTile{i, BT_CONV_DX, x, y});
+                } else {
+                    l1.push_back(BTile{i, BT_SEP_DT, x, y});
+                    if (im.gin || im.gtaps) l2.push_back(BTile{i, BT_SEP_DX, x, y});
+                }
+            }
+        if (it.op == IMCL_OP_CONV2D && im.gin && im.border == IMCL_BORDER_CLAMP) {
+            const int nedge = (im.H > 1 ? 2 * im.W : im.W) + (im.W > 1 ? 2 : 1) * std::max(im.H - 2, 0);
+            for (int c = 0; c * 1024 < nedge; ++c) l1.push_back(BTile{i, BT_CONV_EDGE, c, 0});
+        }
+        if (im.gtaps || im.gtaps2) l3.push_back(BTile{i, BT_FINAL, 0, 0});
+    }
+    if (!any) return IMCL_OK;
+    // costliest first within each phase (large filters, then the rest in plan order)
+    auto by_cost = [&](std::vector<BTile>& l) {
+        std::stable_sort(l.begin(), l.end(), [&](const BTile& a, const BTile& c) {
+            return b->himgs[a.img].K > b->himgs[c.img].K;
+        });
+    };
+    by_cost(l1);
+    by_cost(l2);
+    imcl_status st;
+    // the descriptors now carry gradient pointers: refresh the device copy
+    cudaError_t e = cudaMemcpy(b->dimgs, b->himgs.data(), b->himgs.size() * sizeof(BImg), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "batch descriptors");
+    BTile *d1 = nullptr, *d2 = nullptr, *d3 = nullptr;
+    if ((st = upload(&d1, l1, &b->owned)) != IMCL_OK) return st;
+    if ((st = upload(&d2, l2, &b->owned)) != IMCL_OK) return st;
+    if ((st = upload(&d3, l3, &b->owned)) != IMCL_OK) return st;
+    const size_t smem = batch_bwd_smem_bytes(b->py, b->bx, b->by);
+    if ((st = set_smem_limit(bwd_kernel(b->py), (int)smem)) != IMCL_OK) return st;
+    const int occ = cached_occupancy(bwd_kernel(b->py), 256, (int)smem);
+    if (occ <= 0) return fail(IMCL_ERR_UNSUPPORTED, "batch backward: kernel cannot be resident");
+    const int slots = occ * b->dev->sm_count;
+    e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "batch backward capture");
+    cudaMemsetAsync(b->queue, 0, 4 * sizeof(int), b->cap_stream);
+    const BTile* lists[3] = {d1, d2, d3};
+    const int counts[3] = {(int)l1.size(), (int)l2.size(), (int)l3.size()};
+    for (int ph = 0; ph < 3; ++ph) {
+        if (counts[ph] == 0) continue;
+        const int grid = std::max(1, std::min(counts[ph], slots));
+        if (b->py == 4)
+            k_batch_bwd<4><<<grid, 256, smem, b->cap_stream>>>(b->dimgs, lists[ph], counts[ph], b->queue + 1 + ph, b->bx, b->by);
+        else
+            k_batch_bwd<2><<<grid, 256, smem, b->cap_stream>>>(b->dimgs, lists[ph], counts[ph], b->queue + 1 + ph, b->bx, b->by);
+    }
+    cudaError_t le = cudaGetLastError();
+    e = cudaStreamEndCapture(b->cap_stream, &b->bwd_graph);
+    if (le != cudaSuccess) return cuda_fail(le, "batch backward launch");
+    if (e != cudaSuccess) return cuda_fail(e, "batch backward capture end");
+    e = cudaGraphInstantiate(&b->bwd_exec, b->bwd_graph, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "batch backward graph instantiate");
+    b->bwd_items[0] = counts[0];
+    b->bwd_items[1] = counts[1];
+    b->bwd_items[2] = counts[2];
+    return IMCL_OK;
+}
+
 Batch::~Batch() {
     if (fwd_exec) cudaGraphExecDestroy(fwd_exec);
     if (fwd_graph) cudaGraphDestroy(fwd_graph);
@@ -209,6 +328,7 @@ imcl_status batch_create(const imcl_batch_item* items, int n, double budget_s, B
     if (e != cudaSuccess) return bail(cuda_fail(e, "batch capture end"));
     e = cudaGraphInstantiate(&b->fwd_exec, b->fwd_graph, 0);
     if (e != cudaSuccess) return bail(cuda_fail(e, "batch graph instantiate"));
+    if ((st = plan_backward(b)) != IMCL_OK) return bail(st);
     e = cudaStreamSynchronize(b->cap_stream);
     if (e != cudaSuccess) return bail(cuda_fail(e, "batch sync"));
     *out = b;
@@ -233,6 +353,13 @@ imcl_status imagecl_batch_run(imcl_batch* h, void* stream) {
     Batch* b = reinterpret_cast<Batch*>(h);
     if (!b) return fail(IMCL_ERR_INVALID, "batch is NULL");
     return cuda_fail(cudaGraphLaunch(b->fwd_exec, static_cast<cudaStream_t>(stream)), "batch forward graph launch");
+}
+
+imcl_status imagecl_batch_backward(imcl_batch* h, void* stream) {
+    Batch* b = reinterpret_cast<Batch*>(h);
+    if (!b) return fail(IMCL_ERR_INVALID, "batch is NULL");
+    if (!b->bwd_exec) return fail(IMCL_ERR_INVALID, "no item of this batch carries gradient buffers");
+    return cuda_fail(cudaGraphLaunch(b->bwd_exec, static_cast<cudaStream_t>(stream)), "batch backward graph launch");
 }
 
 imcl_status imagecl_batch_info(const imcl_batch* h, imcl_batch_info_t* info) {

@@ -27,6 +27,7 @@ struct Batch {
     cudaGraphExec_t fwd_exec = nullptr;
     cudaGraph_t bwd_graph = nullptr;
     cudaGraphExec_t bwd_exec = nullptr;
+    int bwd_items[3] = {0, 0, 0};          // work items per backward phase
     std::vector<void*> owned;              // device allocations freed with the handle
     ~Batch();
 };

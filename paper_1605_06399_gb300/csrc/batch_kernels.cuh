@@ -271,4 +271,274 @@ __global__ void __launch_bounds__(256, 2)
     }
 }
 
+// ------------------------------------------------------------------ backward tiles
+// Tap-gradient partial sums over one tile from staged arrays: gs (gh x gsw, the upstream
+// gradient, tile rows at gs_row0) and xs (the operand region, xsw wide, tile-relative
+// origin (-rx, -ry + xs_row0)); out[j*kw + i] = sum_p g(p) x(p + (i - rx, j - ry)).
+__device__ void tile_wgrad(const float* gs, int gsw, int gs_row0, const float* xs, int xsw, int xs_row0, int TW,
+                           int TH, int kw, int kh, float* red, float* out, int tid, int nth) {
+    const int cw = (kw + 3) / 4, ngroups = kh * cw;
+    const int reps = nth / ngroups > 0 ? nth / ngroups : 1;
+    const int gi = tid % ngroups, rep = tid / ngroups;
+    const bool active = rep < reps;
+    const int j = gi / cw, i0 = (gi % cw) * 4;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    if (active) {
+        for (int py = rep; py < TH; py += reps) {
+            const float* gr = gs + (gs_row0 + py) * gsw;
+            const float* xr = xs + (xs_row0 + py + j) * xsw + i0;
+            for (int px = 0; px < TW; ++px) {
+                const float gv = gr[px];
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (i0 + k < kw) acc[k] = __fmaf_rn(gv, xr[px + k], acc[k]);
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) red[tid * 4 + k] = active ? acc[k] : 0.f;
+    __syncthreads();
+    for (int q = tid; q < kw * kh; q += nth) {
+        const int jj = q / kw, ii = q % kw;
+        const int grp = jj * cw + ii / 4, lane = ii % 4;
+        float sum = 0.f;
+        for (int r = 0; r < reps; ++r) sum += red[(r * ngroups + grp) * 4 + lane];
+        out[q] = sum;
+    }
+}
+
+// conv2d: input-gradient tile (all but the image's edge pixels under the clamp rule) and
+// the tile's tap partial sums.
+template <int K, int PY>
+__device__ void batch_conv_dx_tile(const BImg& im, int x0, int y0, int bx, int by, float* sm, int tid, int nth) {
+    const int TW = 4 * bx, TH = PY * by;
+    if (im.gin) {
+        batch_conv_tile<K, PY>(im, x0, y0, bx, by, sm, true, im.g, im.g_pitch, im.gin, im.gin_pitch, IMCL_F32, tid, nth);
+        __syncthreads();
+    }
+    if (im.gtaps) {
+        const int rx = (im.kw - 1) / 2, ry = (im.kh - 1) / 2;
+        const int XW = TW + im.kw - 1, XH = TH + im.kh - 1;
+        float* gs = sm;
+        float* xs = gs + TW * TH;
+        float* red = xs + XW * XH;
+        stage_region(gs, TW, TH, im.g, IMCL_F32, im.g_pitch, x0, y0, im.W, im.H, IMCL_BORDER_CONSTANT, 0.f, 1, tid, nth);
+        stage_region(xs, XW, XH, im.in, im.in_dt, im.in_pitch, x0 - rx, y0 - ry, im.W, im.H, im.border, im.bv, 0, tid,
+                     nth);
+        __syncthreads();
+        const int tile = (y0 / TH) * im.tiles_x + x0 / TW;
+        tile_wgrad(gs, TW, 0, xs, XW, 0, TW, TH, im.kw, im.kh, red, im.part + (size_t)tile * im.kw * im.kh, tid, nth);
+    }
+}
+
+// conv2d, clamp rule: the input gradient at a chunk of the image's edge pixels, with the
+// contributions of clamped taps folded in (the transpose of the clamp).
+__device__ void batch_conv_edges(const BImg& im, int chunk, int tid, int nth) {
+    const int W = im.W, H = im.H;
+    const int ntop = W, nside = H > 2 ? H - 2 : 0;
+    const int rows = H > 1 ? 2 * ntop : ntop;
+    const int nedge = rows + (W > 1 ? 2 * nside : nside);
+    const int rx = (im.kw - 1) / 2, ry = (im.kh - 1) / 2;
+    for (int e = chunk * 1024 + tid; e < min(nedge, (chunk + 1) * 1024); e += nth) {
+        int qx, qy;
+        if (e < rows) {
+            qx = e % W;
+            qy = e < ntop ? 0 : H - 1;
+        } else {
+            const int k = e - rows;
+            qy = 1 + (k % nside);
+            qx = k < nside ? 0 : W - 1;
+        }
+        const int xlo = qx == 0 ? -rx : qx, xhi = qx == W - 1 ? W - 1 + rx : qx;
+        const int ylo = qy == 0 ? -ry : qy, yhi = qy == H - 1 ? H - 1 + ry : qy;
+        float acc = 0.f;
+        for (int ey = ylo; ey <= yhi; ++ey)
+            for (int ex = xlo; ex <= xhi; ++ex)
+                for (int j = 0; j < im.kh; ++j) {
+                    const int sy = ey - j + ry;
+                    if (sy < 0 || sy >= H) continue;
+                    for (int i = 0; i < im.kw; ++i) {
+                        const int sx = ex - i + rx;
+                        if (sx < 0 || sx >= W) continue;
+                        acc = __fmaf_rn(im.taps[j * im.kw + i], im.g[(long long)sy * im.g_pitch + sx], acc);
+                    }
+                }
+        im.gin[(long long)qy * im.gin_pitch + qx] = acc;
+    }
+}
+
+// separable, first backward pass: dt = C^T g on the tile (with the clamp folds on the
+// first and last rows) into the plan's dt plane, and the column-tap partial sums
+// dcol[j] = sum_p g(p) t(p + (0, j - rc)), t the forward row pass.
+template <int R>
+__device__ void batch_sep_dt_tile(const BImg& im, int x0, int y0, int TW, int TH, float* sm, int tid, int nth) {
+    constexpr int PADR = 8;                             // >= R, 16 bytes of f32
+    const int nr = im.kw, nc = im.kh, rr = (nr - 1) / 2, rc = (nc - 1) / 2;
+    const int XW = TW + 2 * PADR, HH = TH + 2 * R;      // R >= rc rows of halo
+    float* gs = sm;                                     // TW x HH, rows y0 - R ..
+    float* w = gs + TW * HH;                            // row taps [0, 16), column taps [16, 32)
+    float* red = w + 32;
+    for (int i = tid; i < 32; i += nth) w[i] = i < 16 ? (i < nr ? im.taps[i] : 0.f) : (i - 16 < nc ? im.taps2[i - 16] : 0.f);
+    stage_region(gs, TW, HH, im.g, IMCL_F32, im.g_pitch, x0, y0 - R, im.W, im.H, IMCL_BORDER_CONSTANT, 0.f, 1, tid, nth);
+    __syncthreads();
+    const float* cw = w + 16;
+    // dt for the tile's pixels
+    if (im.dt) {
+        for (int k = tid; k < TW * TH; k += nth) {
+            const int py = k / TW, px = k % TW;
+            const int gx = x0 + px, gy = y0 + py;
+            if (gx >= im.W || gy >= im.H) continue;
+            float acc = 0.f;
+            for (int j = 0; j < nc; ++j) acc = __fmaf_rn(cw[j], gs[(py + R + rc - j) * TW + px], acc);
+            if (im.border == IMCL_BORDER_CLAMP) {
+                if (gy == 0)
+                    for (int e = -rc; e <= -1; ++e)
+                        for (int j = 0; j < nc; ++j) {
+                            const int sy = e - j + rc;   // image row, < rc
+                            if (sy >= 0 && sy < im.H) acc = __fmaf_rn(cw[j], gs[(sy - y0 + R) * TW + px], acc);
+                        }
+                if (gy == im.H - 1)
+                    for (int e = im.H; e <= im.H - 1 + rc; ++e)
+                        for (int j = 0; j < nc; ++j) {
+                            const int sy = e - j + rc;
+                            if (sy >= 0 && sy < im.H) acc = __fmaf_rn(cw[j], gs[(sy - y0 + R) * TW + px], acc);
+                        }
+            }
+            im.dt[(long long)gy * im.dt_pitch + gx] = acc;
+        }
+    }
+    if (im.gtaps2) {
+        // t on rows y0 - rc .. y0 + TH + rc of the tile's columns (boundary rule on x and t)
+        float* xs = red + 4 * 256;                      // XW x HH
+        float* ts = xs + XW * HH;                       // TW x HH
+        stage_region(xs, XW, HH, im.in, im.in_dt, im.in_pitch, x0 - PADR, y0 - R, im.W, im.H, im.border, im.bv, 0,
+                     tid, nth);
+        __syncthreads();
+        for (int k = tid; k < TW * HH; k += nth) {
+            const int r = k / TW, px = k % TW;
+            const int gy = y0 - R + r;
+            float acc = 0.f;
+            if (im.border == IMCL_BORDER_CONSTANT && (gy < 0 || gy >= im.H)) {
+                acc = im.bv;
+            } else {
+                for (int i = 0; i < nr; ++i) acc = __fmaf_rn(w[i], xs[r * XW + px + PADR - rr + i], acc);
+            }
+            ts[k] = acc;
+        }
+        __syncthreads();
+        const int tile = (y0 / TH) * im.tiles_x + x0 / TW;
+        // g rows of the tile start at row R of gs; t rows at offset R - rc relative to them
+        tile_wgrad(gs, TW, R, ts, TW, R - rc, TW, TH, 1, nc, red, im.part + (size_t)tile * nc, tid, nth);
+    }
+}
+
+// separable, second backward pass: dx = R^T dt on the tile (with the clamp folds on the
+// first and last columns) and the row-tap partials drow[i] = sum_p dt(p) x(p + (i - rr, 0)).
+__device__ void batch_sep_dx_tile(const BImg& im, int x0, int y0, int TW, int TH, float* sm, int tid, int nth) {
+    constexpr int PADR = 8;
+    const int nr = im.kw, rr = (nr - 1) / 2;
+    const int XW = TW + 2 * PADR;
+    float* ds = sm;                                     // XW x TH, columns x0 - PADR ..
+    float* xs = ds + XW * TH;                           // XW x TH
+    float* w = xs + XW * TH;
+    float* red = w + 16;
+    for (int i = tid; i < 16; i += nth) w[i] = i < nr ? im.taps[i] : 0.f;
+    stage_region(ds, XW, TH, im.dt, IMCL_F32, im.dt_pitch, x0 - PADR, y0, im.W, im.H, IMCL_BORDER_CONSTANT, 0.f, 1, tid,
+                 nth);
+    stage_region(xs, XW, TH, im.in, im.in_dt, im.in_pitch, x0 - PADR, y0, im.W, im.H, im.border, im.bv, 0, tid, nth);
+    __syncthreads();
+    if (im.gin) {
+        for (int k = tid; k < TW * TH; k += nth) {
+            const int py = k / TW, px = k % TW;
+            const int gx = x0 + px, gy = y0 + py;
+            if (gx >= im.W || gy >= im.H) continue;
+            float acc = 0.f;
+            for (int i = 0; i < nr; ++i) acc = __fmaf_rn(w[i], ds[py * XW + px + PADR + rr - i], acc);
+            if (im.border == IMCL_BORDER_CLAMP) {
+                if (gx == 0)
+                    for (int e = -rr; e <= -1; ++e)
+                        for (int i = 0; i < nr; ++i) {
+                            const int sx = e - i + rr;
+                            if (sx >= 0 && sx < im.W) acc = __fmaf_rn(w[i], ds[py * XW + sx - x0 + PADR], acc);
+                        }
+                if (gx == im.W - 1)
+                    for (int e = im.W; e <= im.W - 1 + rr; ++e)
+                        for (int i = 0; i < nr; ++i) {
+                            const int sx = e - i + rr;
+                            if (sx >= 0 && sx < im.W) acc = __fmaf_rn(w[i], ds[py * XW + sx - x0 + PADR], acc);
+                        }
+            }
+            im.gin[(long long)gy * im.gin_pitch + gx] = acc;
+        }
+    }
+    if (im.gtaps) {
+        const int tile = (y0 / TH) * im.tiles_x + x0 / TW;
+        const int ntiles = im.tiles_x * im.tiles_y;
+        // dt rows of the tile are ds rows 0..TH at columns PADR..; x at columns PADR - rr + i
+        tile_wgrad(ds + PADR, XW, 0, xs + PADR - rr, XW, 0, TW, TH, nr, 1, red,
+                   im.part + (size_t)ntiles * im.kh + (size_t)tile * nr, tid, nth);
+    }
+}
+
+// Reduce an image's tap partial sums over its tiles (fixed order) into the gradients.
+__device__ void batch_final(const BImg& im, int tid, int nth) {
+    const int ntiles = im.tiles_x * im.tiles_y;
+    // sum_t part[t * n + q] over the tiles, in tile order, for taps q < n
+    auto reduce = [&](const float* part, int n, float* out) {
+        for (int q = tid; q < n; q += nth) {
+            float s = 0.f;
+            for (int t = 0; t < ntiles; ++t) s += part[(size_t)t * n + q];
+            out[q] = s;
+        }
+    };
+    if (im.op == IMCL_OP_CONV2D) {
+        if (im.gtaps) reduce(im.part, im.kw * im.kh, im.gtaps);
+    } else {
+        if (im.gtaps2) reduce(im.part, im.kh, im.gtaps2);                                // column taps
+        if (im.gtaps) reduce(im.part + (size_t)ntiles * im.kh, im.kw, im.gtaps);        // row taps
+    }
+}
+
+template <int PY>
+__device__ void batch_bwd_dispatch(const BImg& im, const BTile& tl, int bx, int by, float* sm, int tid, int nth) {
+    const int TW = 4 * bx, TH = PY * by;
+    switch (tl.kind) {
+        case BT_CONV_DX:
+            switch (im.K) {
+                case 3: batch_conv_dx_tile<3, PY>(im, tl.x0, tl.y0, bx, by, sm, tid, nth); break;
+                case 5: batch_conv_dx_tile<5, PY>(im, tl.x0, tl.y0, bx, by, sm, tid, nth); break;
+                case 7: batch_conv_dx_tile<7, PY>(im, tl.x0, tl.y0, bx, by, sm, tid, nth); break;
+                case 9: batch_conv_dx_tile<9, PY>(im, tl.x0, tl.y0, bx, by, sm, tid, nth); break;
+                case 11: batch_conv_dx_tile<11, PY>(im, tl.x0, tl.y0, bx, by, sm, tid, nth); break;
+                case 13: batch_conv_dx_tile<13, PY>(im, tl.x0, tl.y0, bx, by, sm, tid, nth); break;
+                default: batch_conv_dx_tile<15, PY>(im, tl.x0, tl.y0, bx, by, sm, tid, nth); break;
+            }
+            break;
+        case BT_CONV_EDGE: batch_conv_edges(im, tl.x0, tid, nth); break;
+        case BT_SEP_DT: batch_sep_dt_tile<kBatchMaxR>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
+        case BT_SEP_DX: batch_sep_dx_tile(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
+        default: batch_final(im, tid, nth); break;
+    }
+}
+
+// Persistent backward phase: CTAs take work items from one list until it is exhausted.
+template <int PY>
+__global__ void __launch_bounds__(256, 1)
+    k_batch_bwd(const BImg* __restrict__ imgs, const BTile* __restrict__ items, int nitems, int* queue, int bx, int by) {
+    extern __shared__ __align__(16) float bsm[];
+    __shared__ int s_next;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (;;) {
+        if (tid == 0) s_next = atomicAdd(queue, 1);
+        __syncthreads();
+        const int t = s_next;
+        if (t >= nitems) break;
+        const BTile tl = items[t];
+        const BImg im = imgs[tl.img];
+        batch_bwd_dispatch<PY>(im, tl, bx, by, bsm, tid, nth);
+        __syncthreads();
+    }
+}
+
 }  // namespace imcl

@@ -368,6 +368,11 @@ class Batch:
         check(lib().imagecl_batch_run(self.handle, ctypes.c_void_p(stream_handle(stream))))
         return self.outputs
 
+    def backward(self, stream=None):
+        """Run the batch's adjoint: fills ``grad_in``, ``grad_taps`` (and ``grad_taps2``)."""
+        check(lib().imagecl_batch_backward(self.handle, ctypes.c_void_p(stream_handle(stream))))
+        return self.grad_in, self.grad_taps, self.grad_taps2
+
     def info(self) -> dict:
         i = _abi.BatchInfo()
         check(lib().imagecl_batch_info(self.handle, ctypes.byref(i)))

@@ -115,3 +115,61 @@ def test_workload_256_images_sampled():
             ref, s = sep_reference(it.image, it.taps, it.col_taps, rows=rows, halo=halo)
         check_float_output(yy, ref, s, torch.float16, f"{it.op} k={it.k} {it.height}x{it.width}")
     b.close()
+
+
+TOL_GRAD = 1e-4
+
+
+def _gate(gpu, ref, scale, what):
+    e = np.abs(gpu.detach().cpu().double().numpy() - ref) / np.maximum(scale, 1e-30)
+    assert float(e.max()) <= TOL_GRAD, f"{what}: scaled error {float(e.max()):.3e}"
+
+
+def test_batch_backward_matches_oracle():
+    """Batch adjoint against the single-image oracle adjoints, item by item."""
+    import oracle
+    g = np.random.default_rng(9100)
+    shapes = [(1, 1), (5, 3), (40, 70), (130, 257), (64, 300), (300, 31)]
+    items, meta = [], []
+    i = 0
+    for (h, w) in shapes:
+        for spec in (("conv", 3), ("conv", 15), ("conv", (5, 9)), ("sep", (3, 3)), ("sep", (15, 5)), ("sep", (1, 7))):
+            st = ("f16", "f32", "bf16")[i % 3]
+            border, bv = (("clamp", 0.0), ("constant", 0.375))[i % 2]
+            x = synth.to_storage(synth.uniform_f32(g, h, w), st)
+            gr = torch.from_numpy(g.standard_normal((h, w)).astype(np.float32))
+            if spec[0] == "conv":
+                kh, kw = spec[1] if isinstance(spec[1], tuple) else (spec[1], spec[1])
+                t = g.standard_normal((kh, kw)).astype(np.float32)
+                items.append({"op": "conv", "x": x.cuda(), "taps": torch.from_numpy(t).cuda(), "border": border,
+                              "border_value": bv, "grad_out": gr.cuda(), "out_dtype": torch.float32})
+                meta.append(("conv", x, t, None, gr.numpy(), border, bv))
+            else:
+                nr, nc = spec[1]
+                r = g.standard_normal(nr).astype(np.float32)
+                c = g.standard_normal(nc).astype(np.float32)
+                items.append({"op": "sep", "x": x.cuda(), "taps": torch.from_numpy(r).cuda(),
+                              "col_taps": torch.from_numpy(c).cuda(), "border": border, "border_value": bv,
+                              "grad_out": gr.cuda(), "out_dtype": torch.float32})
+                meta.append(("sep", x, r, c, gr.numpy(), border, bv))
+            i += 1
+    b = Batch(items, tune_budget_s=1.0)
+    assert b.info()["has_backward"]
+    b.run()
+    gin, gt, gt2 = b.backward()
+    torch.cuda.synchronize()
+    for k, (op, x, t1, t2, gr, border, bv) in enumerate(meta):
+        ax = np.abs(x.double().numpy())
+        what = f"item {k} {op} {tuple(x.shape)} {border}"
+        if op == "conv":
+            dx64, dw64 = oracle.conv2d_backward(x, t1, gr, border, bv)
+            sdx, sdw = oracle.conv2d_backward(ax, np.abs(t1), np.abs(gr), border, abs(bv))
+            _gate(gin[k], dx64, sdx, "dx " + what)
+            _gate(gt[k], dw64, sdw, "dw " + what)
+        else:
+            dx64, dr64, dc64 = oracle.sepconv_backward(x, t1, t2, gr, border, bv)
+            sdx, sdr, sdc = oracle.sepconv_backward(ax, np.abs(t1), np.abs(t2), np.abs(gr), border, abs(bv))
+            _gate(gin[k], dx64, sdx, "dx " + what)
+            _gate(gt[k], dr64, sdr, "drow " + what)
+            _gate(gt2[k], dc64, sdc, "dcol " + what)
+    b.close()
