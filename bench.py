@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--tune-budget", type=float, default=20.0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the per-stencil measurements of the other workloads")
     ap.add_argument("--tune-cache", default=None,
                     help="tuning cache file: loaded (and tuning skipped) if it exists, "
                          "written after tuning otherwise")
@@ -216,6 +218,149 @@ def oracle_rate(img, taps_by_k, seconds, gpu_outs=None):
     return px / dt / 1e6, (n, passes), oracle.num_threads(), dt, errs
 
 
+# ----------------------------------------------------------------------------- other stencils
+
+def _median_ms(fn, reps, flush=None):
+    """Median device time of fn() over `reps` runs, each bracketed by CUDA events on the
+    current stream; `flush` (a tensor larger than L2) is rewritten before each run."""
+    import torch
+    stream = torch.cuda.current_stream()
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for r in range(reps):
+        if flush is not None:
+            flush.fill_(float(r))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ts.sort()
+    return ts[len(ts) // 2]
+
+
+def _entry(px, tuned_ms, plain_ms, bytes_px, flops_px, hbm_gbs, fp32_peak, variant=None, note=None):
+    t = tuned_ms / 1e3
+    d = {"tuned_mpx_s": px / t / 1e6, "tuned_ms": tuned_ms,
+         "hbm_gbs": bytes_px * px / t / 1e9, "hbm_frac": bytes_px * px / t / 1e9 / hbm_gbs,
+         "fp32_tflops": flops_px * px / t / 1e12, "fp32_frac": flops_px * px / t / 1e12 / fp32_peak}
+    if plain_ms is not None:
+        d.update({"plain_mpx_s": px / (plain_ms / 1e3) / 1e6, "plain_ms": plain_ms,
+                  "speedup_vs_plain": plain_ms / tuned_ms})
+    if variant is not None:
+        d["variant"] = variant
+    if note:
+        d["note"] = note
+    return d
+
+
+def extra_stencils(hbm_gbs, fp32_peak, budget):
+    """Tuned vs plain for the other workloads (inputs resident; L2 flushed between runs
+    when a working set would fit in L2)."""
+    import torch
+    from paper_1605_06399_gb300 import Batch, _abi, ops, synth
+    out = {}
+    dev = torch.device("cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    plain = {"kind": _abi.KIND_PLAIN, "bx": 16, "by": 16}
+
+    # 512x512 u8, 3x3 integer taps: launch-latency bound, timed by CUDA-graph replay
+    img, taps = synth.workload_int3x3()
+    x = torch.from_numpy(img).to(dev)
+    y = torch.empty((512, 512), dtype=torch.int32, device=dev)
+    res = ops.tune(ops.problem(_abi.OP_CONV2D, "u8", "i32", 3, 3, 512, 512), budget_s=budget, reps=5)
+    times = {}
+    for name, v in (("tuned", None), ("plain", plain)):
+        ops.conv2d(x, taps, out=y, variant=v)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for _ in range(100):
+                ops.conv2d(x, taps, out=y, variant=v)
+        times[name] = _median_ms(g.replay, 7) / 100
+    out["conv3x3_512_u8_i32"] = _entry(512 * 512, times["tuned"], times["plain"], 5, 18, hbm_gbs, fp32_peak,
+                                       res["variant"], "L2-resident, launch-latency bound: % roofline not "
+                                       "meaningful; per-launch time from a 100-launch CUDA graph")
+    del x, y
+
+    # separable Gaussian, 8192x8192, radius R, storage types
+    g = np.random.default_rng(3)
+    base = synth.uniform_f32(g, SIDE, SIDE)
+    for R in (2, 8, 16):
+        t = synth.gaussian_taps(R)
+        for ind, outd in (("f32", "f32"), ("bf16", "f32"), ("f16", "f16"), ("bf16", "bf16")):
+            x = synth.to_storage(base, ind).to(dev)
+            od = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[outd]
+            y = torch.empty((SIDE, SIDE), dtype=od, device=dev)
+            res = ops.tune(ops.problem(_abi.OP_SEPCONV, ind, outd, 2 * R + 1, 2 * R + 1, SIDE, SIDE),
+                           budget_s=budget, reps=3)
+            ws = torch.empty(SIDE * SIDE * 4, dtype=torch.uint8, device=dev)
+            tt = _median_ms(lambda: ops.sepconv(x, t, t, out=y), 7)
+            tp = _median_ms(lambda: ops.sepconv(x, t, t, out=y, variant=plain, workspace=ws), 5)
+            bpx = x.element_size() + y.element_size()
+            out[f"sep_R{R}_8192_{ind}_{outd}"] = _entry(SIDE * SIDE, tt, tp, bpx, 4 * (2 * R + 1), hbm_gbs,
+                                                        fp32_peak, res["variant"])
+            del x, y, ws
+    del base
+
+    # Harris, 4096x4096 rectangles: forward tuned vs the two-kernel form, and the backward
+    img, sx, sy, win, k = synth.workload_harris()
+    x = torch.from_numpy(img).to(dev)
+    y = torch.empty_like(x)
+    res = ops.tune(ops.problem(_abi.OP_HARRIS, "f32", "f32", 5, 5, 4096, 4096), budget_s=budget, reps=3)
+    ws = torch.empty(2 * 4096 * 4096 * 4, dtype=torch.uint8, device=dev)
+    tt = _median_ms(lambda: ops.harris(x, sx, sy, win, k, out=y), 7, flush)
+    tp = _median_ms(lambda: ops.harris(x, sx, sy, win, k, out=y, variant=plain, workspace=ws), 5, flush)
+    px = 4096 * 4096
+    flops_fwd = 2 * 18 * (4100 * 4100) / px + 3 + 2 * 3 * 25 + 7
+    out["harris_4096_fwd"] = _entry(px, tt, tp, 8, flops_fwd, hbm_gbs, fp32_peak, res["variant"])
+    gR = torch.randn(4096, 4096, device=dev)
+    tb = _median_ms(lambda: ops.harris_backward(gR, x, sx, sy, win, k), 5)
+    out["harris_4096_bwd"] = _entry(px, tb, None, 8, 0, hbm_gbs, fp32_peak,
+                                    note="adjoint of the fused forward: image, Sobel and window gradients")
+    del x, y, ws, gR
+
+    # ragged batch: 256 f16 images, one graph launch forward and one backward
+    items = synth.workload_batch()
+    bitems = []
+    for it in items:
+        xi = it.image.to(dev)
+        d = {"op": it.op, "x": xi, "taps": torch.from_numpy(it.taps).to(dev), "out_dtype": torch.float16,
+             "grad_out": torch.randn(xi.shape, device=dev)}
+        if it.op == "sep":
+            d["col_taps"] = torch.from_numpy(it.col_taps).to(dev)
+        bitems.append(d)
+    b = Batch(bitems, tune_budget_s=budget)
+    info = b.info()
+    tf = _median_ms(b.run, 7)
+    tbw = _median_ms(b.backward, 5)
+
+    def plain_loop():
+        for d in bitems:
+            if d["op"] == "conv":
+                ops.conv2d(d["x"], d["taps"], out_dtype=torch.float16, variant=plain)
+            else:
+                ops.sepconv(d["x"], d["taps"], d["col_taps"], out_dtype=torch.float16, variant=plain)
+    tpl = _median_ms(plain_loop, 3)
+    bytes_total = sum(it.width * it.height * 4 for it in items)
+    flops_total = sum(it.width * it.height * (2 * it.k * it.k if it.op == "conv" else 4 * it.k) for it in items)
+    # per-image roofline time: sum of max(bytes / BW, flops / P_fp32)
+    roof_ms = sum(max(it.width * it.height * 4 / (hbm_gbs * 1e9),
+                      it.width * it.height * (2 * it.k * it.k if it.op == "conv" else 4 * it.k) / (fp32_peak * 1e12))
+                  for it in items) * 1e3
+    e = _entry(info["pixels"], tf, tpl, bytes_total / info["pixels"], flops_total / info["pixels"], hbm_gbs,
+               fp32_peak, note=f"{info['images']} images, {info['tiles']} tiles of {info['tile']}; plain = "
+                               "one untuned launch per image")
+    e["roofline_frac"] = roof_ms / tf
+    out["batch256_f16_fwd"] = e
+    out["batch256_f16_bwd"] = _entry(info["pixels"], tbw, None, 0, 0, hbm_gbs, fp32_peak,
+                                     note="input and tap gradients of every image, one graph launch")
+    b.close()
+    return out
+
+
 # ----------------------------------------------------------------------------- our arm
 
 def run_ours(args):
@@ -376,6 +521,10 @@ def run_ours(args):
                 "frac": d["hbm_frac"], "traffic": traffic,
                 "kernel": f"k_conv2d_tiled {dom}x{dom} f32", "peak_source": f"{peak_src} copy bandwidth"}
 
+    probe = {"ffma_tflops": ops.probe_fp32(False), "ffma2_tflops": ops.probe_fp32(True)}
+    if not args.no_extras:
+        per_stencil.update(extra_stencils(hbm_gbs, fp32_peak, max(2.0, args.tune_budget / 4)))
+
     gpu_outs = None
     cpu = None
     errs = {}
@@ -404,6 +553,7 @@ def run_ours(args):
         "clocks": clocks,
         "gpu_launches": args.steps * len(KS),
         "per_stencil": per_stencil,
+        "fp32_probe": probe,
         "max_scaled_err": {f"{k}x{k}": errs.get(k) for k in KS} if errs else None,
         "tolerance": 1e-5,
     }

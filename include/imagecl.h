@@ -331,6 +331,13 @@ void imagecl_tune_clear(void);
 imcl_status imagecl_tune_save(const char *path);
 imcl_status imagecl_tune_load(const char *path);
 
+/* ------------------------------------------------------------------ measurement */
+
+/* FP32 pipe throughput of the current device in TFLOP/s (2 flops per FMA), measured with
+ * independent FMA chains (packed = 0: scalar FMAs; 1: packed f32x2 FMAs).  A measurement
+ * helper for the ALU roofline of the stencils, not an operator; synchronises `stream`. */
+imcl_status imagecl_probe_fp32(int32_t packed, double *tflops, void *stream);
+
 /* ------------------------------------------------------------------ status */
 
 /* Human-readable description of this thread's last failed call ("" if none). */

@@ -16,6 +16,12 @@ namespace imcl {
 static const int kShapes[][3] = {{4, 32, 8}, {4, 16, 16}, {2, 32, 8}, {2, 16, 16}};
 constexpr int kNumShapes = 4;
 
+// Byte alignment every row start of an image shares (16, 4, or 0 for less).
+static int row_alignment(const void* base, int64_t pitch_bytes) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(base) | (uintptr_t)pitch_bytes;
+    return (a & 15) == 0 ? 16 : ((a & 3) == 0 ? 4 : 0);
+}
+
 int batch_side(int op, int kw, int kh) {
     const int m = std::max(kw, kh);
     const int side = std::max(3, m);
@@ -113,6 +119,7 @@ static imcl_status plan_backward(Batch* b) {
             return fail(IMCL_ERR_INVALID, "item " + std::to_string(i) + ": grad_out must be f32 of the image's size");
         im.g = static_cast<const float*>(it.grad_out.data);
         im.g_pitch = it.grad_out.pitch_bytes / 4;
+        im.g_vec = row_alignment(it.grad_out.data, it.grad_out.pitch_bytes);
         if (it.grad_in.data) {
             if ((st = check_image(&it.grad_in, "grad_in")) != IMCL_OK) return st;
             if (it.grad_in.dtype != IMCL_F32 || it.grad_in.width != im.W || it.grad_in.height != im.H)
@@ -252,6 +259,7 @@ static BImg make_bimg(const imcl_batch_item& it) {
     b.taps2 = it.taps2;
     b.border = it.border;
     b.bv = (float)it.border_value;
+    b.in_vec = row_alignment(it.in.data, it.in.pitch_bytes);
     return b;
 }
 

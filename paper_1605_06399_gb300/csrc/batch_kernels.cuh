@@ -30,6 +30,7 @@ struct BImg {
     const float* taps2;                // sep: column taps (kh)
     int border;
     float bv;
+    int in_vec, g_vec;                 // byte alignment of the rows (16, 4 or less) for staging
     // backward
     const float* g;                    // upstream gradient (f32)
     long long g_pitch;
@@ -76,18 +77,89 @@ __device__ __forceinline__ void store_px(void* base, int dt, long long pitch, in
 }
 
 // Stage region [gx0, gx0+sw) x [gy0, gy0+sh) of an image as f32 with its boundary rule
-// (mode 0), or with zeros outside (mode 1, for upstream gradients).
+// (zero_outside = 0), or with zeros outside (1, for upstream gradients).  When the region
+// starts on an 8-pixel boundary and the image rows are 16-byte aligned (vec), chunks of 8
+// pixels inside the image are read with 16-byte loads, several in flight per thread.
+__device__ __forceinline__ float outside_px(const void* img, int dt, long long pitch, int gx, int gy, int W, int H,
+                                            int border, float bv, int zero_outside) {
+    if (gx >= 0 && gx < W && gy >= 0 && gy < H) return load_px(img, dt, pitch, gx, gy);
+    if (zero_outside) return 0.f;
+    if (border == IMCL_BORDER_CONSTANT) return bv;
+    return load_px(img, dt, pitch, clampi(gx, 0, W - 1), clampi(gy, 0, H - 1));
+}
+
+// 8 consecutive pixels of one row starting at gx (all inside the image), with the widest
+// loads the row's alignment allows: 16-byte vectors (vec = 16), pairs of 16-bit pixels
+// (vec = 4), or single pixels; the loads are independent, so they are in flight together.
+__device__ __forceinline__ void load8_inside(const void* img, int dt, long long pitch, int gx, int gy, int vec,
+                                             float* v) {
+    const long long o = (long long)gy * pitch + gx;
+    if (dt == IMCL_F32) {
+        const float* p = static_cast<const float*>(img) + o;
+        if (vec >= 16) {
+            const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+            const float4 b = __ldg(reinterpret_cast<const float4*>(p + 4));
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = __ldg(p + e);
+        }
+        return;
+    }
+    const uint16_t* p = static_cast<const uint16_t*>(img) + o;
+    uint32_t u[4];
+    if (vec >= 16) {
+        const uint4 q = __ldg(reinterpret_cast<const uint4*>(p));
+        u[0] = q.x; u[1] = q.y; u[2] = q.z; u[3] = q.w;
+    } else if (vec >= 4) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) u[k] = __ldg(reinterpret_cast<const unsigned int*>(p) + k);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) u[k] = (uint32_t)__ldg(p + 2 * k) | ((uint32_t)__ldg(p + 2 * k + 1) << 16);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (dt == IMCL_F16) {
+            const __half2 h = *reinterpret_cast<const __half2*>(&u[k]);
+            const float2 f = __half22float2(h);
+            v[2 * k] = f.x;
+            v[2 * k + 1] = f.y;
+        } else {
+            v[2 * k] = __uint_as_float(u[k] << 16);
+            v[2 * k + 1] = __uint_as_float(u[k] & 0xffff0000u);
+        }
+    }
+}
+
+// Stage region [gx0, gx0+sw) x [gy0, gy0+sh) of an image as f32 with its boundary rule
+// (zero_outside = 0), or with zeros outside (1, for upstream gradients), in chunks of 8
+// pixels.  vec: the alignment in bytes of the image's rows (16, 4 or less).
 __device__ void stage_region(float* st, int sw, int sh, const void* img, int dt, long long pitch, int gx0, int gy0,
-                             int W, int H, int border, float bv, int zero_outside, int tid, int nth) {
+                             int W, int H, int border, float bv, int zero_outside, int tid, int nth, int vec = 0) {
+    if ((gx0 & 7) == 0 && (sw & 7) == 0) {
+        const int nch = sw >> 3;
+#pragma unroll 2
+        for (int idx = tid; idx < nch * sh; idx += nth) {
+            const int r = idx / nch, c = (idx - r * nch) << 3;
+            const int gx = gx0 + c, gy = gy0 + r;
+            float v[8];
+            if (gy >= 0 && gy < H && gx >= 0 && gx + 8 <= W) {
+                load8_inside(img, dt, pitch, gx, gy, vec, v);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v[e] = outside_px(img, dt, pitch, gx + e, gy, W, H, border, bv, zero_outside);
+            }
+            float* d = st + r * sw + c;
+            *reinterpret_cast<float4*>(d) = make_float4(v[0], v[1], v[2], v[3]);
+            *reinterpret_cast<float4*>(d + 4) = make_float4(v[4], v[5], v[6], v[7]);
+        }
+        return;
+    }
     for (int idx = tid; idx < sw * sh; idx += nth) {
         const int r = idx / sw, c = idx - r * sw;
-        const int gx = gx0 + c, gy = gy0 + r;
-        float v;
-        if (gx >= 0 && gx < W && gy >= 0 && gy < H) v = load_px(img, dt, pitch, gx, gy);
-        else if (zero_outside) v = 0.f;
-        else if (border == IMCL_BORDER_CONSTANT) v = bv;
-        else v = load_px(img, dt, pitch, clampi(gx, 0, W - 1), clampi(gy, 0, H - 1));
-        st[idx] = v;
+        st[idx] = outside_px(img, dt, pitch, gx0 + c, gy0 + r, W, H, border, bv, zero_outside);
     }
 }
 
@@ -108,7 +180,7 @@ __device__ void batch_conv_tile(const BImg& im, int x0, int y0, int bx, int by, 
                                 const float* g_src, long long g_pitch, void* dst, long long dst_pitch, int dst_dt,
                                 const int tid, const int nth) {
     constexpr int PX = 4;
-    using G = TileGeo<float, K, PX>;
+    using G = TileGeo<__half, K, PX>;    // halo padded to 8 columns: 16-byte aligned staging
     const int TW = bx * PX, TH = by * PY, SW = TW + 2 * G::PAD, SH = TH + K - 1;
     float* st = sm;
     float* w = sm + SW * SH;
@@ -126,10 +198,10 @@ __device__ void batch_conv_tile(const BImg& im, int x0, int y0, int bx, int by, 
     }
     if (flipped_zero)
         stage_region(st, SW, SH, g_src, IMCL_F32, g_pitch, x0 - G::PAD, y0 - R, im.W, im.H, IMCL_BORDER_CONSTANT, 0.f, 1,
-                     tid, nth);
+                     tid, nth, im.g_vec);
     else
         stage_region(st, SW, SH, im.in, im.in_dt, im.in_pitch, x0 - G::PAD, y0 - R, im.W, im.H, im.border, im.bv, 0,
-                     tid, nth);
+                     tid, nth, im.in_vec);
     __syncthreads();
     if (tid < bx * by) {
         const int tx = tid % bx, ty = tid / bx;
@@ -138,11 +210,24 @@ __device__ void batch_conv_tile(const BImg& im, int x0, int y0, int bx, int by, 
         for (int oy = 0; oy < PY; ++oy)
 #pragma unroll
             for (int ox = 0; ox < PX; ++ox) acc[oy][ox] = 0.f;
+        // filter row j outermost: its K taps stay in registers while the PY output rows
+        // that read input row (oy + j) accumulate (one shared-memory read per tap per tile).
+        // The j loop stays rolled: one batch kernel carries every filter side, and fully
+        // unrolled bodies for all of them would not fit the instruction cache together.
+#pragma unroll 1
+        for (int j = 0; j < K; ++j) {
+            float wr[K];
 #pragma unroll
-        for (int yy = 0; yy < PY + K - 1; ++yy) {
-            float seg[G::SEG];
-            load_seg_smem<float, G>(st + (ty * PY + yy) * SW + tx * PX, seg);
-            fma_row_blocked<G, K, PX, PY, 1>(yy, seg, acc, w);
+            for (int i = 0; i < K; ++i) wr[i] = w[j * K + i];
+#pragma unroll
+            for (int oy = 0; oy < PY; ++oy) {
+                float seg[G::SEG];
+                load_seg_smem<float, G>(st + (ty * PY + oy + j) * SW + tx * PX, seg);
+#pragma unroll
+                for (int i = 0; i < K; ++i)
+#pragma unroll
+                    for (int ox = 0; ox < PX; ++ox) acc[oy][ox] = __fmaf_rn(wr[i], seg[G::LO + ox + i], acc[oy][ox]);
+            }
         }
         const bool skip_edges = flipped_zero && im.border == IMCL_BORDER_CLAMP;   // edge items own those
 #pragma unroll
@@ -165,7 +250,7 @@ __device__ void batch_conv_tile(const BImg& im, int x0, int y0, int bx, int by, 
 template <int R, int PY>
 __device__ void batch_sep_tile(const BImg& im, int x0, int y0, int bx, int by, float* sm, const int tid, const int nth) {
     constexpr int PX = 4, NT = 2 * R + 1;
-    using G = TileGeo<float, NT, PX>;
+    using G = TileGeo<__half, NT, PX>;   // halo padded to 8 columns: 16-byte aligned staging
     const int TW = bx * PX, TH = by * PY, SW = TW + 2 * G::PAD, SH = TH + 2 * R;
     float* st = sm;
     float* tb = st + SW * SH;
@@ -176,8 +261,11 @@ __device__ void batch_sep_tile(const BImg& im, int x0, int y0, int bx, int by, f
         w[NT + i] = (i >= orc && i < orc + im.kh) ? im.taps2[i - orc] : 0.f;
     }
     stage_region(st, SW, SH, im.in, im.in_dt, im.in_pitch, x0 - G::PAD, y0 - R, im.W, im.H, im.border, im.bv, 0, tid,
-                 nth);
+                 nth, im.in_vec);
     __syncthreads();
+    float rw[NT], cw[NT];                 // row and column taps, in registers for the tile
+#pragma unroll
+    for (int i = 0; i < NT; ++i) { rw[i] = w[i]; cw[i] = w[NT + i]; }
     const int nseg = TW / PX;
     for (int it = tid; it < SH * nseg; it += nth) {
         const int row = it / nseg, c0 = (it - row * nseg) * PX;
@@ -194,7 +282,7 @@ __device__ void batch_sep_tile(const BImg& im, int x0, int y0, int bx, int by, f
 #pragma unroll
             for (int i = 0; i < NT; ++i)
 #pragma unroll
-                for (int ox = 0; ox < PX; ++ox) r4[ox] = __fmaf_rn(w[i], seg[G::LO + ox + i], r4[ox]);
+                for (int ox = 0; ox < PX; ++ox) r4[ox] = __fmaf_rn(rw[i], seg[G::LO + ox + i], r4[ox]);
         }
         *reinterpret_cast<float4*>(tb + row * TW + c0) = make_float4(r4[0], r4[1], r4[2], r4[3]);
     }
@@ -214,9 +302,8 @@ __device__ void batch_sep_tile(const BImg& im, int x0, int y0, int bx, int by, f
             for (int oy = 0; oy < PY; ++oy) {
                 const int j = yy - oy;
                 if (j >= 0 && j < NT) {
-                    const float cj = w[NT + j];
 #pragma unroll
-                    for (int ox = 0; ox < PX; ++ox) acc[oy][ox] = __fmaf_rn(cj, tv[ox], acc[oy][ox]);
+                    for (int ox = 0; ox < PX; ++ox) acc[oy][ox] = __fmaf_rn(cw[j], tv[ox], acc[oy][ox]);
                 }
             }
         }
@@ -323,7 +410,8 @@ __device__ void batch_conv_dx_tile(const BImg& im, int x0, int y0, int bx, int b
         float* gs = sm;
         float* xs = gs + TW * TH;
         float* red = xs + XW * XH;
-        stage_region(gs, TW, TH, im.g, IMCL_F32, im.g_pitch, x0, y0, im.W, im.H, IMCL_BORDER_CONSTANT, 0.f, 1, tid, nth);
+        stage_region(gs, TW, TH, im.g, IMCL_F32, im.g_pitch, x0, y0, im.W, im.H, IMCL_BORDER_CONSTANT, 0.f, 1, tid, nth,
+                     im.g_vec);
         stage_region(xs, XW, XH, im.in, im.in_dt, im.in_pitch, x0 - rx, y0 - ry, im.W, im.H, im.border, im.bv, 0, tid,
                      nth);
         __syncthreads();
@@ -380,7 +468,8 @@ __device__ void batch_sep_dt_tile(const BImg& im, int x0, int y0, int TW, int TH
     float* w = gs + TW * HH;                            // row taps [0, 16), column taps [16, 32)
     float* red = w + 32;
     for (int i = tid; i < 32; i += nth) w[i] = i < 16 ? (i < nr ? im.taps[i] : 0.f) : (i - 16 < nc ? im.taps2[i - 16] : 0.f);
-    stage_region(gs, TW, HH, im.g, IMCL_F32, im.g_pitch, x0, y0 - R, im.W, im.H, IMCL_BORDER_CONSTANT, 0.f, 1, tid, nth);
+    stage_region(gs, TW, HH, im.g, IMCL_F32, im.g_pitch, x0, y0 - R, im.W, im.H, IMCL_BORDER_CONSTANT, 0.f, 1, tid, nth,
+                 im.g_vec);
     __syncthreads();
     const float* cw = w + 16;
     // dt for the tile's pixels
@@ -413,7 +502,7 @@ __device__ void batch_sep_dt_tile(const BImg& im, int x0, int y0, int TW, int TH
         float* xs = red + 4 * 256;                      // XW x HH
         float* ts = xs + XW * HH;                       // TW x HH
         stage_region(xs, XW, HH, im.in, im.in_dt, im.in_pitch, x0 - PADR, y0 - R, im.W, im.H, im.border, im.bv, 0,
-                     tid, nth);
+                     tid, nth, im.in_vec);
         __syncthreads();
         for (int k = tid; k < TW * HH; k += nth) {
             const int r = k / TW, px = k % TW;
@@ -445,8 +534,9 @@ __device__ void batch_sep_dx_tile(const BImg& im, int x0, int y0, int TW, int TH
     float* red = w + 16;
     for (int i = tid; i < 16; i += nth) w[i] = i < nr ? im.taps[i] : 0.f;
     stage_region(ds, XW, TH, im.dt, IMCL_F32, im.dt_pitch, x0 - PADR, y0, im.W, im.H, IMCL_BORDER_CONSTANT, 0.f, 1, tid,
-                 nth);
-    stage_region(xs, XW, TH, im.in, im.in_dt, im.in_pitch, x0 - PADR, y0, im.W, im.H, im.border, im.bv, 0, tid, nth);
+                 nth, 16);
+    stage_region(xs, XW, TH, im.in, im.in_dt, im.in_pitch, x0 - PADR, y0, im.W, im.H, im.border, im.bv, 0, tid, nth,
+                 im.in_vec);
     __syncthreads();
     if (im.gin) {
         for (int k = tid; k < TW * TH; k += nth) {

@@ -131,10 +131,28 @@ __device__ __forceinline__ void ldg_vec(const T* p, A* dst) {
     }
 }
 
+// Round pairs of f32 to packed 16-bit values (one conversion per pair).
+__device__ __forceinline__ uint32_t pack2(__half, float a, float b) {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16, float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
 // Store N accumulators as N consecutive output pixels with one vector store.
 template <typename T, int N, typename A>
 __device__ __forceinline__ void store_vec(T* p, const A* src) {
     constexpr int B = N * (int)sizeof(T);
+    if constexpr (sizeof(T) == 2 && N % 2 == 0 && (B == 8 || B == 16)) {
+        uint32_t w[N / 2];
+#pragma unroll
+        for (int k = 0; k < N / 2; ++k) w[k] = pack2(T(), src[2 * k], src[2 * k + 1]);
+        if constexpr (B == 16) *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+        else *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
+        return;
+    }
     T e[N];
 #pragma unroll
     for (int k = 0; k < N; ++k) e[k] = Store<T, A>::cvt(src[k]);

@@ -21,6 +21,19 @@
 
 namespace imcl {
 
+// Window-pass geometry: the product buffer's column c holds region column c (image column
+// x0 - RW + c), so a thread's segment starts at its own first output column, 16-byte
+// aligned, and holds exactly the PX + 2 RW products it needs (rounded up to whole float4s).
+template <int WK>
+struct HarrisWindowGeo {
+    static constexpr int PX = 4;
+    static constexpr int R = (WK - 1) / 2;
+    static constexpr int VB = 4;
+    static constexpr int SEG = round_up(PX + 2 * R, 4);
+    static constexpr int LO = 0;
+    static constexpr int USED = PX + 2 * R;
+};
+
 // taps of the Harris operator as they travel in the launch parameters
 template <int WK>
 struct HarrisTaps {
@@ -90,16 +103,15 @@ __global__ void __launch_bounds__(256, 2)
     constexpr int HALO = RW + 1;                       // input rows/cols beyond the tile
     constexpr int PADI = 4;                            // staged input halo columns (16 B)
     static_assert(HALO <= PADI, "window radius too large for the staged halo");
-    using GW = TileGeo<float, WK, PX>;                 // window pass geometry (PAD = PADP)
-    constexpr int PADP = GW::PAD;
+    using GW = HarrisWindowGeo<WK>;                   // window pass: region column == buffer column
     extern __shared__ __align__(128) uint8_t smem[];
 
     const int tid = threadIdx.x, nth = blockDim.x;
     const int bx = a.bx, by = a.by;
     const int TW = bx * PX, TH = by * PY;
     const int SW = TW + 2 * PADI, SH = TH + 2 * HALO;
-    const int PH = TH + 2 * RW, PW = TW + 2 * PADP;
     const int NG = (TW + 2 * RW + 3) / 4;              // product groups of 4 columns per row
+    const int PH = TH + 2 * RW, PW = 4 * NG;
     const int stage_bytes = round_up(SW * SH * 4, 128);
     constexpr int kStages = LOAD == IMCL_LOAD_TMA ? 2 : 1;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
@@ -170,7 +182,8 @@ __global__ void __launch_bounds__(256, 2)
 
         // products for the (TW + 2RW) x (TH + 2RW) window region, 4 columns per item.
         // Product column pc (region-local, 0 = image column x0 - RW) lives at pbuf column
-        // pc - RW + PADP.  Each product is taken at the clamped position of its pixel.
+        // pc, so a group of 4 is one aligned float4 per plane.  Each product is taken at
+        // the clamped position of its pixel.
         const bool interior = x0 - RW >= 0 && y0 - RW >= 0 && x0 - RW + 4 * NG <= a.W && y0 + TH + RW <= a.H;
         for (int it = tid; it < PH * NG; it += nth) {
             const int pr = it / NG, pc0 = (it - pr * NG) * 4;
@@ -221,16 +234,13 @@ __global__ void __launch_bounds__(256, 2)
                     gy[e] = ay;
                 }
             }
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int col = pc0 + e - RW + PADP;
-                if (col < PW) {
-                    float* p = pbuf + pr * PW + col;
-                    p[0] = gx[e] * gx[e];
-                    p[plane] = gy[e] * gy[e];
-                    p[2 * plane] = gx[e] * gy[e];
-                }
-            }
+            float* p = pbuf + pr * PW + pc0;
+            *reinterpret_cast<float4*>(p) =
+                make_float4(gx[0] * gx[0], gx[1] * gx[1], gx[2] * gx[2], gx[3] * gx[3]);
+            *reinterpret_cast<float4*>(p + plane) =
+                make_float4(gy[0] * gy[0], gy[1] * gy[1], gy[2] * gy[2], gy[3] * gy[3]);
+            *reinterpret_cast<float4*>(p + 2 * plane) =
+                make_float4(gx[0] * gy[0], gx[1] * gy[1], gx[2] * gy[2], gx[3] * gy[3]);
         }
         __syncthreads();
 
@@ -285,7 +295,6 @@ imcl_status launch_harris_plain(const ConvCall& c, const imcl_variant& v, cudaSt
 template <int WK, int PY, int LOAD, int FILT>
 imcl_status launch_harris_fused(const ConvCall& c, const imcl_variant& v, cudaStream_t s) {
     constexpr int PX = 4, RW = (WK - 1) / 2, HALO = RW + 1, PADI = 4;
-    using GW = TileGeo<float, WK, PX>;
     const int bx = v.bx, by = v.by, nth = bx * by;
     if (bx <= 0 || by <= 0 || nth > 256 || nth % 32 != 0)
         return fail(IMCL_ERR_UNSUPPORTED, "fused harris: bx*by must be a multiple of 32, at most 256");
@@ -296,7 +305,7 @@ imcl_status launch_harris_fused(const ConvCall& c, const imcl_variant& v, cudaSt
     const int SW = TW + 2 * PADI, SH = TH + 2 * HALO;
     if (LOAD == IMCL_LOAD_TMA && (SW > 256 || SH > 256))
         return fail(IMCL_ERR_UNSUPPORTED, "fused harris: TMA box larger than 256 in a dimension");
-    const int PH = TH + 2 * RW, PW = TW + 2 * GW::PAD;
+    const int PH = TH + 2 * RW, PW = 4 * ((TW + 2 * RW + 3) / 4);
     const int stage_bytes = round_up(SW * SH * 4, 128);
     const int nstage = LOAD == IMCL_LOAD_TMA ? 2 : 1;
     const int smem = 128 + nstage * stage_bytes + 3 * PH * PW * 4 + (18 + WK * WK) * 4;

@@ -73,8 +73,10 @@ __global__ void __launch_bounds__(256, 1)
     k_sepconv_fused(const ConvArgs a, const __grid_constant__ TapsParam<float, 2 * (2 * R + 1)> tp,
                     const __grid_constant__ CUtensorMap tmap) {
     constexpr int NT = 2 * R + 1;
-    using G = TileGeo<Tin, NT, PX>;
+    using G = TileGeo<Tin, NT, PX>;      // staging geometry (PAD)
+    using GR = TileGeo<Tin, NT, 8>;      // row pass: 8 outputs per work item, same PAD
     static_assert(PX == 4, "the t buffer is written and read as float4");
+    static_assert(G::PAD == GR::PAD, "row pass and staging must agree on the halo");
     extern __shared__ __align__(128) uint8_t smem[];
 
     const int tid = threadIdx.x, nth = blockDim.x;
@@ -158,33 +160,37 @@ __global__ void __launch_bounds__(256, 1)
             __syncthreads();
         }
 
-        // row pass: t for the SH staged rows, TW columns, PX per work item
-        const int nseg = TW / PX;
-        for (int it = tid; it < SH * nseg; it += nth) {
-            const int row = it / nseg, c0 = (it - row * nseg) * PX;
-            const int gy = gy0 + row;
-            float4 tv;
-            if (a.border == IMCL_BORDER_CONSTANT && (gy < 0 || gy >= a.H)) {
-                tv = make_float4(a.bv_f, a.bv_f, a.bv_f, a.bv_f);   // t is padded with the constant
-            } else {
-                float seg[G::SEG];
-                if constexpr (LOAD == IMCL_LOAD_GLOBAL)
-                    load_seg_global<Tin, G>(in, a.in_pitch, gy, x0 + c0 - G::PAD, a.W, a.H, a.border, bv,
-                                            a.vec_in != 0, seg);
-                else
-                    load_seg_smem<Tin, G>(st + row * SW + c0, seg);
-                float r4[PX];
+        // row pass: t for the SH staged rows and TW columns, 8 columns per work item; a
+        // thread keeps one column segment and steps down the rows
+        {
+            const int nseg = TW / 8, rstep = nth / nseg;
+            const int c0 = (tid % nseg) * 8;
+            for (int row = tid / nseg; row < SH; row += rstep) {
+                const int gy = gy0 + row;
+                float r8[8];
+                if (a.border == IMCL_BORDER_CONSTANT && (gy < 0 || gy >= a.H)) {
 #pragma unroll
-                for (int ox = 0; ox < PX; ++ox) r4[ox] = 0.f;
+                    for (int ox = 0; ox < 8; ++ox) r8[ox] = a.bv_f;   // t is padded with the constant
+                } else {
+                    float seg[GR::SEG];
+                    if constexpr (LOAD == IMCL_LOAD_GLOBAL)
+                        load_seg_global<Tin, GR>(in, a.in_pitch, gy, x0 + c0 - GR::PAD, a.W, a.H, a.border, bv,
+                                                 a.vec_in != 0, seg);
+                    else
+                        load_seg_smem<Tin, GR>(st + row * SW + c0, seg);
 #pragma unroll
-                for (int i = 0; i < NT; ++i) {
-                    const float w = rw[i];
+                    for (int ox = 0; ox < 8; ++ox) r8[ox] = 0.f;
 #pragma unroll
-                    for (int ox = 0; ox < PX; ++ox) r4[ox] = __fmaf_rn(w, seg[G::LO + ox + i], r4[ox]);
+                    for (int i = 0; i < NT; ++i) {
+                        const float w = rw[i];
+#pragma unroll
+                        for (int ox = 0; ox < 8; ++ox) r8[ox] = __fmaf_rn(w, seg[GR::LO + ox + i], r8[ox]);
+                    }
                 }
-                tv = make_float4(r4[0], r4[1], r4[2], r4[3]);
+                float* tp = tbuf + row * TW + c0;
+                *reinterpret_cast<float4*>(tp) = make_float4(r8[0], r8[1], r8[2], r8[3]);
+                *reinterpret_cast<float4*>(tp + 4) = make_float4(r8[4], r8[5], r8[6], r8[7]);
             }
-            *reinterpret_cast<float4*>(tbuf + row * TW + c0) = tv;
         }
         __syncthreads();
 
@@ -260,6 +266,8 @@ imcl_status launch_sep_fused(const ConvCall& c, const imcl_variant& v, cudaStrea
     if (bx <= 0 || by <= 0 || nth > 256 || nth % 32 != 0)
         return fail(IMCL_ERR_UNSUPPORTED, "fused sepconv: bx*by must be a multiple of 32, at most 256");
     if ((bx * PX) % G::CV != 0) return fail(IMCL_ERR_UNSUPPORTED, "fused sepconv: bx*px must be a multiple of 16 bytes");
+    if ((bx * PX) % 8 != 0 || nth % ((bx * PX) / 8) != 0)
+        return fail(IMCL_ERR_UNSUPPORTED, "fused sepconv: the row pass needs tile widths of 8 columns per thread group");
     if (std::max(1, (std::max(c.kw, c.kh) - 1) / 2) != R)
         return fail(IMCL_ERR_UNSUPPORTED, "fused sepconv: radius mismatch");
     if (c.taps_mem == IMCL_MEM_DEVICE && FILT != IMCL_FILT_SMEM)
@@ -275,7 +283,9 @@ imcl_status launch_sep_fused(const ConvCall& c, const imcl_variant& v, cudaStrea
     auto kfn = k_sepconv_fused<Tin, Tout, R, PX, PY, LOAD, FILT>;
     imcl_status st = set_smem_limit((const void*)kfn, smem);
     if (st != IMCL_OK) return st;
-    const int in_align = (LOAD == IMCL_LOAD_GLOBAL) ? G::VB * G::SZ : 16;
+    // the L1-path row pass reads GR::VB-pixel vectors straight from global memory
+    using GR = TileGeo<Tin, NT, 8>;
+    const int in_align = (LOAD == IMCL_LOAD_GLOBAL) ? GR::VB * GR::SZ : 16;
     ConvArgs a = make_conv_args(c, v, in_align, PX * (int)sizeof(Tout) > 16 ? 16 : PX * (int)sizeof(Tout));
     a.tiles_x = (c.W + TW - 1) / TW;
     a.tiles_y = (c.H + TH - 1) / TH;

@@ -300,6 +300,13 @@ def device_status(stream=None) -> int:
     return int(code.value)
 
 
+def probe_fp32(packed: bool = False, stream=None) -> float:
+    """Measured FP32 FMA throughput of the current GPU in TFLOP/s."""
+    v = ctypes.c_double(0)
+    check(lib().imagecl_probe_fp32(int(packed), ctypes.byref(v), ctypes.c_void_p(stream_handle(stream))))
+    return v.value
+
+
 def version() -> str:
     return lib().imagecl_version().decode()
 
