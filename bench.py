@@ -305,6 +305,27 @@ def extra_stencils(hbm_gbs, fp32_peak, budget):
             del x, y, ws
     del base
 
+    # the paper's own benchmark shapes (§6): 4096^2 f32 separable 5x5 with the constant
+    # border, and 8192^2 u8 non-separable 5x5 with the clamped border
+    x = torch.from_numpy(synth.uniform_f32(g, 4096, 4096)).to(dev)
+    y = torch.empty_like(x)
+    t = synth.gaussian_taps(2)
+    res = ops.tune(ops.problem(_abi.OP_SEPCONV, "f32", "f32", 5, 5, 4096, 4096, "constant"), budget_s=budget, reps=3)
+    ws = torch.empty(4096 * 4096 * 4, dtype=torch.uint8, device=dev)
+    tt = _median_ms(lambda: ops.sepconv(x, t, t, "constant", 0.0, out=y), 7, flush)
+    tp = _median_ms(lambda: ops.sepconv(x, t, t, "constant", 0.0, out=y, variant=plain, workspace=ws), 5, flush)
+    out["paper_sep5x5_4096_f32_constant"] = _entry(4096 * 4096, tt, tp, 8, 20, hbm_gbs, fp32_peak, res["variant"])
+    del x, y, ws
+    x = torch.from_numpy(synth.uniform_u8(g, SIDE, SIDE)).to(dev)
+    y = torch.empty((SIDE, SIDE), dtype=torch.int32, device=dev)
+    w5 = synth.int_filter(g, 5)
+    res = ops.tune(ops.problem(_abi.OP_CONV2D, "u8", "i32", 5, 5, SIDE, SIDE), budget_s=budget, reps=3)
+    tt = _median_ms(lambda: ops.conv2d(x, w5, out=y), 7)
+    tp = _median_ms(lambda: ops.conv2d(x, w5, out=y, variant=plain), 5)
+    out["paper_conv5x5_8192_u8_i32"] = _entry(SIDE * SIDE, tt, tp, 5, 50, hbm_gbs, fp32_peak, res["variant"],
+                                              "integer MADs: fp32_frac counts them as FMAs")
+    del x, y
+
     # Harris, 4096x4096 rectangles: forward tuned vs the two-kernel form, and the backward
     img, sx, sy, win, k = synth.workload_harris()
     x = torch.from_numpy(img).to(dev)
@@ -365,7 +386,7 @@ def extra_stencils(hbm_gbs, fp32_peak, budget):
 
 def run_ours(args):
     import torch
-    from paper_1605_06399_gb300 import _abi, ops
+    from paper_1605_06399_gb300 import _abi, ops, shard
 
     rank, world, local, pg = dist_setup(args.gpus)
     dev = torch.device("cuda", local)
@@ -451,10 +472,7 @@ def run_ours(args):
     elapsed_ms = start.elapsed_time(end)
     per_k_ms = {k: sum(ev[s][i].elapsed_time(ev[s][i + 1]) for s in range(args.steps)) / args.steps
                 for i, k in enumerate(KS)}
-    if pg:
-        t = torch.tensor([elapsed_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = shard.max_over_ranks(elapsed_ms, pg)
 
     px = SIDE * SIDE
     ms_per_step = elapsed_ms / args.steps
@@ -478,10 +496,7 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
-    if pg:
-        t = torch.tensor([e2e_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = shard.max_over_ranks(e2e_ms, pg)
     e2e_value = world * px * len(KS) / (e2e_ms / 1e3) / 1e6
 
     if rank != 0:
