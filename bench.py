@@ -220,12 +220,36 @@ def oracle_rate(img, taps_by_k, seconds, gpu_outs=None):
 
 # ----------------------------------------------------------------------------- other stencils
 
-def _median_ms(fn, reps, flush=None):
-    """Median device time of fn() over `reps` runs, each bracketed by CUDA events on the
-    current stream; `flush` (a tensor larger than L2) is rewritten before each run."""
+def _median_ms(fn, reps, flush=None, calls=8):
+    """Median device time of one fn() call.  `calls` calls are recorded in a CUDA graph
+    (so host-side argument marshalling is not timed), the graph is replayed `reps` times
+    between CUDA events on the current stream, and each replay is divided by `calls`.
+    `flush` (a buffer larger than L2) is rewritten before each replay, outside the events,
+    and then one call is recorded per replay so that every timed call starts cold."""
     import torch
+    if flush is not None and calls > 1:
+        calls = 1
     stream = torch.cuda.current_stream()
     fn()
+    torch.cuda.synchronize()
+    if calls == 0:   # fn itself replays a CUDA graph: time it directly
+        ts = []
+        for r in range(reps):
+            if flush is not None:
+                flush.fill_(float(r))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ts.sort()
+        return ts[len(ts) // 2]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(calls):
+            fn()
+    g.replay()
     torch.cuda.synchronize()
     ts = []
     for r in range(reps):
@@ -233,11 +257,12 @@ def _median_ms(fn, reps, flush=None):
             flush.fill_(float(r))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        fn()
+        g.replay()
         e1.record(stream)
         e1.synchronize()
-        ts.append(e0.elapsed_time(e1))
+        ts.append(e0.elapsed_time(e1) / calls)
     ts.sort()
+    del g
     return ts[len(ts) // 2]
 
 
@@ -271,18 +296,11 @@ def extra_stencils(hbm_gbs, fp32_peak, budget):
     x = torch.from_numpy(img).to(dev)
     y = torch.empty((512, 512), dtype=torch.int32, device=dev)
     res = ops.tune(ops.problem(_abi.OP_CONV2D, "u8", "i32", 3, 3, 512, 512), budget_s=budget, reps=5)
-    times = {}
-    for name, v in (("tuned", None), ("plain", plain)):
-        ops.conv2d(x, taps, out=y, variant=v)
-        torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
-            for _ in range(100):
-                ops.conv2d(x, taps, out=y, variant=v)
-        times[name] = _median_ms(g.replay, 7) / 100
+    times = {name: _median_ms(lambda v=v: ops.conv2d(x, taps, out=y, variant=v), 7, calls=100)
+             for name, v in (("tuned", None), ("plain", plain))}
     out["conv3x3_512_u8_i32"] = _entry(512 * 512, times["tuned"], times["plain"], 5, 18, hbm_gbs, fp32_peak,
                                        res["variant"], "L2-resident, launch-latency bound: % roofline not "
-                                       "meaningful; per-launch time from a 100-launch CUDA graph")
+                                       "meaningful; per-launch time from 100 launches in a CUDA graph")
     del x, y
 
     # separable Gaussian, 8192x8192, radius R, storage types
@@ -338,7 +356,7 @@ def extra_stencils(hbm_gbs, fp32_peak, budget):
     flops_fwd = 2 * 18 * (4100 * 4100) / px + 3 + 2 * 3 * 25 + 7
     out["harris_4096_fwd"] = _entry(px, tt, tp, 8, flops_fwd, hbm_gbs, fp32_peak, res["variant"])
     gR = torch.randn(4096, 4096, device=dev)
-    tb = _median_ms(lambda: ops.harris_backward(gR, x, sx, sy, win, k), 5)
+    tb = _median_ms(lambda: ops.harris_backward(gR, x, sx, sy, win, k), 5, calls=2)
     out["harris_4096_bwd"] = _entry(px, tb, None, 8, 0, hbm_gbs, fp32_peak,
                                     note="adjoint of the fused forward: image, Sobel and window gradients")
     del x, y, ws, gR
@@ -355,8 +373,8 @@ def extra_stencils(hbm_gbs, fp32_peak, budget):
         bitems.append(d)
     b = Batch(bitems, tune_budget_s=budget)
     info = b.info()
-    tf = _median_ms(b.run, 7)
-    tbw = _median_ms(b.backward, 5)
+    tf = _median_ms(b.run, 7, calls=0)
+    tbw = _median_ms(b.backward, 5, calls=0)
 
     def plain_loop():
         for d in bitems:
@@ -364,7 +382,7 @@ def extra_stencils(hbm_gbs, fp32_peak, budget):
                 ops.conv2d(d["x"], d["taps"], out_dtype=torch.float16, variant=plain)
             else:
                 ops.sepconv(d["x"], d["taps"], d["col_taps"], out_dtype=torch.float16, variant=plain)
-    tpl = _median_ms(plain_loop, 3)
+    tpl = _median_ms(plain_loop, 3, calls=1)
     bytes_total = sum(it.width * it.height * 4 for it in items)
     flops_total = sum(it.width * it.height * (2 * it.k * it.k if it.op == "conv" else 4 * it.k) for it in items)
     # per-image roofline time: sum of max(bytes / BW, flops / P_fp32)

@@ -72,7 +72,10 @@ typedef struct {
 typedef enum { IMCL_KIND_PLAIN = 0, IMCL_KIND_TILED = 1 } imcl_kind;
 typedef enum { IMCL_LOAD_GLOBAL = 0, IMCL_LOAD_SMEM = 1, IMCL_LOAD_TMA = 2 } imcl_load;
 typedef enum { IMCL_FILT_PARAM = 0, IMCL_FILT_SMEM = 1 } imcl_filt;
-typedef enum { IMCL_MAP_BLOCKED = 0, IMCL_MAP_INTERLEAVED = 1 } imcl_map;
+/* IMCL_MAP_REGISTER (sepconv only): the row pass result stays in each thread's registers
+ * (the vertical halo rows are computed by every thread that needs them) instead of going
+ * through a shared buffer -- where the intermediate of the fused pair lives. */
+typedef enum { IMCL_MAP_BLOCKED = 0, IMCL_MAP_INTERLEAVED = 1, IMCL_MAP_REGISTER = 2 } imcl_map;
 
 typedef struct {
     int32_t kind;       /* imcl_kind.  PLAIN: the untuned kernel (one pixel per thread,
@@ -82,7 +85,8 @@ typedef struct {
     int32_t load;       /* imcl_load: L1/texture-path loads, a cooperative shared-memory
                            halo tile, or a TMA-staged shared-memory halo tile          */
     int32_t filt;       /* imcl_filt: taps in the constant bank or in shared memory   */
-    int32_t map;        /* imcl_map: a thread's rows contiguous or interleaved by `by` */
+    int32_t map;        /* imcl_map: a thread's rows contiguous or interleaved by `by`;
+                           sepconv: shared-buffer or register intermediate             */
     int32_t unroll;     /* 1: taps fully unrolled (compile-time K); 0: rolled loops   */
     int32_t persistent; /* 1: one CTA per SM slot looping over tiles; 0: one tile each */
 } imcl_variant;

@@ -28,7 +28,7 @@ OP_CONV2D, OP_SEPCONV, OP_HARRIS = 0, 1, 2
 KIND_PLAIN, KIND_TILED = 0, 1
 LOAD_GLOBAL, LOAD_SMEM, LOAD_TMA = 0, 1, 2
 FILT_PARAM, FILT_SMEM = 0, 1
-MAP_BLOCKED, MAP_INTERLEAVED = 0, 1
+MAP_BLOCKED, MAP_INTERLEAVED, MAP_REGISTER = 0, 1, 2
 
 
 class Image(ctypes.Structure):

@@ -16,9 +16,23 @@ namespace imcl {
 constexpr int TMA = IMCL_LOAD_TMA, SMEM = IMCL_LOAD_SMEM, GLB = IMCL_LOAD_GLOBAL;
 constexpr int PARAM = IMCL_FILT_PARAM, SFILT = IMCL_FILT_SMEM;
 
+// register-intermediate forms (MODE 1) for the small radii
+template <typename Tin, typename Tout, int R>
+static void add_register_forms(std::vector<ConvEntry>& t) {
+    if constexpr (R <= 8) {
+        t.push_back(sep_entry<Tin, Tout, R, 4, 8, TMA, PARAM, 1>(32, 8, 1));
+        t.push_back(sep_entry<Tin, Tout, R, 4, 8, TMA, SFILT, 1>(32, 8, 1));
+    }
+    if constexpr (R <= 4) {
+        t.push_back(sep_entry<Tin, Tout, R, 4, 4, TMA, PARAM, 1>(16, 16, 1));
+        t.push_back(sep_entry<Tin, Tout, R, 4, 16, TMA, PARAM, 1>(32, 4, 1));
+    }
+}
+
 template <int R>
 static void add_radius(std::vector<ConvEntry>& t) {
 #if IMCL_SEP_GROUP == 0
+    add_register_forms<float, float, R>(t);
     t.push_back(sep_entry<float, float, R, 4, 8, TMA, PARAM>(32, 8, 1));
     t.push_back(sep_entry<float, float, R, 4, 4, TMA, PARAM>(32, 8, 1));
     t.push_back(sep_entry<float, float, R, 4, 8, SMEM, PARAM>(32, 8, 0));
@@ -26,6 +40,8 @@ static void add_radius(std::vector<ConvEntry>& t) {
     t.push_back(sep_entry<float, float, R, 4, 8, TMA, SFILT>(32, 8, 1));
     t.push_back(sep_entry<float, float, R, 4, 8, GLB, SFILT>(32, 8, 0));
 #elif IMCL_SEP_GROUP == 1
+    add_register_forms<__half, float, R>(t);
+    add_register_forms<__half, __half, R>(t);
     t.push_back(sep_entry<__half, float, R, 4, 8, TMA, PARAM>(32, 8, 1));
     t.push_back(sep_entry<__half, float, R, 4, 8, TMA, SFILT>(32, 8, 1));
     t.push_back(sep_entry<__half, float, R, 4, 8, GLB, PARAM>(32, 8, 0));
@@ -35,6 +51,8 @@ static void add_radius(std::vector<ConvEntry>& t) {
     t.push_back(sep_entry<__half, __half, R, 4, 8, GLB, PARAM>(32, 8, 0));
     t.push_back(sep_entry<__half, __half, R, 4, 8, GLB, SFILT>(32, 8, 0));
 #else
+    add_register_forms<__nv_bfloat16, float, R>(t);
+    add_register_forms<__nv_bfloat16, __nv_bfloat16, R>(t);
     t.push_back(sep_entry<__nv_bfloat16, float, R, 4, 8, TMA, PARAM>(32, 8, 1));
     t.push_back(sep_entry<__nv_bfloat16, float, R, 4, 8, TMA, SFILT>(32, 8, 1));
     t.push_back(sep_entry<__nv_bfloat16, float, R, 4, 8, GLB, PARAM>(32, 8, 0));

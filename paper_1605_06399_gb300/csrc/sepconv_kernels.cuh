@@ -68,8 +68,12 @@ __global__ void __launch_bounds__(256)
 }
 
 // ------------------------------------------------------------------ fused
-template <typename Tin, typename Tout, int R, int PX, int PY, int LOAD, int FILT>
-__global__ void __launch_bounds__(256, 1)
+// MODE 0: the row pass result goes through a shared f32 buffer (rows computed once);
+// MODE 1: each thread keeps the row pass of its own PY + 2R input rows in registers
+// (halo rows computed by the threads above and below as well, no buffer, one barrier
+// less), for small radii.
+template <typename Tin, typename Tout, int R, int PX, int PY, int LOAD, int FILT, int MODE>
+__global__ void __launch_bounds__(256, MODE == 1 ? 3 : 1)
     k_sepconv_fused(const ConvArgs a, const __grid_constant__ TapsParam<float, 2 * (2 * R + 1)> tp,
                     const __grid_constant__ CUtensorMap tmap) {
     constexpr int NT = 2 * R + 1;
@@ -87,7 +91,7 @@ __global__ void __launch_bounds__(256, 1)
     constexpr int kStages = LOAD == IMCL_LOAD_TMA ? 2 : (LOAD == IMCL_LOAD_SMEM ? 1 : 0);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     float* tbuf = reinterpret_cast<float*>(smem + 128 + kStages * stage_bytes);
-    float* wsm = tbuf + SH * TW;
+    float* wsm = tbuf + (MODE == 0 ? SH * TW : 0);
 
     const Tin* in = static_cast<const Tin*>(a.in);
     Tout* out = static_cast<Tout*>(a.out);
@@ -160,42 +164,7 @@ __global__ void __launch_bounds__(256, 1)
             __syncthreads();
         }
 
-        // row pass: t for the SH staged rows and TW columns, 8 columns per work item; a
-        // thread keeps one column segment and steps down the rows
-        {
-            const int nseg = TW / 8, rstep = nth / nseg;
-            const int c0 = (tid % nseg) * 8;
-            for (int row = tid / nseg; row < SH; row += rstep) {
-                const int gy = gy0 + row;
-                float r8[8];
-                if (a.border == IMCL_BORDER_CONSTANT && (gy < 0 || gy >= a.H)) {
-#pragma unroll
-                    for (int ox = 0; ox < 8; ++ox) r8[ox] = a.bv_f;   // t is padded with the constant
-                } else {
-                    float seg[GR::SEG];
-                    if constexpr (LOAD == IMCL_LOAD_GLOBAL)
-                        load_seg_global<Tin, GR>(in, a.in_pitch, gy, x0 + c0 - GR::PAD, a.W, a.H, a.border, bv,
-                                                 a.vec_in != 0, seg);
-                    else
-                        load_seg_smem<Tin, GR>(st + row * SW + c0, seg);
-#pragma unroll
-                    for (int ox = 0; ox < 8; ++ox) r8[ox] = 0.f;
-#pragma unroll
-                    for (int i = 0; i < NT; ++i) {
-                        const float w = rw[i];
-#pragma unroll
-                        for (int ox = 0; ox < 8; ++ox) r8[ox] = __fmaf_rn(w, seg[GR::LO + ox + i], r8[ox]);
-                    }
-                }
-                float* tp = tbuf + row * TW + c0;
-                *reinterpret_cast<float4*>(tp) = make_float4(r8[0], r8[1], r8[2], r8[3]);
-                *reinterpret_cast<float4*>(tp + 4) = make_float4(r8[4], r8[5], r8[6], r8[7]);
-            }
-        }
-        __syncthreads();
-
-        // column pass: PX x PY block per thread, sliding down the t buffer
-        {
+        if constexpr (MODE == 1) {
             const int tx = tid % bx, ty = tid / bx;
             float acc[PY][PX];
 #pragma unroll
@@ -204,15 +173,32 @@ __global__ void __launch_bounds__(256, 1)
                 for (int ox = 0; ox < PX; ++ox) acc[oy][ox] = 0.f;
 #pragma unroll
             for (int yy = 0; yy < PY + 2 * R; ++yy) {
-                const float4 v = *reinterpret_cast<const float4*>(tbuf + (ty * PY + yy) * TW + tx * PX);
-                const float tv[4] = {v.x, v.y, v.z, v.w};
+                const int row = ty * PY + yy;
+                const int gy = gy0 + row;
+                float t4[PX];
+                if (a.border == IMCL_BORDER_CONSTANT && (gy < 0 || gy >= a.H)) {
+#pragma unroll
+                    for (int ox = 0; ox < PX; ++ox) t4[ox] = a.bv_f;   // t is padded with the constant
+                } else {
+                    float seg[G::SEG];
+                    if constexpr (LOAD == IMCL_LOAD_GLOBAL)
+                        load_seg_global<Tin, G>(in, a.in_pitch, gy, x0 + tx * PX - G::PAD, a.W, a.H, a.border, bv,
+                                                a.vec_in != 0, seg);
+                    else
+                        load_seg_smem<Tin, G>(st + row * SW + tx * PX, seg);
+#pragma unroll
+                    for (int ox = 0; ox < PX; ++ox) t4[ox] = 0.f;
+#pragma unroll
+                    for (int i = 0; i < NT; ++i)
+#pragma unroll
+                        for (int ox = 0; ox < PX; ++ox) t4[ox] = __fmaf_rn(rw[i], seg[G::LO + ox + i], t4[ox]);
+                }
 #pragma unroll
                 for (int oy = 0; oy < PY; ++oy) {
                     const int j = yy - oy;
                     if (j >= 0 && j < NT) {
-                        const float w = cw[j];
 #pragma unroll
-                        for (int ox = 0; ox < PX; ++ox) acc[oy][ox] = __fmaf_rn(w, tv[ox], acc[oy][ox]);
+                        for (int ox = 0; ox < PX; ++ox) acc[oy][ox] = __fmaf_rn(cw[j], t4[ox], acc[oy][ox]);
                     }
                 }
             }
@@ -220,6 +206,68 @@ __global__ void __launch_bounds__(256, 1)
             for (int oy = 0; oy < PY; ++oy)
                 store_block_row<Tout, PX>(out, a.out_pitch, x0 + tx * PX, y0 + ty * PY + oy, a.W, a.H,
                                           a.vec_out != 0, acc[oy]);
+        } else {
+            // row pass: t for the SH staged rows and TW columns, 8 columns per work item; a
+            // thread keeps one column segment and steps down the rows
+            {
+                const int nseg = TW / 8, rstep = nth / nseg;
+                const int c0 = (tid % nseg) * 8;
+                for (int row = tid / nseg; row < SH; row += rstep) {
+                    const int gy = gy0 + row;
+                    float r8[8];
+                    if (a.border == IMCL_BORDER_CONSTANT && (gy < 0 || gy >= a.H)) {
+    #pragma unroll
+                        for (int ox = 0; ox < 8; ++ox) r8[ox] = a.bv_f;   // t is padded with the constant
+                    } else {
+                        float seg[GR::SEG];
+                        if constexpr (LOAD == IMCL_LOAD_GLOBAL)
+                            load_seg_global<Tin, GR>(in, a.in_pitch, gy, x0 + c0 - GR::PAD, a.W, a.H, a.border, bv,
+                                                     a.vec_in != 0, seg);
+                        else
+                            load_seg_smem<Tin, GR>(st + row * SW + c0, seg);
+    #pragma unroll
+                        for (int ox = 0; ox < 8; ++ox) r8[ox] = 0.f;
+    #pragma unroll
+                        for (int i = 0; i < NT; ++i) {
+                            const float w = rw[i];
+    #pragma unroll
+                            for (int ox = 0; ox < 8; ++ox) r8[ox] = __fmaf_rn(w, seg[GR::LO + ox + i], r8[ox]);
+                        }
+                    }
+                    float* tp = tbuf + row * TW + c0;
+                    *reinterpret_cast<float4*>(tp) = make_float4(r8[0], r8[1], r8[2], r8[3]);
+                    *reinterpret_cast<float4*>(tp + 4) = make_float4(r8[4], r8[5], r8[6], r8[7]);
+                }
+            }
+            __syncthreads();
+
+            // column pass: PX x PY block per thread, sliding down the t buffer
+            {
+                const int tx = tid % bx, ty = tid / bx;
+                float acc[PY][PX];
+    #pragma unroll
+                for (int oy = 0; oy < PY; ++oy)
+    #pragma unroll
+                    for (int ox = 0; ox < PX; ++ox) acc[oy][ox] = 0.f;
+    #pragma unroll
+                for (int yy = 0; yy < PY + 2 * R; ++yy) {
+                    const float4 v = *reinterpret_cast<const float4*>(tbuf + (ty * PY + yy) * TW + tx * PX);
+                    const float tv[4] = {v.x, v.y, v.z, v.w};
+    #pragma unroll
+                    for (int oy = 0; oy < PY; ++oy) {
+                        const int j = yy - oy;
+                        if (j >= 0 && j < NT) {
+                            const float w = cw[j];
+    #pragma unroll
+                            for (int ox = 0; ox < PX; ++ox) acc[oy][ox] = __fmaf_rn(w, tv[ox], acc[oy][ox]);
+                        }
+                    }
+                }
+    #pragma unroll
+                for (int oy = 0; oy < PY; ++oy)
+                    store_block_row<Tout, PX>(out, a.out_pitch, x0 + tx * PX, y0 + ty * PY + oy, a.W, a.H,
+                                              a.vec_out != 0, acc[oy]);
+            }
         }
         __syncthreads();   // t buffer and stage s may be refilled
         if constexpr (LOAD == IMCL_LOAD_TMA) s ^= 1;
@@ -258,7 +306,7 @@ imcl_status launch_sep_plain(const ConvCall& c, const imcl_variant& v, cudaStrea
     return cuda_fail(cudaGetLastError(), "sepconv plain launch");
 }
 
-template <typename Tin, typename Tout, int R, int PX, int PY, int LOAD, int FILT>
+template <typename Tin, typename Tout, int R, int PX, int PY, int LOAD, int FILT, int MODE>
 imcl_status launch_sep_fused(const ConvCall& c, const imcl_variant& v, cudaStream_t s) {
     constexpr int NT = 2 * R + 1;
     using G = TileGeo<Tin, NT, PX>;
@@ -278,9 +326,9 @@ imcl_status launch_sep_fused(const ConvCall& c, const imcl_variant& v, cudaStrea
         return fail(IMCL_ERR_UNSUPPORTED, "fused sepconv: TMA box larger than 256 in a dimension");
     const int stage_bytes = round_up(SW * SH * G::SZ, 128);
     const int nstage = LOAD == IMCL_LOAD_TMA ? 2 : (LOAD == IMCL_LOAD_SMEM ? 1 : 0);
-    const int smem = 128 + nstage * stage_bytes + SH * TW * 4 + 2 * NT * 4;
+    const int smem = 128 + nstage * stage_bytes + (MODE == 0 ? SH * TW * 4 : 0) + 2 * NT * 4;
     if (smem > c.dev->max_smem_optin) return fail(IMCL_ERR_UNSUPPORTED, "fused sepconv: tile too large for shared memory");
-    auto kfn = k_sepconv_fused<Tin, Tout, R, PX, PY, LOAD, FILT>;
+    auto kfn = k_sepconv_fused<Tin, Tout, R, PX, PY, LOAD, FILT, MODE>;
     imcl_status st = set_smem_limit((const void*)kfn, smem);
     if (st != IMCL_OK) return st;
     // the L1-path row pass reads GR::VB-pixel vectors straight from global memory
@@ -311,7 +359,7 @@ imcl_status launch_sep_fused(const ConvCall& c, const imcl_variant& v, cudaStrea
     return cuda_fail(cudaGetLastError(), "sepconv fused launch");
 }
 
-template <typename Tin, typename Tout, int R, int PX, int PY, int LOAD, int FILT>
+template <typename Tin, typename Tout, int R, int PX, int PY, int LOAD, int FILT, int MODE = 0>
 inline ConvEntry sep_entry(int bx, int by, int persistent) {
     imcl_variant v{};
     v.kind = IMCL_KIND_TILED;
@@ -321,10 +369,11 @@ inline ConvEntry sep_entry(int bx, int by, int persistent) {
     v.py = PY;
     v.load = LOAD;
     v.filt = FILT;
-    v.map = IMCL_MAP_BLOCKED;
+    v.map = MODE == 1 ? IMCL_MAP_REGISTER : IMCL_MAP_BLOCKED;
     v.unroll = 1;
     v.persistent = persistent;
-    return ConvEntry{DtypeOf<Tin>::v, DtypeOf<Tout>::v, R, v, &launch_sep_fused<Tin, Tout, R, PX, PY, LOAD, FILT>};
+    return ConvEntry{DtypeOf<Tin>::v, DtypeOf<Tout>::v, R, v,
+                     &launch_sep_fused<Tin, Tout, R, PX, PY, LOAD, FILT, MODE>};
 }
 
 }  // namespace imcl
