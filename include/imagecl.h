@@ -76,6 +76,11 @@ typedef enum { IMCL_FILT_PARAM = 0, IMCL_FILT_SMEM = 1 } imcl_filt;
  * (the vertical halo rows are computed by every thread that needs them) instead of going
  * through a shared buffer -- where the intermediate of the fused pair lives. */
 typedef enum { IMCL_MAP_BLOCKED = 0, IMCL_MAP_INTERLEAVED = 1, IMCL_MAP_REGISTER = 2 } imcl_map;
+/* Loop form of the tap loops.  PACKED (sepconv only) is unrolled like FULL, with each
+ * multiply-add instruction doing two adjacent output pixels (f32x2 FMA): the
+ * vectorisation that the paper leaves to the OpenCL runtime, as a tuning knob.  It gives
+ * the same bits as FULL. */
+typedef enum { IMCL_UNROLL_NONE = 0, IMCL_UNROLL_FULL = 1, IMCL_UNROLL_PACKED = 2 } imcl_unroll;
 
 typedef struct {
     int32_t kind;       /* imcl_kind.  PLAIN: the untuned kernel (one pixel per thread,
@@ -87,7 +92,8 @@ typedef struct {
     int32_t filt;       /* imcl_filt: taps in the constant bank or in shared memory   */
     int32_t map;        /* imcl_map: a thread's rows contiguous or interleaved by `by`;
                            sepconv: shared-buffer or register intermediate             */
-    int32_t unroll;     /* 1: taps fully unrolled (compile-time K); 0: rolled loops   */
+    int32_t unroll;     /* imcl_unroll: rolled loops, taps fully unrolled (compile-time
+                           K), or fully unrolled with packed f32x2 multiply-adds       */
     int32_t persistent; /* 1: one CTA per SM slot looping over tiles; 0: one tile each */
 } imcl_variant;
 

@@ -24,11 +24,12 @@ U8, I32, F32, F16, BF16 = range(5)
 BORDER_CLAMP, BORDER_CONSTANT = 0, 1
 MEM_HOST, MEM_DEVICE = 0, 1
 OP_CONV2D, OP_SEPCONV, OP_HARRIS = 0, 1, 2
-# imcl_kind / imcl_load / imcl_filt / imcl_map
+# imcl_kind / imcl_load / imcl_filt / imcl_map / imcl_unroll
 KIND_PLAIN, KIND_TILED = 0, 1
 LOAD_GLOBAL, LOAD_SMEM, LOAD_TMA = 0, 1, 2
 FILT_PARAM, FILT_SMEM = 0, 1
 MAP_BLOCKED, MAP_INTERLEAVED, MAP_REGISTER = 0, 1, 2
+UNROLL_NONE, UNROLL_FULL, UNROLL_PACKED = 0, 1, 2
 
 
 class Image(ctypes.Structure):
@@ -49,7 +50,7 @@ class Variant(ctypes.Structure):
     def from_dict(cls, d: dict) -> "Variant":
         v = cls()
         for n in VARIANT_FIELDS:
-            setattr(v, n, int(d.get(n, 0)))
+            setattr(v, n, int(d.get(n, UNROLL_FULL if n == "unroll" else 0)))
         return v
 
     def __repr__(self):

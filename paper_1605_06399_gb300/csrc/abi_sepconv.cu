@@ -31,7 +31,7 @@ static const ConvEntry* sep_find(const ConvCall& c, const imcl_variant& v) {
     for (const ConvEntry* e : sep_entries_for(c.in_dtype, c.out_dtype, c.kw, c.kh, c.taps_mem)) {
         if (v.kind == IMCL_KIND_PLAIN && e->v.kind == IMCL_KIND_PLAIN) return e;
         if (e->v.kind == v.kind && e->v.px == v.px && e->v.py == v.py && e->v.load == v.load &&
-            e->v.filt == v.filt && e->v.map == v.map)
+            e->v.filt == v.filt && e->v.map == v.map && e->v.unroll == v.unroll)
             return e;
     }
     return nullptr;

@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "imagecl.h"
 
 namespace imcl {
@@ -62,16 +64,53 @@ __device__ __forceinline__ int32_t mad(int32_t a, int32_t b, int32_t c) {
     return (int32_t)((uint32_t)a * (uint32_t)b + (uint32_t)c);
 }
 
+// Two f32 multiply-adds in one packed f32x2 instruction; each lane is rounded exactly
+// like __fmaf_rn, so a packed kernel gives the same bits as its scalar form.
+__device__ __forceinline__ float2 mad2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
 
 // ------------------------------------------------------------------ vector loads
+// Widen the two 16-bit pixels of a 32-bit word (element 0 in the low half) to f32.
+// bf16 is the upper half of an f32, so widening is a shift or a mask (exact).
+__device__ __forceinline__ void unpack2(__nv_bfloat16, uint32_t w, float* d) {
+    d[0] = __uint_as_float(w << 16);
+    d[1] = __uint_as_float(w & 0xffff0000u);
+}
+__device__ __forceinline__ void unpack2(__half, uint32_t w, float* d) {
+    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w));
+    d[0] = f.x;
+    d[1] = f.y;
+}
+
+// N pixels held in N/2 words (16-bit types widened to f32).
+template <typename T, int N, typename A>
+__device__ __forceinline__ void unpack_words(const uint32_t* w, A* dst) {
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) unpack2(T(), w[k], dst + 2 * k);
+}
+
+template <typename T, typename A>
+constexpr bool kWordUnpack = sizeof(T) == 2 && std::is_same<A, float>::value;
+
 // Load N consecutive pixels (N * sizeof(T) in {2, 4, 8, 16} bytes, naturally aligned)
 // and convert them to the accumulation type.
 template <typename T, int N, typename A>
 __device__ __forceinline__ void load_vec(const T* p, A* dst) {
     constexpr int B = N * (int)sizeof(T);
     static_assert(B == 2 || B == 4 || B == 8 || B == 16 || B == 1, "vector width");
-    if constexpr (B == 16) {
+    if constexpr (kWordUnpack<T, A> && B == 16) {
+        const uint4 v = *reinterpret_cast<const uint4*>(p);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        unpack_words<T, N>(w, dst);
+    } else if constexpr (kWordUnpack<T, A> && B == 8) {
+        const uint2 v = *reinterpret_cast<const uint2*>(p);
+        const uint32_t w[2] = {v.x, v.y};
+        unpack_words<T, N>(w, dst);
+    } else if constexpr (kWordUnpack<T, A> && B == 4) {
+        const uint32_t w = *reinterpret_cast<const uint32_t*>(p);
+        unpack_words<T, N>(&w, dst);
+    } else if constexpr (B == 16) {
         uint4 v = *reinterpret_cast<const uint4*>(p);
         const T* e = reinterpret_cast<const T*>(&v);
 #pragma unroll
@@ -110,7 +149,18 @@ template <> __device__ __forceinline__ __nv_bfloat16 ldg<__nv_bfloat16>(const __
 template <typename T, int N, typename A>
 __device__ __forceinline__ void ldg_vec(const T* p, A* dst) {
     constexpr int B = N * (int)sizeof(T);
-    if constexpr (B == 16) {
+    if constexpr (kWordUnpack<T, A> && B == 16) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        unpack_words<T, N>(w, dst);
+    } else if constexpr (kWordUnpack<T, A> && B == 8) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+        const uint32_t w[2] = {v.x, v.y};
+        unpack_words<T, N>(w, dst);
+    } else if constexpr (kWordUnpack<T, A> && B == 4) {
+        const uint32_t w = __ldg(reinterpret_cast<const unsigned int*>(p));
+        unpack_words<T, N>(&w, dst);
+    } else if constexpr (B == 16) {
         uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
         const T* e = reinterpret_cast<const T*>(&v);
 #pragma unroll

@@ -15,6 +15,7 @@ namespace imcl {
 
 constexpr int TMA = IMCL_LOAD_TMA, SMEM = IMCL_LOAD_SMEM, GLB = IMCL_LOAD_GLOBAL;
 constexpr int PARAM = IMCL_FILT_PARAM, SFILT = IMCL_FILT_SMEM;
+constexpr int PK = IMCL_UNROLL_PACKED;
 
 // register-intermediate forms (MODE 1) for the small radii
 template <typename Tin, typename Tout, int R>
@@ -22,11 +23,20 @@ static void add_register_forms(std::vector<ConvEntry>& t) {
     if constexpr (R <= 8) {
         t.push_back(sep_entry<Tin, Tout, R, 4, 8, TMA, PARAM, 1>(32, 8, 1));
         t.push_back(sep_entry<Tin, Tout, R, 4, 8, TMA, SFILT, 1>(32, 8, 1));
+        t.push_back(sep_entry<Tin, Tout, R, 4, 8, TMA, PARAM, 1, PK>(32, 8, 1));
     }
     if constexpr (R <= 4) {
         t.push_back(sep_entry<Tin, Tout, R, 4, 4, TMA, PARAM, 1>(16, 16, 1));
         t.push_back(sep_entry<Tin, Tout, R, 4, 16, TMA, PARAM, 1>(32, 4, 1));
+        t.push_back(sep_entry<Tin, Tout, R, 4, 16, TMA, PARAM, 1, PK>(32, 4, 1));
     }
+}
+
+// packed f32x2 forms of the shared-buffer kernel
+template <typename Tin, typename Tout, int R>
+static void add_packed_forms(std::vector<ConvEntry>& t) {
+    t.push_back(sep_entry<Tin, Tout, R, 4, 8, TMA, PARAM, 0, PK>(32, 8, 1));
+    t.push_back(sep_entry<Tin, Tout, R, 4, 8, TMA, SFILT, 0, PK>(32, 8, 1));
 }
 
 template <int R>
@@ -39,6 +49,7 @@ static void add_radius(std::vector<ConvEntry>& t) {
     t.push_back(sep_entry<float, float, R, 4, 8, GLB, PARAM>(32, 8, 0));
     t.push_back(sep_entry<float, float, R, 4, 8, TMA, SFILT>(32, 8, 1));
     t.push_back(sep_entry<float, float, R, 4, 8, GLB, SFILT>(32, 8, 0));
+    add_packed_forms<float, float, R>(t);
 #elif IMCL_SEP_GROUP == 1
     add_register_forms<__half, float, R>(t);
     add_register_forms<__half, __half, R>(t);
@@ -50,6 +61,8 @@ static void add_radius(std::vector<ConvEntry>& t) {
     t.push_back(sep_entry<__half, __half, R, 4, 8, TMA, SFILT>(32, 8, 1));
     t.push_back(sep_entry<__half, __half, R, 4, 8, GLB, PARAM>(32, 8, 0));
     t.push_back(sep_entry<__half, __half, R, 4, 8, GLB, SFILT>(32, 8, 0));
+    add_packed_forms<__half, float, R>(t);
+    add_packed_forms<__half, __half, R>(t);
 #else
     add_register_forms<__nv_bfloat16, float, R>(t);
     add_register_forms<__nv_bfloat16, __nv_bfloat16, R>(t);
@@ -61,6 +74,8 @@ static void add_radius(std::vector<ConvEntry>& t) {
     t.push_back(sep_entry<__nv_bfloat16, __nv_bfloat16, R, 4, 8, TMA, SFILT>(32, 8, 1));
     t.push_back(sep_entry<__nv_bfloat16, __nv_bfloat16, R, 4, 8, GLB, PARAM>(32, 8, 0));
     t.push_back(sep_entry<__nv_bfloat16, __nv_bfloat16, R, 4, 8, GLB, SFILT>(32, 8, 0));
+    add_packed_forms<__nv_bfloat16, float, R>(t);
+    add_packed_forms<__nv_bfloat16, __nv_bfloat16, R>(t);
 #endif
 }
 

@@ -14,7 +14,8 @@
 //    shared memory, then the column pass from that buffer, and writes the tile once:
 //    one HBM read and one write per pixel.
 // Row and column tap counts may differ: both are zero-padded (exactly neutral) to the
-// kernel's radius R = max(rr, rc).
+// kernel's radius R = max(rr, rc).  The UNROLL_PACKED form does both passes with f32x2
+// FMAs over adjacent column pairs.
 #pragma once
 
 #include "tile_common.cuh"
@@ -68,13 +69,65 @@ __global__ void __launch_bounds__(256)
 }
 
 // ------------------------------------------------------------------ fused
+// t[ox] = sum_i w[i] * seg[LO + ox + i] for ox < N, as scalar FMAs or as packed f32x2
+// FMAs over the column pairs (2p, 2p + 1); each lane keeps the scalar operation order.
+// The packed form takes its taps duplicated, (w, w) per tap.
+template <int N, int NT, int LO, int UNR, typename W>
+__device__ __forceinline__ void row_taps(const float* seg, const W* w, float* t) {
+    if constexpr (UNR == IMCL_UNROLL_PACKED) {
+        static_assert(N % 2 == 0, "packed rows need an even width");
+        float2 sp[N + NT - 2];
+#pragma unroll
+        for (int k = 0; k < N + NT - 2; ++k) sp[k] = make_float2(seg[LO + k], seg[LO + k + 1]);
+        float2 t2[N / 2];
+#pragma unroll
+        for (int p = 0; p < N / 2; ++p) t2[p] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < NT; ++i) {
+#pragma unroll
+            for (int p = 0; p < N / 2; ++p) t2[p] = mad2(w[i], sp[2 * p + i], t2[p]);
+        }
+#pragma unroll
+        for (int p = 0; p < N / 2; ++p) {
+            t[2 * p] = t2[p].x;
+            t[2 * p + 1] = t2[p].y;
+        }
+    } else {
+#pragma unroll
+        for (int ox = 0; ox < N; ++ox) t[ox] = 0.f;
+#pragma unroll
+        for (int i = 0; i < NT; ++i) {
+            const float wi = w[i];
+#pragma unroll
+            for (int ox = 0; ox < N; ++ox) t[ox] = __fmaf_rn(wi, seg[LO + ox + i], t[ox]);
+        }
+    }
+}
+
+// acc[ox] += w * t[ox] for ox < N (scalar, or packed over column pairs with w = (w, w)).
+template <int N, int UNR, typename W>
+__device__ __forceinline__ void axpy_row(const W w, const float* t, float* acc) {
+    if constexpr (UNR == IMCL_UNROLL_PACKED) {
+        const float2 w2 = w;
+#pragma unroll
+        for (int p = 0; p < N / 2; ++p) {
+            const float2 r = mad2(w2, make_float2(t[2 * p], t[2 * p + 1]), make_float2(acc[2 * p], acc[2 * p + 1]));
+            acc[2 * p] = r.x;
+            acc[2 * p + 1] = r.y;
+        }
+    } else {
+#pragma unroll
+        for (int ox = 0; ox < N; ++ox) acc[ox] = __fmaf_rn(w, t[ox], acc[ox]);
+    }
+}
+
 // MODE 0: the row pass result goes through a shared f32 buffer (rows computed once);
 // MODE 1: each thread keeps the row pass of its own PY + 2R input rows in registers
 // (halo rows computed by the threads above and below as well, no buffer, one barrier
 // less), for small radii.
-template <typename Tin, typename Tout, int R, int PX, int PY, int LOAD, int FILT, int MODE>
+template <typename Tin, typename Tout, int R, int PX, int PY, int LOAD, int FILT, int MODE, int UNR>
 __global__ void __launch_bounds__(256, MODE == 1 ? 3 : 1)
-    k_sepconv_fused(const ConvArgs a, const __grid_constant__ TapsParam<float, 2 * (2 * R + 1)> tp,
+    k_sepconv_fused(const ConvArgs a, const __grid_constant__ TapsParamFor<float, 2 * (2 * R + 1), UNR> tp,
                     const __grid_constant__ CUtensorMap tmap) {
     constexpr int NT = 2 * R + 1;
     using G = TileGeo<Tin, NT, PX>;      // staging geometry (PAD)
@@ -91,7 +144,8 @@ __global__ void __launch_bounds__(256, MODE == 1 ? 3 : 1)
     constexpr int kStages = LOAD == IMCL_LOAD_TMA ? 2 : (LOAD == IMCL_LOAD_SMEM ? 1 : 0);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     float* tbuf = reinterpret_cast<float*>(smem + 128 + kStages * stage_bytes);
-    float* wsm = tbuf + (MODE == 0 ? SH * TW : 0);
+    using W = typename std::remove_cv<typename std::remove_reference<decltype(tp.w[0])>::type>::type;
+    W* wsm = reinterpret_cast<W*>(tbuf + (MODE == 0 ? SH * TW : 0));
 
     const Tin* in = static_cast<const Tin*>(a.in);
     Tout* out = static_cast<Tout*>(a.out);
@@ -104,16 +158,23 @@ __global__ void __launch_bounds__(256, MODE == 1 ? 3 : 1)
             const float* rd = static_cast<const float*>(a.taps_dev);
             const float* cd = static_cast<const float*>(a.taps2_dev);
             for (int i = tid; i < NT; i += nth) {
-                wsm[i] = (i >= orr && i < orr + a.kw) ? rd[i - orr] : 0.f;
-                wsm[NT + i] = (i >= orc && i < orc + a.kh) ? cd[i - orc] : 0.f;
+                const float r = (i >= orr && i < orr + a.kw) ? rd[i - orr] : 0.f;
+                const float c = (i >= orc && i < orc + a.kh) ? cd[i - orc] : 0.f;
+                if constexpr (UNR == IMCL_UNROLL_PACKED) {
+                    wsm[i] = make_float2(r, r);
+                    wsm[NT + i] = make_float2(c, c);
+                } else {
+                    wsm[i] = r;
+                    wsm[NT + i] = c;
+                }
             }
         } else {
             for (int i = tid; i < 2 * NT; i += nth) wsm[i] = tp.w[i];
         }
     }
-    const float* rw;
+    const W* rw;
     if constexpr (FILT == IMCL_FILT_SMEM) rw = wsm; else rw = tp.w;
-    const float* cw = rw + NT;
+    const W* cw = rw + NT;
 
     const int ntiles = a.tiles_x * a.tiles_y;
     int t = blockIdx.x;
@@ -186,20 +247,12 @@ __global__ void __launch_bounds__(256, MODE == 1 ? 3 : 1)
                                                 a.vec_in != 0, seg);
                     else
                         load_seg_smem<Tin, G>(st + row * SW + tx * PX, seg);
-#pragma unroll
-                    for (int ox = 0; ox < PX; ++ox) t4[ox] = 0.f;
-#pragma unroll
-                    for (int i = 0; i < NT; ++i)
-#pragma unroll
-                        for (int ox = 0; ox < PX; ++ox) t4[ox] = __fmaf_rn(rw[i], seg[G::LO + ox + i], t4[ox]);
+                    row_taps<PX, NT, G::LO, UNR>(seg, rw, t4);
                 }
 #pragma unroll
                 for (int oy = 0; oy < PY; ++oy) {
                     const int j = yy - oy;
-                    if (j >= 0 && j < NT) {
-#pragma unroll
-                        for (int ox = 0; ox < PX; ++ox) acc[oy][ox] = __fmaf_rn(cw[j], t4[ox], acc[oy][ox]);
-                    }
+                    if (j >= 0 && j < NT) axpy_row<PX, UNR>(cw[j], t4, acc[oy]);
                 }
             }
 #pragma unroll
@@ -225,14 +278,7 @@ __global__ void __launch_bounds__(256, MODE == 1 ? 3 : 1)
                                                      a.vec_in != 0, seg);
                         else
                             load_seg_smem<Tin, GR>(st + row * SW + c0, seg);
-    #pragma unroll
-                        for (int ox = 0; ox < 8; ++ox) r8[ox] = 0.f;
-    #pragma unroll
-                        for (int i = 0; i < NT; ++i) {
-                            const float w = rw[i];
-    #pragma unroll
-                            for (int ox = 0; ox < 8; ++ox) r8[ox] = __fmaf_rn(w, seg[GR::LO + ox + i], r8[ox]);
-                        }
+                        row_taps<8, NT, GR::LO, UNR>(seg, rw, r8);
                     }
                     float* tp = tbuf + row * TW + c0;
                     *reinterpret_cast<float4*>(tp) = make_float4(r8[0], r8[1], r8[2], r8[3]);
@@ -256,11 +302,7 @@ __global__ void __launch_bounds__(256, MODE == 1 ? 3 : 1)
     #pragma unroll
                     for (int oy = 0; oy < PY; ++oy) {
                         const int j = yy - oy;
-                        if (j >= 0 && j < NT) {
-                            const float w = cw[j];
-    #pragma unroll
-                            for (int ox = 0; ox < PX; ++ox) acc[oy][ox] = __fmaf_rn(w, tv[ox], acc[oy][ox]);
-                        }
+                        if (j >= 0 && j < NT) axpy_row<PX, UNR>(cw[j], tv, acc[oy]);
                     }
                 }
     #pragma unroll
@@ -275,15 +317,16 @@ __global__ void __launch_bounds__(256, MODE == 1 ? 3 : 1)
 }
 
 // ------------------------------------------------------------------ host launchers
-inline void fill_sep_taps(float* w, int R, const ConvCall& c) {
+template <typename W>
+inline void fill_sep_taps(W* w, int R, const ConvCall& c) {
     const int NT = 2 * R + 1;
-    for (int i = 0; i < 2 * NT; ++i) w[i] = 0.f;
+    for (int i = 0; i < 2 * NT; ++i) set_tap(w[i], 0.f);
     if (c.taps_mem != IMCL_MEM_HOST) return;
     const float* row = static_cast<const float*>(c.taps);
     const float* col = static_cast<const float*>(c.taps2);
     const int orr = R - (c.kw - 1) / 2, orc = R - (c.kh - 1) / 2;
-    for (int i = 0; i < c.kw; ++i) w[orr + i] = row[i];
-    for (int j = 0; j < c.kh; ++j) w[NT + orc + j] = col[j];
+    for (int i = 0; i < c.kw; ++i) set_tap(w[orr + i], row[i]);
+    for (int j = 0; j < c.kh; ++j) set_tap(w[NT + orc + j], col[j]);
 }
 
 template <typename Tin, typename Tout>
@@ -306,7 +349,7 @@ imcl_status launch_sep_plain(const ConvCall& c, const imcl_variant& v, cudaStrea
     return cuda_fail(cudaGetLastError(), "sepconv plain launch");
 }
 
-template <typename Tin, typename Tout, int R, int PX, int PY, int LOAD, int FILT, int MODE>
+template <typename Tin, typename Tout, int R, int PX, int PY, int LOAD, int FILT, int MODE, int UNR>
 imcl_status launch_sep_fused(const ConvCall& c, const imcl_variant& v, cudaStream_t s) {
     constexpr int NT = 2 * R + 1;
     using G = TileGeo<Tin, NT, PX>;
@@ -326,9 +369,10 @@ imcl_status launch_sep_fused(const ConvCall& c, const imcl_variant& v, cudaStrea
         return fail(IMCL_ERR_UNSUPPORTED, "fused sepconv: TMA box larger than 256 in a dimension");
     const int stage_bytes = round_up(SW * SH * G::SZ, 128);
     const int nstage = LOAD == IMCL_LOAD_TMA ? 2 : (LOAD == IMCL_LOAD_SMEM ? 1 : 0);
-    const int smem = 128 + nstage * stage_bytes + (MODE == 0 ? SH * TW * 4 : 0) + 2 * NT * 4;
+    using TP = TapsParamFor<float, 2 * NT, UNR>;
+    const int smem = 128 + nstage * stage_bytes + (MODE == 0 ? SH * TW * 4 : 0) + (int)sizeof(TP);
     if (smem > c.dev->max_smem_optin) return fail(IMCL_ERR_UNSUPPORTED, "fused sepconv: tile too large for shared memory");
-    auto kfn = k_sepconv_fused<Tin, Tout, R, PX, PY, LOAD, FILT, MODE>;
+    auto kfn = k_sepconv_fused<Tin, Tout, R, PX, PY, LOAD, FILT, MODE, UNR>;
     imcl_status st = set_smem_limit((const void*)kfn, smem);
     if (st != IMCL_OK) return st;
     // the L1-path row pass reads GR::VB-pixel vectors straight from global memory
@@ -346,7 +390,7 @@ imcl_status launch_sep_fused(const ConvCall& c, const imcl_variant& v, cudaStrea
         st = encode_tmap_2d(&tmap, c.in_dtype, c.in, c.W, c.H, c.in_pitch_b, SW, SH);
         if (st != IMCL_OK) return st;
     }
-    TapsParam<float, 2 * NT> tp;
+    TP tp;
     fill_sep_taps(tp.w, R, c);
     int grid = ntiles;
     if (v.persistent || LOAD == IMCL_LOAD_TMA) {
@@ -359,7 +403,8 @@ imcl_status launch_sep_fused(const ConvCall& c, const imcl_variant& v, cudaStrea
     return cuda_fail(cudaGetLastError(), "sepconv fused launch");
 }
 
-template <typename Tin, typename Tout, int R, int PX, int PY, int LOAD, int FILT, int MODE = 0>
+template <typename Tin, typename Tout, int R, int PX, int PY, int LOAD, int FILT, int MODE = 0,
+          int UNR = IMCL_UNROLL_FULL>
 inline ConvEntry sep_entry(int bx, int by, int persistent) {
     imcl_variant v{};
     v.kind = IMCL_KIND_TILED;
@@ -370,10 +415,10 @@ inline ConvEntry sep_entry(int bx, int by, int persistent) {
     v.load = LOAD;
     v.filt = FILT;
     v.map = MODE == 1 ? IMCL_MAP_REGISTER : IMCL_MAP_BLOCKED;
-    v.unroll = 1;
+    v.unroll = UNR;
     v.persistent = persistent;
     return ConvEntry{DtypeOf<Tin>::v, DtypeOf<Tout>::v, R, v,
-                     &launch_sep_fused<Tin, Tout, R, PX, PY, LOAD, FILT, MODE>};
+                     &launch_sep_fused<Tin, Tout, R, PX, PY, LOAD, FILT, MODE, UNR>};
 }
 
 }  // namespace imcl

@@ -29,6 +29,14 @@ struct TapsParam {
     Acc w[N];
 };
 
+// Taps as kernel parameters: one value per tap, or (w, w) pairs for the packed forms.
+template <typename Acc, int N, int UNR>
+using TapsParamFor = typename std::conditional<UNR == IMCL_UNROLL_PACKED, TapsParam<float2, N>, TapsParam<Acc, N>>::type;
+
+inline void set_tap(float& d, float w) { d = w; }
+inline void set_tap(int32_t& d, int32_t w) { d = w; }
+inline void set_tap(float2& d, float w) { d = make_float2(w, w); }
+
 // ------------------------------------------------------------------ tile geometry
 template <typename Tin, int K, int PX>
 struct TileGeo {

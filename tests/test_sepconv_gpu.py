@@ -102,3 +102,30 @@ def test_workload_8192_sampled_rows(radius, dt, out_dtype):
         check_float_output(y[rows[0]:rows[1]], ref, s, out_dtype, f"R={radius} {dt} rows={rows}")
     del xd, y
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("radius", [1, 2, 4, 8, 13])
+@pytest.mark.parametrize("dt,out_dtype", [("f32", torch.float32), ("bf16", torch.bfloat16), ("f16", torch.float32)])
+def test_packed_fma_form_gives_the_scalar_bits(dt, out_dtype, radius):
+    """Both passes of UNROLL_PACKED keep the scalar operation order per lane: its output
+    equals the scalar variant with the same axes bit for bit."""
+    g = np.random.default_rng(5200 + radius)
+    x = place(synth.to_storage(synth.uniform_f32(g, 263, 301), dt), "padded")
+    row = synth.gaussian_taps(radius)
+    col = g.standard_normal(2 * radius + 1).astype(np.float32)
+    prob = ops.problem(_abi.OP_SEPCONV, dt, out_dtype, row.size, col.size, 301, 263)
+    vs = ops.variants(prob)
+    packed = [v for v in vs if v["unroll"] == _abi.UNROLL_PACKED]
+    assert packed, "no packed variant compiled"
+    axes = ("kind", "px", "py", "load", "filt", "map")
+    for border, bv in (("clamp", 0.0), ("constant", 0.25)):
+        for v in packed:
+            twins = [u for u in vs if u["unroll"] == _abi.UNROLL_FULL and all(u[f] == v[f] for f in axes)]
+            yp = ops.sepconv(x, row, col, border, bv, out=out_buffer(263, 301, out_dtype, "padded"), variant=v)
+            if twins:
+                ys = ops.sepconv(x, row, col, border, bv, out=out_buffer(263, 301, out_dtype, "padded"),
+                                 variant=dict(twins[0], bx=v["bx"], by=v["by"]))
+                assert torch.equal(ys, yp), f"packed {v} differs from its scalar form"
+            else:
+                ref, s = sep_reference(x.cpu(), row, col, border, bv)
+                check_float_output(yp, ref, s, out_dtype, f"packed {v}")
