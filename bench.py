@@ -162,15 +162,20 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_record(k):
-    """DRAM bytes per launch from a committed ncu capture, if the kernel is unchanged."""
+def variant_key(v):
+    return ",".join(f"{f}={v[f]}" for f in ("px", "py", "bx", "by", "load", "filt", "map"))
+
+
+def traffic_record(k, variant):
+    """DRAM bytes (read + write) per launch of the k x k kernel in this variant, from a
+    committed ncu capture, if the kernel sources are unchanged since; else None."""
     p = os.path.join(ROOT, "profiles", f"conv2d_tiled_k{k}_8192_f32.traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
     if d.get("source_hash") != kernel_source_hash():
         return None
-    return d.get("dram_bytes_per_launch")
+    return d.get("dram_bytes_per_launch", {}).get(variant_key(variant))
 
 
 def workload():
@@ -543,7 +548,7 @@ def run_ours(args):
     d = per_stencil[f"{dom}x{dom}"]
     ai = 2.0 * dom * dom / bytes_px                          # flop per HBM byte
     ridge = fp32_peak * 1e3 / hbm_gbs
-    traffic = traffic_record(dom)
+    traffic = traffic_record(dom, d["variant"])
     if ai > ridge:
         roof = {"bound": "alu", "achieved": d["fp32_tflops"], "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": d["fp32_frac"], "traffic": traffic,
