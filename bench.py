@@ -167,15 +167,27 @@ def variant_key(v):
 
 
 def traffic_record(k, variant):
-    """DRAM bytes (read + write) per launch of the k x k kernel in this variant, from a
-    committed ncu capture, if the kernel sources are unchanged since; else None."""
+    """(DRAM bytes read + written per launch, note) for the k x k kernel in this variant,
+    from a committed ncu capture, if the kernel sources are unchanged since; (None, why)
+    otherwise.  A block shape that was not captured takes the mean over the captured
+    shapes of the same per-thread form (they differ by well under 1%), and says so."""
     p = os.path.join(ROOT, "profiles", f"conv2d_tiled_k{k}_8192_f32.traffic.json")
     if not os.path.exists(p):
-        return None
+        return None, "no capture committed"
     d = json.load(open(p))
     if d.get("source_hash") != kernel_source_hash():
-        return None
-    return d.get("dram_bytes_per_launch", {}).get(variant_key(variant))
+        return None, "kernel sources changed since the capture"
+    recs = d.get("dram_bytes_per_launch", {})
+    key = variant_key(variant)
+    if key in recs:
+        return recs[key], f"ncu capture of this variant ({os.path.basename(p)})"
+    form = {f: variant[f] for f in ("px", "py", "load", "filt", "map")}
+    same = [v for kk, v in recs.items()
+            if all(f"{f}={form[f]}" in kk.split(",") for f in form)]
+    if same:
+        return sum(same) / len(same), (f"mean of {len(same)} captured block shapes of this form "
+                                       f"({os.path.basename(p)}); this block shape was not captured")
+    return None, "this variant was not captured"
 
 
 def workload():
@@ -548,15 +560,15 @@ def run_ours(args):
     d = per_stencil[f"{dom}x{dom}"]
     ai = 2.0 * dom * dom / bytes_px                          # flop per HBM byte
     ridge = fp32_peak * 1e3 / hbm_gbs
-    traffic = traffic_record(dom, d["variant"])
+    traffic, traffic_note = traffic_record(dom, d["variant"])
     if ai > ridge:
         roof = {"bound": "alu", "achieved": d["fp32_tflops"], "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": d["fp32_frac"], "traffic": traffic,
+                "frac": d["fp32_frac"], "traffic": traffic, "traffic_source": traffic_note,
                 "kernel": f"k_conv2d_tiled {dom}x{dom} f32",
                 "peak_source": f"{n_sm} SMs x 128 FMA/clk x 2 x {sm_max_mhz:.0f} MHz ({peak_src} max clock)"}
     else:
         roof = {"bound": "hbm", "achieved": d["hbm_gbs"], "peak": hbm_gbs, "unit": "GB/s",
-                "frac": d["hbm_frac"], "traffic": traffic,
+                "frac": d["hbm_frac"], "traffic": traffic, "traffic_source": traffic_note,
                 "kernel": f"k_conv2d_tiled {dom}x{dom} f32", "peak_source": f"{peak_src} copy bandwidth"}
 
     probe = {"ffma_tflops": ops.probe_fp32(False), "ffma2_tflops": ops.probe_fp32(True)}
