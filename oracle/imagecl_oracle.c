@@ -154,6 +154,9 @@ int ora_sepconv_f64(const double *x, int64_t W, int64_t H, const double *row, in
  *   Pxx = Ix*Ix,  Pyy = Iy*Iy,  Pxy = Ix*Iy
  *   Sc = G (*) Pc  for c in {xx, yy, xy}                  (wk x wk window)
  *   R = Sxx*Syy - Sxy*Sxy - k*(Sxx + Syy)^2
+ * Window tap (j, i) reads the product at offset (i - wk/2, j - wk/2) (integer division):
+ * centred for odd wk; for even wk (the 2x2 "block" of the Harris benchmark) the anchor is
+ * the lower-right of the four central taps, offsets {-1, 0} for wk = 2.
  * Output rows [y0, y1) of R.  If `inter` is not NULL it receives, for those rows,
  * 8 planes [Ix, Iy, Pxx, Pyy, Pxy, Sxx, Syy, Sxy], each (y1 - y0) * W.
  */
@@ -176,7 +179,7 @@ int ora_harris_f64(const double *I, int64_t W, int64_t H, const double *sx, cons
     if (!I || !sx || !sy || !win || !R || W <= 0 || H <= 0 || wk <= 0) return 1;
     if (y0 < 0 || y1 > H || y0 > y1) return 1;
     if (y0 == y1) return 0;
-    const int rw = (wk - 1) / 2;
+    const int rw = wk / 2;   /* anchor: odd wk centred, even wk offsets -wk/2 .. wk/2-1 */
     const int64_t p0 = clampi(y0 - rw, 0, H - 1), p1 = clampi(y1 - 1 + rw, 0, H - 1) + 1;
     const int64_t np = (p1 - p0) * W;
     double *P = (double *)malloc(sizeof(double) * (size_t)(3 * np + 2 * np));
@@ -333,7 +336,7 @@ int ora_harris_bwd_f64(const double *I, int64_t W, int64_t H, const double *sx, 
                        const double *win, int wk, double k, const double *gR, double *dI,
                        double *dsx, double *dsy, double *dwin) {
     if (!I || !sx || !sy || !win || !gR || W <= 0 || H <= 0 || wk <= 0) return 1;
-    const int rw = (wk - 1) / 2;
+    const int rw = wk / 2;   /* anchor: odd wk centred, even wk offsets -wk/2 .. wk/2-1 */
     const int64_t n = W * H;
     double *inter = (double *)malloc(sizeof(double) * (size_t)(8 * n));
     double *R = (double *)malloc(sizeof(double) * (size_t)n);

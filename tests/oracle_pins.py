@@ -16,7 +16,8 @@ What pins what:
   * brute force on 4x4 inputs;
   * separable = 2D with the outer-product filter (clamped rule);
   * Harris: R = 0 on a constant image, R <= 0 on a straight edge, transpose symmetry,
-    degree-4 homogeneity, corners of rectangles found at their positions;
+    degree-4 homogeneity, corners of rectangles found at their positions; even windows
+    against scipy, a delta window's closed form and the zero-padded odd window;
   * adjoints: <A x, g> = <x, A^T g>, linearity in the taps, torch autograd on the
     library formulation, Euler's identity for the homogeneous Harris response and
     central finite differences.
@@ -319,6 +320,56 @@ def check_harris_corners(ora):
         assert d <= 2, (cx, cy, d)
 
 
+def _pad_window(win):
+    """An even wk x wk window as the (wk+1) x (wk+1) centred window with the same offsets:
+    tap (j, i) reads offset (i - wk/2, j - wk/2) in both, so a zero last row and column."""
+    wk = win.shape[0]
+    out = np.zeros((wk + 1, wk + 1))
+    out[:wk, :wk] = win
+    return out
+
+
+def check_harris_even_window(ora):
+    """Even windows (the 2x2 block of the Harris benchmark, §6) anchored at offsets
+    -wk/2 .. wk/2 - 1: scipy.ndimage.correlate centres an even filter at index size // 2,
+    the same offsets; a delta window gives the closed form -k (Ix^2 + Iy^2)^2 at the
+    delta's offset; and the window equals its zero-padded odd form exactly, forward and
+    backward."""
+    g = np.random.default_rng(33)
+    k = 0.04
+    for (h, w) in [(1, 1), (2, 3), (9, 7), (16, 21)]:
+        img = g.random((h, w))
+        for wk in (2, 4, 6):
+            win = g.random((wk, wk))
+            ref, _, _ = _harris_library(img, SX, SY, win, k)
+            R = ora.harris(img, SX, SY, win, k)
+            assert _rel(R, ref, max(np.abs(ref).max(), 1.0)) < 1e-12
+            assert np.array_equal(R, ora.harris(img, SX, SY, _pad_window(win), k))
+        ix = ndi.correlate(img, SX, mode="nearest")
+        iy = ndi.correlate(img, SY, mode="nearest")
+        m = ix * ix + iy * iy
+        closed = -k * m * m
+        scale = max(np.abs(closed).max(), 1e-300)
+        for (j, i) in ((1, 1), (0, 0), (0, 1), (1, 0)):   # offsets (i - 1, j - 1)
+            delta = np.zeros((2, 2))
+            delta[j, i] = 1.0
+            R = ora.harris(img, SX, SY, delta, k)
+            ys = np.clip(np.arange(h) + j - 1, 0, h - 1)
+            xs = np.clip(np.arange(w) + i - 1, 0, w - 1)
+            assert _rel(R, closed[np.ix_(ys, xs)], scale) < 1e-12, (j, i)
+    img = g.random((8, 9))
+    gR = g.standard_normal((8, 9))
+    win = g.random((2, 2))
+    dI, dsx, dsy, dwin = ora.harris_backward(img, SX, SY, win, gR, k)
+    pI, psx, psy, pwin = ora.harris_backward(img, SX, SY, _pad_window(win), gR, k)
+    assert np.array_equal(dI, pI) and np.array_equal(dsx, psx) and np.array_equal(dsy, psy)
+    assert np.array_equal(dwin, pwin[:2, :2])
+    L = lambda a: np.sum(gR * ora.harris(img, SX, SY, a, k))
+    for idx in [(0, 0), (1, 1), (0, 1)]:
+        fd = _fd(L, win, idx)
+        assert abs(fd - dwin[idx]) < 1e-6 * (abs(dwin[idx]) + abs(fd) + 1e-3)
+
+
 # ------------------------------------------------------------------ adjoints
 
 def check_conv_adjoint(ora):
@@ -425,6 +476,7 @@ ALL_CHECKS = [check_golden_conv, check_delta_identity, check_constant_image, che
               check_int_wraparound, check_row_range, check_sep_outer_product,
               check_sep_library, check_sep_constant_and_mirror,
               check_sep_constant_border_differs, check_golden_harris, check_harris_library,
-              check_harris_invariants, check_harris_corners, check_conv_adjoint,
+              check_harris_invariants, check_harris_corners, check_harris_even_window,
+              check_conv_adjoint,
               check_conv_backward_autograd, check_sep_adjoint, check_harris_backward,
               check_conv_sep_fd]

@@ -29,6 +29,8 @@ MUTATIONS = {
                           "gI[p] = Ix[p] * gP[p] + Iy[p] * gP[2 * n + p];"),
     "sep_column_flipped": ("int64_t qy = py + j - rc;\n                double v;",
                            "int64_t qy = py - j + rc;\n                double v;"),
+    "harris_even_anchor": ("    const int rw = wk / 2;   /* anchor: odd wk centred, even wk offsets -wk/2 .. wk/2-1 */",
+                           "    const int rw = (wk - 1) / 2;"),
     "int_no_wrap": ("out[(py - y0) * W + px] = (int32_t)(uint32_t)(uint64_t)s;",
                     "out[(py - y0) * W + px] = s > 2147483647 ? 2147483647 : (int32_t)s;"),
 }
