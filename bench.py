@@ -378,6 +378,21 @@ def extra_stencils(hbm_gbs, fp32_peak, budget):
                                     note="adjoint of the fused forward: image, Sobel and window gradients")
     del x, y, ws, gR
 
+    # the paper's Harris shape (§6): 5120x5120 f32 with a 2x2 box block (offsets -1, 0)
+    img, sx, sy, _, k = synth.workload_harris(5120, 5120)
+    win2 = synth.box_window(2)
+    x = torch.from_numpy(img).to(dev)
+    y = torch.empty_like(x)
+    res = ops.tune(ops.problem(_abi.OP_HARRIS, "f32", "f32", 2, 2, 5120, 5120), budget_s=budget, reps=3)
+    ws = torch.empty(2 * 5120 * 5120 * 4, dtype=torch.uint8, device=dev)
+    tt = _median_ms(lambda: ops.harris(x, sx, sy, win2, k, out=y), 7, flush)
+    tp = _median_ms(lambda: ops.harris(x, sx, sy, win2, k, out=y, variant=plain, workspace=ws), 5, flush)
+    px = 5120 * 5120
+    flops_box2 = 2 * 18 * (5122 * 5122) / px + 3 + 2 * 3 * 4 + 7   # algorithmic: a 2x2 window
+    out["paper_harris_5120_f32_box2"] = _entry(px, tt, tp, 8, flops_box2, hbm_gbs, fp32_peak, res["variant"],
+                                               "even window run as the 3x3 kernel with a zero row and column")
+    del x, y, ws
+
     # ragged batch: 256 f16 images, one graph launch forward and one backward
     items = synth.workload_batch()
     bitems = []

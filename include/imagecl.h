@@ -163,11 +163,15 @@ size_t imagecl_sepconv_workspace_size(const imcl_problem *problem, const imcl_va
  *   Pxx = Ix^2,  Pyy = Iy^2,  Pxy = Ix Iy
  *   Sc = window (*) Pc                                (wk x wk, c in {xx, yy, xy})
  *   out = Sxx Syy - Sxy^2 - k (Sxx + Syy)^2
- * in and out: f32.  sobel_x, sobel_y: 9 taps each; window: wk*wk taps (wk odd, 1..7);
- * all three host or device per taps_mem.  The fused variants (the default; wk 3 or 5)
- * need no workspace.  The PLAIN variant (any odd wk up to 7) runs the paper's two
- * kernels with Ix, Iy in `workspace` (2*width*height*4 bytes, caller-owned device
- * memory; see imagecl_harris_workspace_size); NULL or short -> IMCL_ERR_INVALID.
+ * in and out: f32.  sobel_x, sobel_y: 9 taps each; window: wk*wk taps (wk 1..7);
+ * all three host or device per taps_mem.  Window tap (j, i) reads the product at offset
+ * (i - wk/2, j - wk/2) (integer division): centred for odd wk; for even wk (the 2x2
+ * "block" of the paper's Harris benchmark) offsets -wk/2 .. wk/2-1, and the call runs
+ * the (wk+1) x (wk+1) kernels with a zero last row and column (the same sums).  The
+ * fused variants (the default; wk 2..5) need no workspace.  The PLAIN variant (any wk up
+ * to 7) runs the paper's two kernels with Ix, Iy in `workspace` (2*width*height*4 bytes,
+ * caller-owned device memory; see imagecl_harris_workspace_size); NULL or short ->
+ * IMCL_ERR_INVALID.
  */
 imcl_status imagecl_harris(const imcl_image *in, const imcl_image *out, const float *sobel_x,
                            const float *sobel_y, const float *window, int32_t wk, float k,
@@ -189,7 +193,8 @@ size_t imagecl_harris_workspace_size(const imcl_problem *problem, const imcl_var
  *  - tap gradient: dtaps[o] = sum_p grad_out(p) * in_b(p + o), with in_b the boundary
  *    rule's read, reduced per CTA and then over CTAs in a fixed order (deterministic);
  *  - Harris: the chain rule R -> (Sxx, Syy, Sxy) -> products -> (Ix, Iy) -> image, and
- *    the window and Sobel tap gradients on the way.
+ *    the window and Sobel tap gradients on the way (any window side 1..7, anchored as in
+ *    imagecl_harris).
  * grad_out is f32 with the size of `in`; in is f32, f16 or bf16 (Harris: f32).
  * grad_in (f32, nullable: not computed) must not overlap grad_out or in.  The tap
  * gradients (nullable) are device f32 arrays the caller owns, written (not accumulated).

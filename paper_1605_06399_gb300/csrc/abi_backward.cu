@@ -69,7 +69,7 @@ size_t imagecl_sepconv_backward_workspace_size(int32_t width, int32_t height, in
 
 size_t imagecl_harris_backward_workspace_size(int32_t width, int32_t height, int32_t wk) {
     if (width <= 0 || height <= 0 || wk <= 0) return 0;
-    return harris_backward_ws(width, height, wk);
+    return harris_backward_ws(width, height, harris_kernel_side(wk));
 }
 
 imcl_status imagecl_conv2d_backward(const imcl_image* grad_out, const imcl_image* in, const float* taps, int32_t kw,
@@ -129,7 +129,6 @@ imcl_status imagecl_harris_backward(const imcl_image* grad_out, const imcl_image
                                     const imcl_image* grad_in, float* grad_sobel_x, float* grad_sobel_y,
                                     float* grad_window, void* workspace, size_t workspace_bytes, void* stream) {
     if (wk <= 0) return fail(IMCL_ERR_INVALID, "window side must be positive");
-    if (wk % 2 == 0) return fail(IMCL_ERR_UNSUPPORTED, "window side must be odd (centred window)");
     if (wk > 7) return fail(IMCL_ERR_UNSUPPORTED, "window side above 7 is not provided");
     if (!sobel_x || !sobel_y || !window) return fail(IMCL_ERR_INVALID, "sobel_x, sobel_y and window must not be NULL");
     if (taps_mem != IMCL_MEM_HOST && taps_mem != IMCL_MEM_DEVICE)
@@ -137,9 +136,10 @@ imcl_status imagecl_harris_backward(const imcl_image* grad_out, const imcl_image
     if (in && in->dtype != IMCL_F32) return fail(IMCL_ERR_UNSUPPORTED, "harris takes an f32 image");
     imcl_status st;
     BwdArgs b;
-    const size_t need = (in && in->width > 0 && in->height > 0) ? harris_backward_ws(in->width, in->height, wk) : 0;
+    const size_t need =
+        (in && in->width > 0 && in->height > 0) ? harris_backward_ws(in->width, in->height, harris_kernel_side(wk)) : 0;
     if ((st = bwd_common(grad_out, in, grad_in, workspace, workspace_bytes, need, &b)) != IMCL_OK) return st;
-    b.fwd.kw = wk;
+    b.fwd.kw = harris_kernel_side(wk);
     b.fwd.kh = wk;
     b.fwd.taps = sobel_x;
     b.fwd.taps2 = sobel_y;

@@ -5,9 +5,23 @@
 
 namespace imcl {
 
+// Harris calls keep the caller's window side in kh and the side of the kernels that run
+// it in kw: equal for odd windows; an even window runs as the next odd one with a zero
+// last row and column (tap (j, i) keeps its offset (i - wk/2, j - wk/2)).
+int harris_kernel_side(int wk) { return wk % 2 ? wk : wk + 1; }
+
+ConvCall harris_problem_call(const imcl_problem& p) {
+    ConvCall c = problem_call(p);
+    c.in_dtype = c.out_dtype = IMCL_F32;
+    c.kh = p.kw;
+    c.kw = harris_kernel_side(p.kw);
+    return c;
+}
+
 imcl_problem harris_problem(const ConvCall& c) {
     imcl_problem p = conv_problem(c);
     p.op = IMCL_OP_HARRIS;
+    p.kw = p.kh = c.kh;
     return p;
 }
 
@@ -48,7 +62,6 @@ imcl_status harris_prepare(const imcl_image* in, const imcl_image* out, const fl
     if (in->dtype != IMCL_F32 || out->dtype != IMCL_F32)
         return fail(IMCL_ERR_UNSUPPORTED, "harris takes an f32 image and writes f32");
     if (wk <= 0) return fail(IMCL_ERR_INVALID, "window side must be positive");
-    if (wk % 2 == 0) return fail(IMCL_ERR_UNSUPPORTED, "window side must be odd (centred window)");
     if (wk > 7) return fail(IMCL_ERR_UNSUPPORTED, "window side above 7 is not provided");
     if (!sx || !sy || !win) return fail(IMCL_ERR_INVALID, "sobel_x, sobel_y and window must not be NULL");
     if (taps_mem != IMCL_MEM_HOST && taps_mem != IMCL_MEM_DEVICE)
@@ -64,7 +77,7 @@ imcl_status harris_prepare(const imcl_image* in, const imcl_image* out, const fl
     c->H = in->height;
     c->in_pitch_b = in->pitch_bytes;
     c->out_pitch_b = out->pitch_bytes;
-    c->kw = wk;
+    c->kw = harris_kernel_side(wk);
     c->kh = wk;
     c->taps = sx;
     c->taps2 = sy;
@@ -107,7 +120,7 @@ size_t imagecl_harris_workspace_size(const imcl_problem* problem, const imcl_var
     if (!problem || problem->width <= 0 || problem->height <= 0) return 0;
     imcl_problem q = *problem;
     q.in_dtype = q.out_dtype = IMCL_F32;
-    const imcl_variant v = variant ? *variant : harris_default_variant(problem_call(q));
+    const imcl_variant v = variant ? *variant : harris_default_variant(harris_problem_call(q));
     if (v.kind == IMCL_KIND_PLAIN) return (size_t)2 * problem->width * (size_t)problem->height * sizeof(float);
     return 0;
 }

@@ -39,6 +39,8 @@ imcl_status sep_prepare(const imcl_image* in, const imcl_image* out, const float
                         int nc, int taps_mem, int border, double bv, void* ws, size_t ws_bytes, ConvCall* c);
 imcl_status sep_run(const ConvCall& c, const imcl_variant* variant, cudaStream_t s);
 
+int harris_kernel_side(int wk);
+ConvCall harris_problem_call(const imcl_problem& p);
 imcl_problem harris_problem(const ConvCall& c);
 std::vector<const ConvEntry*> harris_entries_for(int wk, int taps_mem);
 imcl_variant harris_default_variant(const ConvCall& c);

@@ -247,7 +247,7 @@ imcl_status sepconv_backward_run(const BwdArgs& b, cudaStream_t s) {
 // ------------------------------------------------------------------ Harris
 imcl_status harris_backward_run(const BwdArgs& b, cudaStream_t s) {
     const ConvCall& f = b.fwd;
-    const int W = f.W, H = f.H, wk = f.kw;
+    const int W = f.W, H = f.H, wk = f.kw, src = f.kh;   // kernel side, caller's window side
     const size_t pf = plane_floats(W, H);
     const int64_t pp = (int64_t)plane_pitch(W), pp_b = pp * 4;
     float* ws = static_cast<float*>(b.workspace);
@@ -263,6 +263,25 @@ imcl_status harris_backward_run(const BwdArgs& b, cudaStream_t s) {
     const float* gw = static_cast<const float*>(f.taps3);
     const int grid = wgrad_grid(W, H);
     dim3 eg((W + 255) / 256, H);
+    // an even window runs as the next odd one with a zero last row and column; its
+    // gradient is the top-left src x src block of that window's gradient
+    std::vector<float> gw_host;
+    float* dwin_pad = nullptr;
+    if (src != wk) {
+        if (f.taps_mem == IMCL_MEM_HOST) {
+            gw_host.assign((size_t)wk * wk, 0.f);
+            for (int j = 0; j < src; ++j)
+                for (int i = 0; i < src; ++i) gw_host[j * wk + i] = gw[j * src + i];
+            gw = gw_host.data();
+        } else {
+            float* d = tap_slot + 192;
+            IMCL_TRY(cuda_fail(cudaMemsetAsync(d, 0, sizeof(float) * wk * wk, s), "window padding"));
+            IMCL_TRY(cuda_fail(cudaMemcpy2DAsync(d, sizeof(float) * wk, gw, sizeof(float) * src, sizeof(float) * src,
+                                                 src, cudaMemcpyDeviceToDevice, s), "window padding"));
+            gw = d;
+        }
+        if (b.dw2) dwin_pad = tap_slot + 256;
+    }
 
     // forward intermediates: Ix, Iy, P, S
     ConvCall base = f;
@@ -292,7 +311,11 @@ imcl_status harris_backward_run(const BwdArgs& b, cudaStream_t s) {
         for (int ch = 0; ch < 3; ++ch)
             IMCL_TRY(wgrad_partials<float>(S[ch], pp, P[ch], pp, W, H, wk, wk, IMCL_BORDER_CLAMP, 0.f,
                                            partials + (size_t)ch * grid * wk * wk, s));
-        IMCL_TRY(finalize(partials, 3 * grid, wk * wk, b.dw2, s));
+        IMCL_TRY(finalize(partials, 3 * grid, wk * wk, dwin_pad ? dwin_pad : b.dw2, s));
+        if (dwin_pad)
+            IMCL_TRY(cuda_fail(cudaMemcpy2DAsync(b.dw2, sizeof(float) * src, dwin_pad, sizeof(float) * wk,
+                                                 sizeof(float) * src, src, cudaMemcpyDeviceToDevice, s),
+                               "window gradient"));
     }
     // gP = window adjoint of gS (into the P planes)
     TapSet tg;

@@ -12,12 +12,7 @@ imcl_status launch_harris_plain(const ConvCall& c, const imcl_variant& v, cudaSt
     if (bx * by > 256) return fail(IMCL_ERR_UNSUPPORTED, "plain kernel: bx*by must be <= 256");
     ConvArgs a = make_conv_args(c, v, 1, 1);
     HarrisTaps<7> tp;
-    memset(&tp, 0, sizeof tp);
-    if (c.taps_mem == IMCL_MEM_HOST) {
-        memcpy(tp.sx, c.taps, 9 * sizeof(float));
-        memcpy(tp.sy, c.taps2, 9 * sizeof(float));
-        memcpy(tp.g, c.taps3, (size_t)c.kw * c.kw * sizeof(float));
-    }
+    fill_harris_taps(tp, c);
     dim3 grid((c.W + bx - 1) / bx, (c.H + by - 1) / by), block(bx, by);
     k_harris_sobel_plain<<<grid, block, 0, s>>>(a, tp);
     k_harris_resp_plain<<<grid, block, 0, s>>>(a, tp);

@@ -74,8 +74,10 @@ __global__ void __launch_bounds__(256)
     if (x >= a.W || y >= a.H) return;
     const float* ix = static_cast<const float*>(a.work);
     const float* iy = ix + (long long)a.W * a.H;
-    const float* g = a.taps3_dev ? static_cast<const float*>(a.taps3_dev) : tp.g;
-    const int wk = a.kw, rw = (wk - 1) / 2;
+    // a.kw: the (odd) side run; a.kh: the caller's side, the stride of device taps (an
+    // even window runs with a zero last row and column)
+    const float* gd = static_cast<const float*>(a.taps3_dev);
+    const int wk = a.kw, rw = (wk - 1) / 2, src = a.kh;
     float sxx = 0.f, syy = 0.f, sxy = 0.f;
 #pragma unroll 1
     for (int j = 0; j < wk; ++j) {
@@ -83,7 +85,8 @@ __global__ void __launch_bounds__(256)
 #pragma unroll 1
         for (int i = 0; i < wk; ++i) {
             const long long o = (long long)yy * a.W + clampi(x + i - rw, 0, a.W - 1);
-            const float gx = ix[o], gy = iy[o], w = g[j * wk + i];
+            const float w = gd ? ((j < src && i < src) ? gd[j * src + i] : 0.f) : tp.g[j * wk + i];
+            const float gx = ix[o], gy = iy[o];
             sxx = __fmaf_rn(w, gx * gx, sxx);
             syy = __fmaf_rn(w, gy * gy, syy);
             sxy = __fmaf_rn(w, gx * gy, sxy);
@@ -122,9 +125,19 @@ __global__ void __launch_bounds__(256, 2)
     if constexpr (FILT == IMCL_FILT_SMEM) {
         const float* sx = a.taps_dev ? static_cast<const float*>(a.taps_dev) : tp.sx;
         const float* sy = a.taps2_dev ? static_cast<const float*>(a.taps2_dev) : tp.sy;
-        const float* g = a.taps3_dev ? static_cast<const float*>(a.taps3_dev) : tp.g;
-        for (int i = tid; i < 18 + WK * WK; i += nth)
-            wsm[i] = i < 9 ? sx[i] : (i < 18 ? sy[i - 9] : g[i - 18]);
+        const float* gd = static_cast<const float*>(a.taps3_dev);
+        const int src = a.kh;   // the caller's window side (device taps' stride)
+        for (int i = tid; i < 18 + WK * WK; i += nth) {
+            float v;
+            if (i < 9) v = sx[i];
+            else if (i < 18) v = sy[i - 9];
+            else if (!gd) v = tp.g[i - 18];
+            else {
+                const int j = (i - 18) / WK, c = (i - 18) % WK;
+                v = (j < src && c < src) ? gd[j * src + c] : 0.f;
+            }
+            wsm[i] = v;
+        }
     }
     const float *sxw, *syw, *gw;
     if constexpr (FILT == IMCL_FILT_SMEM) { sxw = wsm; syw = wsm + 9; gw = wsm + 18; }
@@ -281,13 +294,17 @@ __global__ void __launch_bounds__(256, 2)
 }
 
 // ------------------------------------------------------------------ host launchers
+// Host taps into the launch parameters; the window (c.kh x c.kh, the caller's side)
+// goes into the top-left of the c.kw x c.kw table, zeros elsewhere.
 template <int WK>
 inline void fill_harris_taps(HarrisTaps<WK>& tp, const ConvCall& c) {
     memset(&tp, 0, sizeof tp);
     if (c.taps_mem != IMCL_MEM_HOST) return;
     memcpy(tp.sx, c.taps, 9 * sizeof(float));
     memcpy(tp.sy, c.taps2, 9 * sizeof(float));
-    memcpy(tp.g, c.taps3, (size_t)c.kw * c.kw * sizeof(float));
+    const float* g = static_cast<const float*>(c.taps3);
+    for (int j = 0; j < c.kh; ++j)
+        for (int i = 0; i < c.kh; ++i) tp.g[j * c.kw + i] = g[j * c.kh + i];
 }
 
 imcl_status launch_harris_plain(const ConvCall& c, const imcl_variant& v, cudaStream_t s);

@@ -27,7 +27,7 @@ imcl_status list_variants(const imcl_problem& p, std::vector<imcl_variant>* out)
         return IMCL_OK;
     }
     if (p.op == IMCL_OP_HARRIS) {
-        for (const ConvEntry* e : harris_entries_for(p.kw, p.taps_mem)) out->push_back(e->v);
+        for (const ConvEntry* e : harris_entries_for(harris_kernel_side(p.kw), p.taps_mem)) out->push_back(e->v);
         return IMCL_OK;
     }
     return fail(IMCL_ERR_UNSUPPORTED, "unknown op");
@@ -54,7 +54,10 @@ imcl_status default_variant(const imcl_problem& p, imcl_variant* out) {
         DeviceInfo* dev = nullptr;
         imcl_status st = device_info(&dev);
         if (st != IMCL_OK) return st;
-        *out = harris_default_variant(conv_call_for(p, dev));
+        ConvCall c = harris_problem_call(p);
+        c.dev = dev;
+        c.status = dev->status;
+        *out = harris_default_variant(c);
         if (out->kind < 0) return fail(IMCL_ERR_UNSUPPORTED, "no harris variant for this problem");
         return IMCL_OK;
     }
@@ -162,13 +165,13 @@ static imcl_status make_sep_job(const imcl_problem& p, cudaStream_t s, TuneJob* 
 }
 
 static imcl_status make_harris_job(const imcl_problem& p, cudaStream_t s, TuneJob* job) {
-    if (p.kw <= 0 || p.kw % 2 == 0 || p.kw > 7) return fail(IMCL_ERR_UNSUPPORTED, "harris window must be odd, 1..7");
+    if (p.kw <= 0 || p.kw > 7) return fail(IMCL_ERR_UNSUPPORTED, "harris window side must be 1..7");
     imcl_status st;
     DeviceInfo* dev = nullptr;
     if ((st = device_info(&dev)) != IMCL_OK) return st;
-    imcl_problem q = p;
-    q.in_dtype = q.out_dtype = IMCL_F32;
-    ConvCall c = conv_call_for(q, dev);
+    ConvCall c = harris_problem_call(p);
+    c.dev = dev;
+    c.status = dev->status;
     void *in = nullptr, *out = nullptr, *ws = nullptr;
     if ((st = job->scratch.image(IMCL_F32, p.width, p.height, 1605u, &in, &c.in_pitch_b, s)) != IMCL_OK) return st;
     if ((st = job->scratch.image(IMCL_F32, p.width, p.height, 7u, &out, &c.out_pitch_b, s)) != IMCL_OK) return st;
@@ -184,7 +187,7 @@ static imcl_status make_harris_job(const imcl_problem& p, cudaStream_t s, TuneJo
         for (int i = 0; i < 3; ++i) job->taps_f.push_back(sob[i * 3 + j]);
     double gsum = 0;
     const int r = p.kw / 2;
-    for (int j = 0; j < p.kw; ++j)
+    for (int j = 0; j < p.kw; ++j)   // a Gaussian over the window's offsets (caller's side)
         for (int i = 0; i < p.kw; ++i) {
             job->taps_f.push_back((float)std::exp(-0.5 * ((i - r) * (i - r) + (j - r) * (j - r))));
             gsum += job->taps_f.back();
@@ -206,7 +209,7 @@ static imcl_status make_harris_job(const imcl_problem& p, cudaStream_t s, TuneJo
     }
     job->conv = c;
     std::vector<imcl_variant> base;
-    for (const ConvEntry* e : harris_entries_for(p.kw, p.taps_mem)) base.push_back(e->v);
+    for (const ConvEntry* e : harris_entries_for(c.kw, p.taps_mem)) base.push_back(e->v);
     job->candidates = expand_shapes(base);
     job->run = [job](const imcl_variant& v, cudaStream_t st2) { return harris_run(job->conv, &v, st2); };
     job->out = out;

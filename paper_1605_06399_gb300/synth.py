@@ -165,6 +165,11 @@ def workload_sep(radius: int, h: int = 8192, w: int = 8192, seed_offset: int = 3
     return img, t, t.copy()
 
 
+def box_window(size: int) -> np.ndarray:
+    """size x size box window with unit sum (the Harris benchmark's 2x2 block, §6)."""
+    return np.full((size, size), 1.0 / (size * size), dtype=np.float32)
+
+
 def workload_harris(h: int = 4096, w: int = 4096, seed_offset: int = 4):
     """4096x4096 rectangles + noise image, Sobel taps, 5x5 sigma=1 Gaussian window."""
     g = rng(seed_offset)

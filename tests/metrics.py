@@ -103,7 +103,10 @@ def harris_reference(img, sx, sy, win, k=0.04, rows=None, halo=None):
     ai = np.abs(to_f64(img))
     ax = oracle.conv2d(ai, np.abs(to_f64(sx)))
     ay = oracle.conv2d(ai, np.abs(to_f64(sy)))
-    T = oracle.conv2d(ax * ax + ay * ay, np.abs(to_f64(win)), rows=rows)
+    aw = np.abs(to_f64(win))
+    if aw.shape[0] % 2 == 0:   # even window: offsets -wk/2 .. wk/2-1, the centred odd one padded
+        aw = np.pad(aw, ((0, 1), (0, 1)))
+    T = oracle.conv2d(ax * ax + ay * ay, aw, rows=rows)
     return R, T * T
 
 

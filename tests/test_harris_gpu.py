@@ -28,12 +28,20 @@ def _variants(wk, w, h, mem):
     return [None] + vs + extra
 
 
-@pytest.mark.parametrize("wk", [1, 3, 5, 7])
+def _window(g, wk):
+    if wk == 1:
+        return np.ones((1, 1), np.float32)
+    if wk % 2:
+        return synth.gaussian_window(wk, 1.0)
+    return (g.random((wk, wk)) + 0.5).astype(np.float32)   # even: no symmetry to hide the anchor
+
+
+@pytest.mark.parametrize("wk", [1, 2, 3, 4, 5, 6, 7])
 def test_harris_every_variant_matches_oracle(wk):
     g = np.random.default_rng(3000 + wk)
     sx = synth.sobel_x() + 0.1 * g.standard_normal((3, 3)).astype(np.float32)
     sy = synth.sobel_y() + 0.1 * g.standard_normal((3, 3)).astype(np.float32)
-    win = synth.gaussian_window(wk, 1.0) if wk > 1 else np.ones((1, 1), np.float32)
+    win = _window(g, wk)
     n = 0
     for (h, w) in SIZES:
         img = synth.rectangles_image(g, h, w, n_rect=12, side_lo=2, side_hi=max(3, min(h, w)))
@@ -88,8 +96,21 @@ def test_harris_corners_found():
             assert min(max(abs(cx - fx), abs(cy - fy)) for fx, fy in found) <= 2
 
 
-def test_harris_rejects_even_window():
+def test_harris_rejects_window_above_7():
     x = torch.rand(16, 16, device="cuda")
     with pytest.raises(ImclError) as ei:
-        ops.harris(x, synth.sobel_x(), synth.sobel_y(), np.ones((2, 2), np.float32))
+        ops.harris(x, synth.sobel_x(), synth.sobel_y(), np.ones((8, 8), np.float32))
     assert ei.value.status == _abi.ERR_UNSUPPORTED
+
+
+def test_harris_box2_block_5120_sampled_rows():
+    """The paper's Harris benchmark shape: 5120x5120 f32 rectangles + noise with a 2x2
+    box block (offsets -1, 0), tuned launch, checked on row bands (top, middle, bottom)."""
+    img, sx, sy, _, k = synth.workload_harris(5120, 5120)
+    win = synth.box_window(2)
+    x = torch.from_numpy(img).cuda()
+    ops.tune(ops.problem(_abi.OP_HARRIS, "f32", "f32", 2, 2, 5120, 5120), budget_s=4.0, reps=3)
+    y = ops.harris(x, sx, sy, win, k)
+    for rows in [(0, 6), (2555, 2565), (5114, 5120)]:
+        R64, sc = harris_reference(img, sx, sy, win, k, rows=rows, halo=3)
+        check_harris_output(y[rows[0]:rows[1]], R64, sc, f"box2 rows={rows}")
