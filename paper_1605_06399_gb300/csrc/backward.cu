@@ -104,30 +104,54 @@ static imcl_status fold_1d(float* dst, int64_t dst_pitch, const float* g, int64_
     return cuda_fail(cudaGetLastError(), "fold 1d");
 }
 
-template <typename Tx>
-static imcl_status wgrad_partials(const float* g, int64_t g_pitch, const Tx* x, int64_t x_pitch, int W, int H, int kw,
-                                  int kh, int border, float bv, float* partials, cudaStream_t s) {
-    const int grid = wgrad_grid(W, H);
-    const int smem = (kWgTileW * kWgTileH + (kWgTileW + kw - 1) * (kWgTileH + kh - 1) + 256 * 4) * 4;
-    if (kh * ((kw + 3) / 4) > 256) return fail(IMCL_ERR_UNSUPPORTED, "tap gradient: too many taps");
-    k_wgrad_partial<Tx><<<grid, 256, smem, s>>>(g, g_pitch, x, x_pitch, W, H, kw, kh, border, bv, partials);
+// CTAs of a tap-gradient launch: two per SM (the kernel's residency), at most one per
+// tile and at most kWgMaxParts; fixed for a device and an image size.
+static int wgrad_launch_grid(int W, int H, const DeviceInfo* dev) {
+    const int resident = 2 * (dev ? dev->sm_count : 1);
+    return std::max(1, std::min(wgrad_grid(W, H), resident));
+}
+
+template <int KW>
+static imcl_status wgrad_launch(const float* g, int64_t g_pitch, const void* x, int x_dt, int64_t x_pitch, int W,
+                                int H, int kh, int border, float bvf, float* partials, int grid, cudaStream_t s) {
+    const int smem = wgrad_smem_bytes<KW>(kh, 256);
+    auto kfn = k_wgrad_partial<KW>;
+    imcl_status st = set_smem_limit((const void*)kfn, smem);
+    if (st != IMCL_OK) return st;
+    const int esz = x_dt == IMCL_F32 ? 4 : 2;
+    const int vec = ((reinterpret_cast<uintptr_t>(g) | (uintptr_t)(g_pitch * 4) | reinterpret_cast<uintptr_t>(x) |
+                      (uintptr_t)(x_pitch * esz)) & 15) == 0;
+    kfn<<<grid, 256, smem, s>>>(g, g_pitch, x, x_dt, x_pitch, W, H, kh, border, bvf, vec, partials);
     return cuda_fail(cudaGetLastError(), "tap gradient partials");
 }
 
-static imcl_status wgrad_any(const float* g, int64_t g_pitch, const void* x, int x_dtype, int64_t x_pitch_b, int W,
-                             int H, int kw, int kh, int border, float bv, float* partials, cudaStream_t s) {
-    switch (x_dtype) {
-        case IMCL_F32:
-            return wgrad_partials<float>(g, g_pitch, static_cast<const float*>(x), x_pitch_b / 4, W, H, kw, kh, border,
-                                         bv, partials, s);
-        case IMCL_F16:
-            return wgrad_partials<__half>(g, g_pitch, static_cast<const __half*>(x), x_pitch_b / 2, W, H, kw, kh, border,
-                                          bv, partials, s);
-        case IMCL_BF16:
-            return wgrad_partials<__nv_bfloat16>(g, g_pitch, static_cast<const __nv_bfloat16*>(x), x_pitch_b / 2, W, H,
-                                                 kw, kh, border, bv, partials, s);
-        default: return fail(IMCL_ERR_UNSUPPORTED, "tap gradient: pixel type");
+// Per-CTA partial sums of a kw x kh tap gradient; x of type x_dt with pitch in elements.
+// `grid` CTAs write partials[0 .. grid * kw * kh).
+static imcl_status wgrad_partials(const float* g, int64_t g_pitch, const void* x, int x_dt, int64_t x_pitch, int W,
+                                  int H, int kw, int kh, int border, float bv, float* partials, int grid,
+                                  cudaStream_t s) {
+    if (kw % 2 == 0 || kw > 33 || kh < 1 || kh > 33)
+        return fail(IMCL_ERR_UNSUPPORTED, "tap gradient: odd kw and kh up to 33");
+    // the constant as the pixel type reads it back
+    float bvf = bv;
+    if (x_dt == IMCL_F16) bvf = __half2float(__float2half_rn(bv));
+    else if (x_dt == IMCL_BF16) bvf = __bfloat162float(__float2bfloat16_rn(bv));
+#define IMCL_WG(K) \
+    case K: return wgrad_launch<K>(g, g_pitch, x, x_dt, x_pitch, W, H, kh, border, bvf, partials, grid, s);
+    switch (kw) {
+        IMCL_WG(1) IMCL_WG(3) IMCL_WG(5) IMCL_WG(7) IMCL_WG(9) IMCL_WG(11) IMCL_WG(13) IMCL_WG(15)
+        IMCL_WG(17) IMCL_WG(19) IMCL_WG(21) IMCL_WG(23) IMCL_WG(25) IMCL_WG(27) IMCL_WG(29) IMCL_WG(31) IMCL_WG(33)
+        default: return fail(IMCL_ERR_UNSUPPORTED, "tap gradient: tap row length");
     }
+#undef IMCL_WG
+}
+
+static imcl_status wgrad_any(const float* g, int64_t g_pitch, const void* x, int x_dtype, int64_t x_pitch_b, int W,
+                             int H, int kw, int kh, int border, float bv, float* partials, int grid, cudaStream_t s) {
+    if (x_dtype != IMCL_F32 && x_dtype != IMCL_F16 && x_dtype != IMCL_BF16)
+        return fail(IMCL_ERR_UNSUPPORTED, "tap gradient: pixel type");
+    const int64_t esz = x_dtype == IMCL_F32 ? 4 : 2;
+    return wgrad_partials(g, g_pitch, x, x_dtype, x_pitch_b / esz, W, H, kw, kh, border, bv, partials, grid, s);
 }
 
 static imcl_status finalize(const float* partials, int nparts, int ntaps, float* out, cudaStream_t s) {
@@ -160,6 +184,7 @@ imcl_status conv2d_backward_run(const BwdArgs& b, cudaStream_t s) {
     float* ws = static_cast<float*>(b.workspace);
     float* tap_slot = ws;
     float* partials = ws + kTapScratch;
+    const int wgrid = wgrad_launch_grid(W, H, f.dev);
     if (b.dx) {
         TapSet t;
         IMCL_TRY(make_taps(static_cast<const float*>(f.taps), n, f.taps_mem, tap_slot, s, &t));
@@ -174,8 +199,8 @@ imcl_status conv2d_backward_run(const BwdArgs& b, cudaStream_t s) {
     }
     if (b.dw0) {
         IMCL_TRY(wgrad_any(b.g, b.g_pitch_b / 4, f.in, f.in_dtype, f.in_pitch_b, W, H, f.kw, f.kh, f.border,
-                           (float)f.border_value, partials, s));
-        IMCL_TRY(finalize(partials, wgrad_grid(W, H), n, b.dw0, s));
+                           (float)f.border_value, partials, wgrid, s));
+        IMCL_TRY(finalize(partials, wgrid, n, b.dw0, s));
     }
     return IMCL_OK;
 }
@@ -191,6 +216,7 @@ imcl_status sepconv_backward_run(const BwdArgs& b, cudaStream_t s) {
     float* DT = ws + pf;
     float* tap_slot = ws + 2 * pf;
     float* partials = tap_slot + kTapScratch;
+    const int wgrid = wgrad_launch_grid(W, H, f.dev);
     const float* one = nullptr;
     IMCL_TRY(unit_tap(f.taps_mem, tap_slot + 4 * kMaxAdjTaps, s, &one));
     TapSet tr, tc;
@@ -224,8 +250,8 @@ imcl_status sepconv_backward_run(const BwdArgs& b, cudaStream_t s) {
     }
     if (b.dw0) {  // drow[i] = sum dt(p) x_b(p + i - rr)
         IMCL_TRY(wgrad_any(DT, pp_b / 4, f.in, f.in_dtype, f.in_pitch_b, W, H, nr, 1, f.border,
-                           (float)f.border_value, partials, s));
-        IMCL_TRY(finalize(partials, wgrad_grid(W, H), nr, b.dw0, s));
+                           (float)f.border_value, partials, wgrid, s));
+        IMCL_TRY(finalize(partials, wgrid, nr, b.dw0, s));
     }
     if (b.dw1) {  // dcol[j] = sum g(p) t_b(p + j - rc), t the forward row pass
         ConvCall t = f;
@@ -238,8 +264,8 @@ imcl_status sepconv_backward_run(const BwdArgs& b, cudaStream_t s) {
         t.ws_bytes = 0;
         IMCL_TRY(sep_run_fused(t, s));
         IMCL_TRY(wgrad_any(b.g, b.g_pitch_b / 4, T, IMCL_F32, pp_b, W, H, 1, nc, f.border, (float)f.border_value,
-                           partials, s));
-        IMCL_TRY(finalize(partials, wgrad_grid(W, H), nc, b.dw1, s));
+                           partials, wgrid, s));
+        IMCL_TRY(finalize(partials, wgrid, nc, b.dw1, s));
     }
     return IMCL_OK;
 }
@@ -261,7 +287,7 @@ imcl_status harris_backward_run(const BwdArgs& b, cudaStream_t s) {
     const float* sx = static_cast<const float*>(f.taps);
     const float* sy = static_cast<const float*>(f.taps2);
     const float* gw = static_cast<const float*>(f.taps3);
-    const int grid = wgrad_grid(W, H);
+    const int grid = wgrad_launch_grid(W, H, f.dev);
     dim3 eg((W + 255) / 256, H);
     // an even window runs as the next odd one with a zero last row and column; its
     // gradient is the top-left src x src block of that window's gradient
@@ -309,8 +335,8 @@ imcl_status harris_backward_run(const BwdArgs& b, cudaStream_t s) {
     // window gradient: sum over the three channels
     if (b.dw2) {
         for (int ch = 0; ch < 3; ++ch)
-            IMCL_TRY(wgrad_partials<float>(S[ch], pp, P[ch], pp, W, H, wk, wk, IMCL_BORDER_CLAMP, 0.f,
-                                           partials + (size_t)ch * grid * wk * wk, s));
+            IMCL_TRY(wgrad_partials(S[ch], pp, P[ch], IMCL_F32, pp, W, H, wk, wk, IMCL_BORDER_CLAMP, 0.f,
+                                    partials + (size_t)ch * grid * wk * wk, grid, s));
         IMCL_TRY(finalize(partials, 3 * grid, wk * wk, dwin_pad ? dwin_pad : b.dw2, s));
         if (dwin_pad)
             IMCL_TRY(cuda_fail(cudaMemcpy2DAsync(b.dw2, sizeof(float) * src, dwin_pad, sizeof(float) * wk,
@@ -350,13 +376,13 @@ imcl_status harris_backward_run(const BwdArgs& b, cudaStream_t s) {
         IMCL_TRY(edges_2d(b.dx, b.dx_pitch_b / 4, S[0], pp, sx, S[1], pp, sy, W, H, 3, 3, f.taps_mem, s));
     }
     if (b.dw0) {
-        IMCL_TRY(wgrad_partials<float>(S[0], pp, static_cast<const float*>(f.in), f.in_pitch_b / 4, W, H, 3, 3,
-                                       IMCL_BORDER_CLAMP, 0.f, partials, s));
+        IMCL_TRY(wgrad_partials(S[0], pp, f.in, IMCL_F32, f.in_pitch_b / 4, W, H, 3, 3, IMCL_BORDER_CLAMP, 0.f,
+                                partials, grid, s));
         IMCL_TRY(finalize(partials, grid, 9, b.dw0, s));
     }
     if (b.dw1) {
-        IMCL_TRY(wgrad_partials<float>(S[1], pp, static_cast<const float*>(f.in), f.in_pitch_b / 4, W, H, 3, 3,
-                                       IMCL_BORDER_CLAMP, 0.f, partials, s));
+        IMCL_TRY(wgrad_partials(S[1], pp, f.in, IMCL_F32, f.in_pitch_b / 4, W, H, 3, 3, IMCL_BORDER_CLAMP, 0.f,
+                                partials, grid, s));
         IMCL_TRY(finalize(partials, grid, 9, b.dw1, s));
     }
     return IMCL_OK;

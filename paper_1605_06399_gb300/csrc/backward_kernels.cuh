@@ -21,7 +21,7 @@
 
 namespace imcl {
 
-constexpr int kWgTileW = 64, kWgTileH = 32;   // tile of the tap-gradient reduction
+constexpr int kWgTileW = 128, kWgTileH = 64;  // tile of the tap-gradient reduction
 constexpr int kWgMaxParts = 1024;             // CTAs (partial sums per tap) at most
 constexpr int kMaxAdjTaps = 33 * 33;
 
@@ -102,71 +102,204 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// Per-CTA partial sums of dw[j][i] = sum_p g(p) x_b(p + (i - rx, j - ry)) (kw, kh <= 33,
-// kw*kh <= 1089) over the CTA's tiles (static assignment t = blockIdx.x + k gridDim.x).
-// partials[blockIdx.x * kw*kh + tap].
-template <typename Tx>
-__global__ void __launch_bounds__(256)
-    k_wgrad_partial(const float* g, long long g_pitch, const Tx* x, long long x_pitch, int W, int H, int kw, int kh,
-                    int border, float bv, float* partials) {
+// Per-CTA partial sums of dw[j][i] = sum_p g(p) x_b(p + (i - rx, j - ry)), KW taps per
+// tap row (compile time, odd, <= 33), kh tap rows (runtime, <= 33); x is f32, f16 or
+// bf16 (x_dt), bvf the constant border value as that type reads back in f32.  vec: g and
+// x rows start on 16-byte boundaries, so tiles inside the image stage with 16-byte loads.  A CTA stages a
+// kWgTileW x kWgTileH tile of g and the matching (kWgTileH + kh - 1) x (kWgTileW + KW - 1)
+// region of x (boundary rule applied) in shared memory.  The tile splits into 4 x 8
+// pixel blocks; a thread owns JR consecutive tap rows and every column of them (JR x KW
+// accumulators) and walks its blocks: the block's 32 g values stay in registers while
+// the 8 + JR - 1 x rows it meets stream through, each x row feeding every (block row,
+// tap row) pair it serves -- about 27 FMAs per shared-memory load for 11 x 11 taps.
+// Lanes of a warp take neighbouring blocks of one block row, so their 16-byte loads are
+// contiguous (no bank conflicts).  Tiles go to CTAs statically (t = blockIdx.x + k
+// gridDim.x), per-thread sums run in a fixed order and the threads of a tap-row group
+// are combined in a fixed order: partials[blockIdx.x * KW*kh + tap], deterministic.
+constexpr int kWgLx = 4, kWgLy = 8;           // pixels of a thread's block (x, y)
+
+template <int KW>
+struct WgCfg {
+    static constexpr int JR = KW > 15 ? 1 : (48 / KW < 8 ? 48 / KW : 8);   // tap rows per thread
+    static constexpr int XQ = (kWgLx + KW - 1 + 3) / 4;                    // float4s per x row
+    static constexpr int XW = kWgTileW - kWgLx + 4 * XQ;                   // staged x row pitch
+};
+
+template <int KW>
+constexpr int wgrad_smem_bytes(int kh, int nth) {
+    return 4 * ((kWgTileW * kWgTileH + WgCfg<KW>::XW * (kWgTileH + kh - 1)) > nth * WgCfg<KW>::JR * KW
+                    ? (kWgTileW * kWgTileH + WgCfg<KW>::XW * (kWgTileH + kh - 1))
+                    : nth * WgCfg<KW>::JR * KW);
+}
+
+// one x pixel of type x_dt (f32, f16 or bf16) widened to f32
+__device__ __forceinline__ float load_px_f32(const void* x, int x_dt, long long o) {
+    if (x_dt == IMCL_F32) return static_cast<const float*>(x)[o];
+    if (x_dt == IMCL_F16) return __half2float(static_cast<const __half*>(x)[o]);
+    return __bfloat162float(static_cast<const __nv_bfloat16*>(x)[o]);
+}
+
+template <int KW>
+__global__ void __launch_bounds__(256, 2)
+    k_wgrad_partial(const float* g, long long g_pitch, const void* x, int x_dt, long long x_pitch, int W, int H,
+                    int kh, int border, float bvf, int vec, float* partials) {
     extern __shared__ __align__(16) float wsm[];
+    constexpr int JR = WgCfg<KW>::JR, XQ = WgCfg<KW>::XQ, XW = WgCfg<KW>::XW;
+    constexpr int LX = kWgLx, LY = kWgLy, BX = kWgTileW / LX, NB = BX * (kWgTileH / LY);
     const int tid = threadIdx.x, nth = blockDim.x;
-    const int rx = (kw - 1) / 2, ry = (kh - 1) / 2;
-    const int XW = kWgTileW + kw - 1, XH = kWgTileH + kh - 1;
+    const int rx = (KW - 1) / 2, ry = (kh - 1) / 2;
+    const int XH = kWgTileH + kh - 1;
     float* gs = wsm;                                  // kWgTileH x kWgTileW
     float* xs = gs + kWgTileW * kWgTileH;             // XH x XW
-    float* red = xs + XW * XH;                        // reduction scratch, nth * 4
-    const int cw = (kw + 3) / 4;                      // groups of 4 taps per tap row
-    const int ngroups = kh * cw;
-    const int reps = nth / ngroups > 0 ? nth / ngroups : 1;
-    const int gi = tid % ngroups, rep = tid / ngroups;
-    const bool active = rep < reps && tid < ngroups * reps;
-    const int j = gi / cw, i0 = (gi % cw) * 4;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const int G = (kh + JR - 1) / JR;                 // tap-row groups
+    const int T = nth / G;                            // threads per group
+    const int grp = tid / T, lt = tid - grp * T;
+    const bool active = grp < G;
+    const int j0 = grp * JR;
+    float acc[JR][KW];
+#pragma unroll
+    for (int jr = 0; jr < JR; ++jr)
+#pragma unroll
+        for (int i = 0; i < KW; ++i) acc[jr][i] = 0.f;
     const int tiles_x = (W + kWgTileW - 1) / kWgTileW, tiles_y = (H + kWgTileH - 1) / kWgTileH;
-    const Tx bvt = Store<Tx, float>::cvt(bv);
     for (int t = blockIdx.x; t < tiles_x * tiles_y; t += gridDim.x) {
         const int x0 = (t % tiles_x) * kWgTileW, y0 = (t / tiles_x) * kWgTileH;
         __syncthreads();
-        for (int k = tid; k < kWgTileW * kWgTileH; k += nth) {
-            const int r = k / kWgTileW, c = k % kWgTileW;
-            gs[k] = (x0 + c < W && y0 + r < H) ? g[(long long)(y0 + r) * g_pitch + x0 + c] : 0.f;
+        if (vec && x0 + kWgTileW <= W && y0 + kWgTileH <= H) {
+            // whole g tile inside: 16-byte loads, several in flight per thread
+            // all of a thread's loads first, then its stores: 4 in flight per thread
+            constexpr int NC = kWgTileW / 4, NB4 = 4;
+            for (int k0 = 0; k0 < NC * kWgTileH; k0 += NB4 * nth) {
+                float4 q[NB4];
+#pragma unroll
+                for (int u = 0; u < NB4; ++u) {
+                    const int k = k0 + u * nth + tid;
+                    if (k < NC * kWgTileH) {
+                        const int r = k / NC, c = (k - r * NC) * 4;
+                        q[u] = __ldg(reinterpret_cast<const float4*>(g + (long long)(y0 + r) * g_pitch + x0 + c));
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < NB4; ++u) {
+                    const int k = k0 + u * nth + tid;
+                    if (k < NC * kWgTileH) {
+                        const int r = k / NC, c = (k - r * NC) * 4;
+                        *reinterpret_cast<float4*>(gs + r * kWgTileW + c) = q[u];
+                    }
+                }
+            }
+        } else {
+            for (int k = tid; k < kWgTileW * kWgTileH; k += nth) {
+                const int r = k / kWgTileW, c = k - r * kWgTileW;
+                gs[k] = (x0 + c < W && y0 + r < H) ? g[(long long)(y0 + r) * g_pitch + x0 + c] : 0.f;
+            }
         }
-        for (int k = tid; k < XW * XH; k += nth) {
-            const int r = k / XW, c = k % XW;
-            const int gx = x0 - rx + c, gy = y0 - ry + r;
-            float v;
-            if (gx >= 0 && gx < W && gy >= 0 && gy < H) v = to_acc(x[(long long)gy * x_pitch + gx]);
-            else if (border == IMCL_BORDER_CONSTANT) v = to_acc(bvt);
-            else v = to_acc(x[(long long)clampi(gy, 0, H - 1) * x_pitch + clampi(gx, 0, W - 1)]);
-            xs[k] = v;
+        const int sx0 = x0 - rx, sy0 = y0 - ry;
+        const int epc = x_dt == IMCL_F32 ? 4 : 8;                     // elements per 16 bytes
+        if (vec && sx0 >= 0 && sy0 >= 0 && round_up(sx0 + XW, epc) <= W && sy0 + XH <= H) {
+            // whole x region inside, whole 16-byte chunks too: aligned loads, each element
+            // to its column
+            const int a0 = sx0 - sx0 % epc;
+            const int nch = (sx0 + XW - a0 + epc - 1) / epc;
+            const char* xb = static_cast<const char*>(x);
+            const int esz = x_dt == IMCL_F32 ? 4 : 2;
+            constexpr int NB16 = 4;    // 16-byte loads in flight per thread
+            for (int k0 = 0; k0 < nch * XH; k0 += NB16 * nth) {
+                uint4 q[NB16];
+#pragma unroll
+                for (int u = 0; u < NB16; ++u) {
+                    const int k = k0 + u * nth + tid;
+                    if (k < nch * XH) {
+                        const int r = k / nch, a = a0 + (k - r * nch) * epc;
+                        q[u] = __ldg(reinterpret_cast<const uint4*>(xb + ((long long)(sy0 + r) * x_pitch + a) * esz));
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < NB16; ++u) {
+                    const int k = k0 + u * nth + tid;
+                    if (k < nch * XH) {
+                        const int r = k / nch, a = a0 + (k - r * nch) * epc;
+                        float v[8];
+                        if (x_dt == IMCL_F32) {
+                            v[0] = __uint_as_float(q[u].x); v[1] = __uint_as_float(q[u].y);
+                            v[2] = __uint_as_float(q[u].z); v[3] = __uint_as_float(q[u].w);
+                            v[4] = v[5] = v[6] = v[7] = 0.f;
+                        } else {
+                            const uint32_t w[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+                            if (x_dt == IMCL_F16) unpack_words<__half, 8>(w, v);
+                            else unpack_words<__nv_bfloat16, 8>(w, v);
+                        }
+                        float* row = xs + r * XW;
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const int c = a + e - sx0;
+                            if (e < epc && c >= 0 && c < XW) row[c] = v[e];
+                        }
+                    }
+                }
+            }
+        } else {
+            for (int k = tid; k < XW * XH; k += nth) {
+                const int r = k / XW, c = k - r * XW;
+                const int gx = sx0 + c, gy = sy0 + r;
+                float v;
+                if (gx >= 0 && gx < W && gy >= 0 && gy < H) v = load_px_f32(x, x_dt, (long long)gy * x_pitch + gx);
+                else if (border == IMCL_BORDER_CONSTANT) v = bvf;
+                else v = load_px_f32(x, x_dt, (long long)clampi(gy, 0, H - 1) * x_pitch + clampi(gx, 0, W - 1));
+                xs[k] = v;
+            }
         }
         __syncthreads();
-        if (active) {
-            for (int py = rep; py < kWgTileH; py += reps) {
-                const float* xr = xs + (py + j) * XW + i0;
-                const float* gr = gs + py * kWgTileW;
-#pragma unroll 4
-                for (int px = 0; px < kWgTileW; ++px) {
-                    const float gv = gr[px];
+        if (!active) continue;
+        for (int b = lt; b < NB; b += T) {
+            const int by = b / BX, bxx = b - by * BX;
+            const int px0 = bxx * LX, py0 = by * LY;
+            float gv[LY][LX];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (i0 + k < kw) acc[k] = __fmaf_rn(gv, xr[px + k], acc[k]);
+            for (int yy = 0; yy < LY; ++yy) {
+                const float4 q = *reinterpret_cast<const float4*>(gs + (py0 + yy) * kWgTileW + px0);
+                gv[yy][0] = q.x; gv[yy][1] = q.y; gv[yy][2] = q.z; gv[yy][3] = q.w;
+            }
+            // x row (py0 + r + j0) serves block row yy = r - jr for each tap row jr
+#pragma unroll
+            for (int r = 0; r < LY + JR - 1; ++r) {
+                float xv[4 * XQ];
+                const float* xr = xs + (py0 + r + j0) * XW + px0;
+                const bool row_used = r < LY || j0 + (r - LY + 1) < kh;   // some jr < kh with yy = r - jr < LY
+                if (row_used) {
+#pragma unroll
+                    for (int q = 0; q < XQ; ++q) {
+                        const float4 v = *reinterpret_cast<const float4*>(xr + 4 * q);
+                        xv[4 * q] = v.x; xv[4 * q + 1] = v.y; xv[4 * q + 2] = v.z; xv[4 * q + 3] = v.w;
+                    }
+#pragma unroll
+                    for (int jr = 0; jr < JR; ++jr) {
+                        const int yy = r - jr;
+                        if (yy >= 0 && yy < LY && j0 + jr < kh) {
+#pragma unroll
+                            for (int i = 0; i < KW; ++i)
+#pragma unroll
+                                for (int p = 0; p < LX; ++p) acc[jr][i] = __fmaf_rn(gv[yy][p], xv[p + i], acc[jr][i]);
+                        }
+                    }
                 }
             }
         }
     }
-    // combine the replicas of each tap group in a fixed order
+    // combine the threads of each tap-row group in a fixed order (the staging area is free)
     __syncthreads();
+    float* red = wsm;                                 // nth x (JR * KW)
 #pragma unroll
-    for (int k = 0; k < 4; ++k) red[tid * 4 + k] = acc[k];
+    for (int jr = 0; jr < JR; ++jr)
+#pragma unroll
+        for (int i = 0; i < KW; ++i) red[tid * JR * KW + jr * KW + i] = active ? acc[jr][i] : 0.f;
     __syncthreads();
-    for (int q = tid; q < kw * kh; q += nth) {
-        const int jj = q / kw, ii = q % kw;
-        const int grp = jj * cw + ii / 4, lane = ii % 4;
-        float s = 0.f;
-        for (int r = 0; r < reps; ++r) s += red[(r * ngroups + grp) * 4 + lane];
-        partials[(long long)blockIdx.x * kw * kh + q] = s;
+    for (int q = tid; q < KW * kh; q += nth) {
+        const int j = q / KW, i = q - j * KW;
+        const int gq = j / JR, jr = j - gq * JR;
+        float sum = 0.f;
+        for (int r = 0; r < T; ++r) sum += red[(gq * T + r) * JR * KW + jr * KW + i];
+        partials[(long long)blockIdx.x * KW * kh + q] = sum;
     }
 }
 
