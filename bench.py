@@ -374,9 +374,29 @@ def extra_stencils(hbm_gbs, fp32_peak, budget):
     out["harris_4096_fwd"] = _entry(px, tt, tp, 8, flops_fwd, hbm_gbs, fp32_peak, res["variant"])
     gR = torch.randn(4096, 4096, device=dev)
     tb = _median_ms(lambda: ops.harris_backward(gR, x, sx, sy, win, k), 5, calls=2)
-    out["harris_4096_bwd"] = _entry(px, tb, None, 8, 0, hbm_gbs, fp32_peak,
-                                    note="adjoint of the fused forward: image, Sobel and window gradients")
+    # algorithmic: read I and gR, write dI (12 B/px); forward recomputed (flops_fwd) plus
+    # the window adjoint and window gradient (2 x 3 x 2 x 25), the Sobel adjoint and
+    # Sobel gradients (2 x 2 x 2 x 9) and the product / response derivatives (~16)
+    flops_bwd = flops_fwd + 2 * 3 * 2 * 25 + 2 * 2 * 2 * 9 + 16
+    out["harris_4096_bwd"] = _entry(px, tb, None, 12, flops_bwd, hbm_gbs, fp32_peak,
+                                    note="image, Sobel and window gradients; ~20 launches over workspace planes")
     del x, y, ws, gR
+
+    # conv2d and separable backward on the 8192^2 f32 image: input and tap gradients
+    img, w11 = synth.workload_conv_f32(11)
+    x = torch.from_numpy(img).to(dev)
+    gO = torch.randn_like(x)
+    tb = _median_ms(lambda: ops.conv2d_backward(gO, x, w11), 5, calls=2)
+    # read g and x, write dx (12 B/px); dx and dw are each a K^2 correlation (4 K^2 flop/px)
+    out["conv2d_bwd_11x11_8192_f32"] = _entry(SIDE * SIDE, tb, None, 12, 4 * 121, hbm_gbs, fp32_peak,
+                                              note="dx (zero-border correlation + clamp folds) and dw (two-stage)")
+    t5 = synth.gaussian_taps(2)
+    tb = _median_ms(lambda: ops.sepconv_backward(gO, x, t5, t5), 5, calls=2)
+    # dx (two 1D passes), drow and dcol (a 1D pass each to rebuild their operand, then a
+    # dot product per tap): 6 x 2 x 5 flop/px; read g and x, write dx
+    out["sep_bwd_R2_8192_f32"] = _entry(SIDE * SIDE, tb, None, 12, 6 * 2 * 5, hbm_gbs, fp32_peak,
+                                        note="dx, row-tap and column-tap gradients")
+    del x, gO
 
     # the paper's Harris shape (§6): 5120x5120 f32 with a 2x2 box block (offsets -1, 0)
     img, sx, sy, _, k = synth.workload_harris(5120, 5120)
@@ -426,8 +446,15 @@ def extra_stencils(hbm_gbs, fp32_peak, budget):
                                "one untuned launch per image")
     e["roofline_frac"] = roof_ms / tf
     out["batch256_f16_fwd"] = e
-    out["batch256_f16_bwd"] = _entry(info["pixels"], tbw, None, 0, 0, hbm_gbs, fp32_peak,
-                                     note="input and tap gradients of every image, one graph launch")
+    # backward, per image: read the f32 upstream gradient and the f16 input, write the f32
+    # input gradient (10 B/px); dx and dw each a correlation of the forward's size
+    bw_flops = [it.width * it.height * 2 * (2 * it.k * it.k if it.op == "conv" else 4 * it.k) for it in items]
+    roof_bwd_ms = sum(max(it.width * it.height * 10 / (hbm_gbs * 1e9), f / (fp32_peak * 1e12))
+                      for it, f in zip(items, bw_flops)) * 1e3
+    eb = _entry(info["pixels"], tbw, None, 10.0, sum(bw_flops) / info["pixels"], hbm_gbs, fp32_peak,
+                note="input and tap gradients of every image, one graph launch (three persistent phases)")
+    eb["roofline_frac"] = roof_bwd_ms / tbw
+    out["batch256_f16_bwd"] = eb
     b.close()
     return out
 

@@ -17,7 +17,7 @@
 // deterministic run to run.
 #pragma once
 
-#include "tile_common.cuh"
+#include "wgrad_tile.cuh"
 
 namespace imcl {
 
@@ -104,31 +104,18 @@ __global__ void __launch_bounds__(256)
 
 // Per-CTA partial sums of dw[j][i] = sum_p g(p) x_b(p + (i - rx, j - ry)), KW taps per
 // tap row (compile time, odd, <= 33), kh tap rows (runtime, <= 33); x is f32, f16 or
-// bf16 (x_dt), bvf the constant border value as that type reads back in f32.  vec: g and
-// x rows start on 16-byte boundaries, so tiles inside the image stage with 16-byte loads.  A CTA stages a
-// kWgTileW x kWgTileH tile of g and the matching (kWgTileH + kh - 1) x (kWgTileW + KW - 1)
-// region of x (boundary rule applied) in shared memory.  The tile splits into 4 x 8
-// pixel blocks; a thread owns JR consecutive tap rows and every column of them (JR x KW
-// accumulators) and walks its blocks: the block's 32 g values stay in registers while
-// the 8 + JR - 1 x rows it meets stream through, each x row feeding every (block row,
-// tap row) pair it serves -- about 27 FMAs per shared-memory load for 11 x 11 taps.
-// Lanes of a warp take neighbouring blocks of one block row, so their 16-byte loads are
-// contiguous (no bank conflicts).  Tiles go to CTAs statically (t = blockIdx.x + k
-// gridDim.x), per-thread sums run in a fixed order and the threads of a tap-row group
-// are combined in a fixed order: partials[blockIdx.x * KW*kh + tap], deterministic.
-constexpr int kWgLx = 4, kWgLy = 8;           // pixels of a thread's block (x, y)
-
-template <int KW>
-struct WgCfg {
-    static constexpr int JR = KW > 15 ? 1 : (48 / KW < 8 ? 48 / KW : 8);   // tap rows per thread
-    static constexpr int XQ = (kWgLx + KW - 1 + 3) / 4;                    // float4s per x row
-    static constexpr int XW = kWgTileW - kWgLx + 4 * XQ;                   // staged x row pitch
-};
-
+// bf16 (x_dt), bvf the constant border value as that type reads back in f32.  A CTA
+// stages a kWgTileW x kWgTileH tile of g and the matching region of x (boundary rule
+// applied) in shared memory -- with 16-byte loads for tiles inside the image when the
+// rows are 16-byte aligned (vec) -- and reduces it with wgrad_accumulate (4 x 8 pixel
+// blocks, JR tap rows x KW columns per thread; about 27 FMAs per shared-memory load for
+// 11 x 11 taps).  Tiles go to CTAs statically (t = blockIdx.x + k gridDim.x) and the
+// threads are combined in a fixed order: partials[blockIdx.x * KW*kh + tap],
+// deterministic.
 template <int KW>
 constexpr int wgrad_smem_bytes(int kh, int nth) {
-    return 4 * ((kWgTileW * kWgTileH + WgCfg<KW>::XW * (kWgTileH + kh - 1)) > nth * WgCfg<KW>::JR * KW
-                    ? (kWgTileW * kWgTileH + WgCfg<KW>::XW * (kWgTileH + kh - 1))
+    return 4 * ((kWgTileW * kWgTileH + wg_xpitch<KW>(kWgTileW) * (kWgTileH + kh - 1)) > nth * WgCfg<KW>::JR * KW
+                    ? (kWgTileW * kWgTileH + wg_xpitch<KW>(kWgTileW) * (kWgTileH + kh - 1))
                     : nth * WgCfg<KW>::JR * KW);
 }
 
@@ -144,8 +131,7 @@ __global__ void __launch_bounds__(256, 2)
     k_wgrad_partial(const float* g, long long g_pitch, const void* x, int x_dt, long long x_pitch, int W, int H,
                     int kh, int border, float bvf, int vec, float* partials) {
     extern __shared__ __align__(16) float wsm[];
-    constexpr int JR = WgCfg<KW>::JR, XQ = WgCfg<KW>::XQ, XW = WgCfg<KW>::XW;
-    constexpr int LX = kWgLx, LY = kWgLy, BX = kWgTileW / LX, NB = BX * (kWgTileH / LY);
+    constexpr int JR = WgCfg<KW>::JR, XW = wg_xpitch<KW>(kWgTileW);
     const int tid = threadIdx.x, nth = blockDim.x;
     const int rx = (KW - 1) / 2, ry = (kh - 1) / 2;
     const int XH = kWgTileH + kh - 1;
@@ -250,57 +236,10 @@ __global__ void __launch_bounds__(256, 2)
             }
         }
         __syncthreads();
-        if (!active) continue;
-        for (int b = lt; b < NB; b += T) {
-            const int by = b / BX, bxx = b - by * BX;
-            const int px0 = bxx * LX, py0 = by * LY;
-            float gv[LY][LX];
-#pragma unroll
-            for (int yy = 0; yy < LY; ++yy) {
-                const float4 q = *reinterpret_cast<const float4*>(gs + (py0 + yy) * kWgTileW + px0);
-                gv[yy][0] = q.x; gv[yy][1] = q.y; gv[yy][2] = q.z; gv[yy][3] = q.w;
-            }
-            // x row (py0 + r + j0) serves block row yy = r - jr for each tap row jr
-#pragma unroll
-            for (int r = 0; r < LY + JR - 1; ++r) {
-                float xv[4 * XQ];
-                const float* xr = xs + (py0 + r + j0) * XW + px0;
-                const bool row_used = r < LY || j0 + (r - LY + 1) < kh;   // some jr < kh with yy = r - jr < LY
-                if (row_used) {
-#pragma unroll
-                    for (int q = 0; q < XQ; ++q) {
-                        const float4 v = *reinterpret_cast<const float4*>(xr + 4 * q);
-                        xv[4 * q] = v.x; xv[4 * q + 1] = v.y; xv[4 * q + 2] = v.z; xv[4 * q + 3] = v.w;
-                    }
-#pragma unroll
-                    for (int jr = 0; jr < JR; ++jr) {
-                        const int yy = r - jr;
-                        if (yy >= 0 && yy < LY && j0 + jr < kh) {
-#pragma unroll
-                            for (int i = 0; i < KW; ++i)
-#pragma unroll
-                                for (int p = 0; p < LX; ++p) acc[jr][i] = __fmaf_rn(gv[yy][p], xv[p + i], acc[jr][i]);
-                        }
-                    }
-                }
-            }
-        }
+        if (active) wgrad_accumulate<KW>(gs, kWgTileW, xs, XW, kWgTileW, kWgTileH, kh, j0, lt, T, acc);
     }
     // combine the threads of each tap-row group in a fixed order (the staging area is free)
-    __syncthreads();
-    float* red = wsm;                                 // nth x (JR * KW)
-#pragma unroll
-    for (int jr = 0; jr < JR; ++jr)
-#pragma unroll
-        for (int i = 0; i < KW; ++i) red[tid * JR * KW + jr * KW + i] = active ? acc[jr][i] : 0.f;
-    __syncthreads();
-    for (int q = tid; q < KW * kh; q += nth) {
-        const int j = q / KW, i = q - j * KW;
-        const int gq = j / JR, jr = j - gq * JR;
-        float sum = 0.f;
-        for (int r = 0; r < T; ++r) sum += red[(gq * T + r) * JR * KW + jr * KW + i];
-        partials[(long long)blockIdx.x * KW * kh + q] = sum;
-    }
+    wgrad_combine<KW>(acc, active, wsm, kh, T, partials + (long long)blockIdx.x * KW * kh, tid, nth);
 }
 
 // out[tap] = (accumulate ? out[tap] : 0) + sum over nparts partial sums, as a fixed tree.

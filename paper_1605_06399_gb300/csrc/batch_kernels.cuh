@@ -13,6 +13,7 @@
 #pragma once
 
 #include "tile_common.cuh"
+#include "wgrad_tile.cuh"
 
 namespace imcl {
 
@@ -405,18 +406,34 @@ __device__ void batch_conv_dx_tile(const BImg& im, int x0, int y0, int bx, int b
         __syncthreads();
     }
     if (im.gtaps) {
-        const int rx = (im.kw - 1) / 2, ry = (im.kh - 1) / 2;
-        const int XW = TW + im.kw - 1, XH = TH + im.kh - 1;
+        // the K x K centred tap gradient by the register-blocked reduction; a kw x kh
+        // filter (kw, kh <= K) takes its block of it
+        constexpr int R = (K - 1) / 2, JR = WgCfg<K>::JR;
+        const int XW = wg_xpitch<K>(TW), XH = TH + K - 1;
         float* gs = sm;
         float* xs = gs + TW * TH;
-        float* red = xs + XW * XH;
         stage_region(gs, TW, TH, im.g, IMCL_F32, im.g_pitch, x0, y0, im.W, im.H, IMCL_BORDER_CONSTANT, 0.f, 1, tid, nth,
                      im.g_vec);
-        stage_region(xs, XW, XH, im.in, im.in_dt, im.in_pitch, x0 - rx, y0 - ry, im.W, im.H, im.border, im.bv, 0, tid,
+        stage_region(xs, XW, XH, im.in, im.in_dt, im.in_pitch, x0 - R, y0 - R, im.W, im.H, im.border, im.bv, 0, tid,
                      nth);
         __syncthreads();
+        const int G = (K + JR - 1) / JR, T = nth / G, grp = tid / T, lt = tid - grp * T;
+        const bool active = grp < G;
+        float acc[JR][K];
+#pragma unroll
+        for (int jr = 0; jr < JR; ++jr)
+#pragma unroll
+            for (int i = 0; i < K; ++i) acc[jr][i] = 0.f;
+        if (active) wgrad_accumulate<K>(gs, TW, xs, XW, TW, TH, K, grp * JR, lt, T, acc);
+        float* kk = sm + nth * JR * K;                  // the K x K sums, after the combine scratch
+        wgrad_combine<K>(acc, active, sm, K, T, kk, tid, nth);
         const int tile = (y0 / TH) * im.tiles_x + x0 / TW;
-        tile_wgrad(gs, TW, 0, xs, XW, 0, TW, TH, im.kw, im.kh, red, im.part + (size_t)tile * im.kw * im.kh, tid, nth);
+        const int rx = (im.kw - 1) / 2, ry = (im.kh - 1) / 2;
+        float* out = im.part + (size_t)tile * im.kw * im.kh;
+        for (int q = tid; q < im.kw * im.kh; q += nth) {
+            const int j = q / im.kw, i = q - j * im.kw;
+            out[q] = kk[(j - ry + R) * K + (i - rx + R)];
+        }
     }
 }
 
