@@ -8,6 +8,7 @@
 #include "abi_internal.h"
 #include "backward_internal.h"
 #include "backward_kernels.cuh"
+#include "harris_bwd_kernels.cuh"
 
 namespace imcl {
 
@@ -25,8 +26,14 @@ size_t conv2d_backward_ws(int W, int H, int kw, int kh) {
 size_t sepconv_backward_ws(int W, int H, int nr, int nc) {
     return (2 * plane_floats(W, H) + kTapScratch + (size_t)wgrad_grid(W, H) * std::max(nr, nc)) * sizeof(float);
 }
+// CTAs (tap-gradient partial sets) of the fused Harris adjoint at most
+static int harris_fused_parts(int W, int H) {
+    const int tiles = ((W + kHbTile - 1) / kHbTile) * ((H + kHbTile - 1) / kHbTile);
+    return std::min(tiles, kWgMaxParts);
+}
 size_t harris_backward_ws(int W, int H, int wk) {
-    return (9 * plane_floats(W, H) + kTapScratch + (size_t)3 * wgrad_grid(W, H) * wk * wk) * sizeof(float);
+    const size_t parts = std::max((size_t)3 * wgrad_grid(W, H) * wk * wk, (size_t)harris_fused_parts(W, H) * (wk * wk + 18));
+    return (9 * plane_floats(W, H) + kTapScratch + parts) * sizeof(float);
 }
 
 // ------------------------------------------------------------------ helpers
@@ -271,6 +278,33 @@ imcl_status sepconv_backward_run(const BwdArgs& b, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ Harris
+template <int WK>
+static imcl_status harris_bwd_fused(const BwdArgs& b, const float* sx, const float* sy, const float* gw, int grid,
+                                    float* pw, float* psx, float* psy, cudaStream_t s) {
+    const ConvCall& f = b.fwd;
+    HbTaps<WK> tp;
+    memset(&tp, 0, sizeof tp);
+    const float *sxd = nullptr, *syd = nullptr, *gwd = nullptr;
+    if (f.taps_mem == IMCL_MEM_HOST) {
+        memcpy(tp.sx, sx, sizeof tp.sx);
+        memcpy(tp.sy, sy, sizeof tp.sy);
+        memcpy(tp.g, gw, sizeof tp.g);
+    } else {
+        sxd = sx;
+        syd = sy;
+        gwd = gw;
+    }
+    constexpr int smem = HbGeo<WK>::TOTAL * (int)sizeof(float);
+    static_assert(HbGeo<WK>::TOTAL >= 256 * HbGeo<WK>::NTAP, "the tap combine reuses the tile buffers");
+    auto kfn = k_harris_bwd_fused<WK>;
+    imcl_status st = set_smem_limit((const void*)kfn, smem);
+    if (st != IMCL_OK) return st;
+    const int vec = ((reinterpret_cast<uintptr_t>(f.in) | (uintptr_t)f.in_pitch_b) & 15) == 0;
+    kfn<<<grid, 256, smem, s>>>(static_cast<const float*>(f.in), f.in_pitch_b / 4, b.g, b.g_pitch_b / 4, b.dx,
+                                b.dx_pitch_b / 4, f.W, f.H, f.hk, vec, sxd, syd, gwd, tp, pw, psx, psy);
+    return cuda_fail(cudaGetLastError(), "harris backward (fused)");
+}
+
 imcl_status harris_backward_run(const BwdArgs& b, cudaStream_t s) {
     const ConvCall& f = b.fwd;
     const int W = f.W, H = f.H, wk = f.kw, src = f.kh;   // kernel side, caller's window side
@@ -309,7 +343,27 @@ imcl_status harris_backward_run(const BwdArgs& b, cudaStream_t s) {
         if (b.dw2) dwin_pad = tap_slot + 256;
     }
 
-    // forward intermediates: Ix, Iy, P, S
+    if (wk == 3 || wk == 5) {   // one fused tile kernel, then the tap reductions
+        const int hgrid = std::max(1, std::min(harris_fused_parts(W, H), 2 * (f.dev ? f.dev->sm_count : 1)));
+        float* pw = partials;
+        float* psx = pw + (size_t)hgrid * wk * wk;
+        float* psy = psx + (size_t)hgrid * 9;
+        if (wk == 3) IMCL_TRY(harris_bwd_fused<3>(b, sx, sy, gw, hgrid, pw, psx, psy, s));
+        else IMCL_TRY(harris_bwd_fused<5>(b, sx, sy, gw, hgrid, pw, psx, psy, s));
+        if (b.dw2) {
+            IMCL_TRY(finalize(pw, hgrid, wk * wk, dwin_pad ? dwin_pad : b.dw2, s));
+            if (dwin_pad)
+                IMCL_TRY(cuda_fail(cudaMemcpy2DAsync(b.dw2, sizeof(float) * src, dwin_pad, sizeof(float) * wk,
+                                                     sizeof(float) * src, src, cudaMemcpyDeviceToDevice, s),
+                                   "window gradient"));
+        }
+        if (b.dw0) IMCL_TRY(finalize(psx, hgrid, 9, b.dw0, s));
+        if (b.dw1) IMCL_TRY(finalize(psy, hgrid, 9, b.dw1, s));
+        return IMCL_OK;
+    }
+
+    // other window sides: forward intermediates on workspace planes, then each adjoint
+    // step as its own launch.  Forward intermediates: Ix, Iy, P, S
     ConvCall base = f;
     base.kw = base.kh = 3;
     ConvCall c = f32_call(base, static_cast<const float*>(f.in), f.in_pitch_b, IX, pp_b);
