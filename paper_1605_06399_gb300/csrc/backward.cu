@@ -299,9 +299,8 @@ static imcl_status harris_bwd_fused(const BwdArgs& b, const float* sx, const flo
     auto kfn = k_harris_bwd_fused<WK>;
     imcl_status st = set_smem_limit((const void*)kfn, smem);
     if (st != IMCL_OK) return st;
-    const int vec = ((reinterpret_cast<uintptr_t>(f.in) | (uintptr_t)f.in_pitch_b) & 15) == 0;
     kfn<<<grid, 256, smem, s>>>(static_cast<const float*>(f.in), f.in_pitch_b / 4, b.g, b.g_pitch_b / 4, b.dx,
-                                b.dx_pitch_b / 4, f.W, f.H, f.hk, vec, sxd, syd, gwd, tp, pw, psx, psy);
+                                b.dx_pitch_b / 4, f.W, f.H, f.hk, sxd, syd, gwd, tp, pw, psx, psy);
     return cuda_fail(cudaGetLastError(), "harris backward (fused)");
 }
 

@@ -40,7 +40,7 @@ struct HbGeo {
     static constexpr int TB = kHbTile;
     static constexpr int HI = 2 + 2 * RW, HP = 1 + 2 * RW, HS = 1 + RW, HG = 1;
     static constexpr int WI = TB + 2 * HI;                                  // I region rows
-    static constexpr int XI = round_up(HI, 4);                              // I region's left halo (16 B)
+    static constexpr int XI = HI;                                           // I region's left halo
     static constexpr int WIX = TB + 2 * XI;                                 // I region columns
     static constexpr int WP = TB + 2 * HP;                                  // P region side
     static constexpr int WS = TB + 2 * HS;                                  // gS region side
@@ -67,7 +67,7 @@ struct HbGeo {
 template <int WK>
 __global__ void __launch_bounds__(256, 2)
     k_harris_bwd_fused(const float* __restrict__ I, long long i_pitch, const float* __restrict__ gR, long long g_pitch,
-                       float* dI, long long d_pitch, int W, int H, float k, int vec, const float* sx_dev, const float* sy_dev,
+                       float* dI, long long d_pitch, int W, int H, float k, const float* sx_dev, const float* sy_dev,
                        const float* gw_dev, const __grid_constant__ HbTaps<WK> tp, float* part_w, float* part_sx,
                        float* part_sy) {
     using G = HbGeo<WK>;
@@ -104,20 +104,10 @@ __global__ void __launch_bounds__(256, 2)
         const bool border_tile = x0 - HI < 0 || y0 - HI < 0 || x0 + TB + HI > W || y0 + TB + HI > H;
         __syncthreads();   // taps staged / the previous tile's planes are no longer read
         // (1) I on the I region (rows from y0 - HI, columns from x0 - XI), at clamped positions
-        if (vec && x0 - XI >= 0 && x0 - XI + G::WIX <= W) {
-            constexpr int NC = G::WIX / 4;
-            for (int q = tid; q < G::WI * NC; q += nth) {
-                const int r = q / NC, c = (q - r * NC) * 4;
-                const int gy = clampi(y0 - HI + r, 0, H - 1);
-                *reinterpret_cast<float4*>(Is + r * G::PPI + c) =
-                    __ldg(reinterpret_cast<const float4*>(I + (long long)gy * i_pitch + x0 - XI + c));
-            }
-        } else {
-            for (int q = tid; q < G::WI * G::WIX; q += nth) {
-                const int r = q / G::WIX, c = q - r * G::WIX;
-                const int gy = clampi(y0 - HI + r, 0, H - 1), gx = clampi(x0 - XI + c, 0, W - 1);
-                Is[r * G::PPI + c] = I[(long long)gy * i_pitch + gx];
-            }
+        for (int q = tid; q < G::WI * G::WIX; q += nth) {
+            const int r = q / G::WIX, c = q - r * G::WIX;
+            const int gy = clampi(y0 - HI + r, 0, H - 1), gx = clampi(x0 - XI + c, 0, W - 1);
+            Is[r * G::PPI + c] = I[(long long)gy * i_pitch + gx];
         }
         __syncthreads();
         // (2) Ix, Iy and the products on the P region, each at its clamped pixel
