@@ -631,7 +631,7 @@ __device__ void batch_bwd_dispatch(const BImg& im, const BTile& tl, int bx, int 
 
 // Persistent backward phase: CTAs take work items from one list until it is exhausted.
 template <int PY>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 3)
     k_batch_bwd(const BImg* __restrict__ imgs, const BTile* __restrict__ items, int nitems, int* queue, int bx, int by) {
     extern __shared__ __align__(16) float bsm[];
     __shared__ int s_next;
