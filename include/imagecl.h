@@ -337,6 +337,31 @@ imcl_status imagecl_variant_default(const imcl_problem *problem, imcl_variant *o
 imcl_status imagecl_tune(const imcl_problem *problem, double budget_s, int32_t reps,
                          imcl_variant *best, double *best_ms, double *plain_ms, void *stream);
 
+/*
+ * Model-guided tuning (§4: the paper's auto-tuner times a random sample of
+ * configurations, fits an artificial neural network to their run times, predicts the
+ * time of every configuration and runs the best predicted ones).  The space is that of
+ * imagecl_tune (variants x block shapes).  `n_sample` configurations drawn with `seed`
+ * are checked against the PLAIN kernel and timed; a one-hidden-layer network (16 tanh
+ * units) is fitted to their log times from the configuration's axes (one-hot per axis
+ * value); the `n_confirm` untimed configurations it predicts fastest are then checked
+ * and timed, and the fastest of all timed ones is cached as imagecl_tune would.
+ * `report` (nullable) receives the counts, the model's fit and the search's wall time.
+ * Synchronises `stream`.
+ */
+typedef struct {
+    int32_t candidates;    /* configurations in the space                              */
+    int32_t sampled;       /* drawn at random and timed to train the model             */
+    int32_t confirmed;     /* best-predicted configurations timed afterwards           */
+    int32_t valid;         /* timed configurations that launched and passed the check  */
+    double model_rmse;     /* rms error of the fitted log time on the sampled points   */
+    double seconds;        /* wall time of the search                                  */
+} imcl_tune_report;
+
+imcl_status imagecl_tune_model(const imcl_problem *problem, int32_t n_sample, int32_t n_confirm,
+                               int32_t reps, uint64_t seed, imcl_variant *best, double *best_ms,
+                               double *plain_ms, imcl_tune_report *report, void *stream);
+
 /* Store / drop a tuning result by hand (the "force an optimisation" directive of §5). */
 imcl_status imagecl_tune_set(const imcl_problem *problem, const imcl_variant *variant);
 void imagecl_tune_clear(void);

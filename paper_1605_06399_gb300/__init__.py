@@ -5,11 +5,11 @@ The compute path is ``libimagecl.so`` (hand-written sm_103a CUDA behind the C AB
 with ``python -m paper_1605_06399_gb300.build``; calls fail loudly if it is missing.
 """
 from .ops import (conv2d, sepconv, harris, default_variant, device_status, image, problem, tune, tune_clear,
-                  tune_load, tune_save, tune_set, variants, version)
+                  tune_load, tune_model, tune_save, tune_set, variants, version)
 from ._abi import ImclError
 from . import autograd
 from .ops import Batch, conv2d_backward, harris_backward, sepconv_backward
 
 __all__ = ["conv2d", "sepconv", "harris", "default_variant", "device_status", "image", "problem", "tune", "tune_clear",
-           "tune_load", "tune_save", "tune_set", "variants", "version", "ImclError", "autograd", "conv2d_backward",
+           "tune_load", "tune_model", "tune_save", "tune_set", "variants", "version", "ImclError", "autograd", "conv2d_backward",
            "sepconv_backward", "harris_backward", "Batch"]

@@ -77,6 +77,14 @@ class BatchInfo(ctypes.Structure):
                 ("has_backward", c_int32)]
 
 
+class TuneReport(ctypes.Structure):
+    _fields_ = [("candidates", c_int32), ("sampled", c_int32), ("confirmed", c_int32), ("valid", c_int32),
+                ("model_rmse", c_double), ("seconds", c_double)]
+
+    def as_dict(self) -> dict:
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 class ImclError(RuntimeError):
     def __init__(self, status: int, message: str):
         self.status = status
@@ -120,6 +128,8 @@ SIGNATURES = {
     "imagecl_variant_default": (c_int32, [P(Problem), P(Variant)]),
     "imagecl_tune": (c_int32, [P(Problem), c_double, c_int32, P(Variant), P(c_double), P(c_double),
                                c_void_p]),
+    "imagecl_tune_model": (c_int32, [P(Problem), c_int32, c_int32, c_int32, ctypes.c_uint64, P(Variant),
+                                     P(c_double), P(c_double), P(TuneReport), c_void_p]),
     "imagecl_tune_set": (c_int32, [P(Problem), P(Variant)]),
     "imagecl_tune_clear": (None, []),
     "imagecl_tune_save": (c_int32, [ctypes.c_char_p]),

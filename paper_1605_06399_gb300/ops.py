@@ -264,6 +264,20 @@ def default_variant(prob: _abi.Problem) -> dict:
     return v.as_dict()
 
 
+def tune_model(prob: _abi.Problem, n_sample: int = 32, n_confirm: int = 8, reps: int = 3, seed: int = 0,
+               stream=None) -> dict:
+    """Model-guided tuning of ``prob`` (random sample, neural-network cost model, the best
+    predicted confirmed by timing); returns the winner, its time, PLAIN's and the report."""
+    v = _abi.Variant()
+    best_ms, plain_ms = ctypes.c_double(0), ctypes.c_double(0)
+    rep = _abi.TuneReport()
+    check(lib().imagecl_tune_model(ctypes.byref(prob), int(n_sample), int(n_confirm), int(reps), int(seed),
+                                   ctypes.byref(v), ctypes.byref(best_ms), ctypes.byref(plain_ms),
+                                   ctypes.byref(rep), ctypes.c_void_p(stream_handle(stream))))
+    return {"variant": v.as_dict(), "best_ms": best_ms.value, "plain_ms": plain_ms.value,
+            "report": rep.as_dict()}
+
+
 def tune(prob: _abi.Problem, budget_s: float = 20.0, reps: int = 5, stream=None) -> dict:
     """Run the auto-tuner on ``prob``; returns the winner and its time against PLAIN."""
     v = _abi.Variant()

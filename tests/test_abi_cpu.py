@@ -46,9 +46,10 @@ def test_library_exports_every_declared_symbol(lib):
 def test_struct_layout_matches_header(tmp_path):
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "imagecl.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(imcl_image), '
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(imcl_image), '
                    'sizeof(imcl_variant), sizeof(imcl_problem), offsetof(imcl_image, pitch_bytes), '
-                   'sizeof(imcl_batch_item), offsetof(imcl_batch_item, grad_in), sizeof(imcl_batch_info_t));'
+                   'sizeof(imcl_batch_item), offsetof(imcl_batch_item, grad_in), sizeof(imcl_batch_info_t), '
+                   'sizeof(imcl_tune_report), offsetof(imcl_tune_report, model_rmse));'
                    'return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
@@ -57,7 +58,8 @@ def test_struct_layout_matches_header(tmp_path):
     assert sizes == [ctypes.sizeof(_abi.Image), ctypes.sizeof(_abi.Variant),
                      ctypes.sizeof(_abi.Problem), _abi.Image.pitch_bytes.offset,
                      ctypes.sizeof(_abi.BatchItem), _abi.BatchItem.grad_in.offset,
-                     ctypes.sizeof(_abi.BatchInfo)]
+                     ctypes.sizeof(_abi.BatchInfo), ctypes.sizeof(_abi.TuneReport),
+                     _abi.TuneReport.model_rmse.offset]
 
 
 def test_version_and_last_error(lib):
