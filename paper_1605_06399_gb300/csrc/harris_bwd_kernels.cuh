@@ -47,10 +47,12 @@ struct HbGeo {
     static constexpr int WG = TB + 2 * HG;                                  // gI region side
     static constexpr int NSI = (WS + 3) / 4;                                // 4-wide items per gS row
     static constexpr int NGI = (WG + 3) / 4;                                // 4-wide items per gI row
-    static constexpr int PPI = WIX;                                         // row pitches (floats)
-    static constexpr int PPP = round_up(4 * NSI + 2 * RW, 4);
-    static constexpr int PPS = round_up(4 * NGI + 2 * RW, 4) > 4 * NSI ? round_up(4 * NGI + 2 * RW, 4) : 4 * NSI;
-    static constexpr int PPG = 4 * NGI;
+    // row pitches (floats): odd, so that threads walking down a column of items (the
+    // mapping of steps 3 to 5) touch distinct banks
+    static constexpr int PPI = WIX;
+    static constexpr int PPP = (4 * NSI + 2 * RW) | 1;
+    static constexpr int PPS = ((4 * NGI + 2 * RW) > 4 * NSI ? (4 * NGI + 2 * RW) : 4 * NSI) | 1;
+    static constexpr int PPG = (4 * NGI) | 1;
     static constexpr int NTAP = WK * WK + 18;                               // window, Sobel x, Sobel y
     // shared memory (floats): taps, I, Ix Iy Pxx Pyy Pxy, gSxx gSyy gSxy, gIx gIy
     static constexpr int O_TAP = 0;
@@ -137,7 +139,7 @@ __global__ void __launch_bounds__(256, 2)
         __syncthreads();
         // (3) window sums and gS on the gS region, 4 columns per item (zero outside)
         for (int it = tid; it < G::WS * G::NSI; it += nth) {
-            const int r = it / G::NSI, c0 = (it - r * G::NSI) * 4;
+            const int c0 = (it / G::WS) * 4, r = it - (c0 / 4) * G::WS;   // rows fastest
             float s[3][4];
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch)
@@ -181,7 +183,7 @@ __global__ void __launch_bounds__(256, 2)
         __syncthreads();
         // (4) window-tap gradient: dG[o] += sum_c gS_c(p) P_c(b(p + o)) over the tile's pixels
         for (int it = tid; it < TB * (TB / 4); it += nth) {
-            const int ty = it / (TB / 4), tx0 = (it - ty * (TB / 4)) * 4;
+            const int tx0 = (it / TB) * 4, ty = it - (tx0 / 4) * TB;     // rows fastest
             if (y0 + ty >= H) continue;
             float g[3][4];
 #pragma unroll
@@ -209,7 +211,7 @@ __global__ void __launch_bounds__(256, 2)
         // (5) gP (window adjoint, with the clamp folds on the image's edges) and gI on the
         //     gI region, 4 columns per item (zero outside)
         for (int it = tid; it < G::WG * G::NGI; it += nth) {
-            const int r = it / G::NGI, c0 = (it - r * G::NGI) * 4;
+            const int c0 = (it / G::WG) * 4, r = it - (c0 / 4) * G::WG;   // rows fastest
             float gp[3][4];
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch)
