@@ -171,3 +171,18 @@ def test_tuner_reports_and_caches(tmp_path):
     ops.tune_clear()
     ops.tune_load(path)
     assert ops.default_variant(prob) == res["variant"]
+
+
+@pytest.mark.parametrize("k,border,bv", [(5, "clamp", 0.0), (11, "constant", 0.25)])
+def test_row_bands_on_one_gpu_match_whole_image(k, border, bv):
+    """The row-band partition of one image (what each rank of a multi-GPU run computes
+    after its halo exchange), run band by band on one GPU: the band's own rows of the
+    result on its extended band equal the whole image's rows bit for bit."""
+    from paper_1605_06399_gb300 import shard
+    g = np.random.default_rng(6100 + k)
+    x = torch.from_numpy(g.random((517, 301), dtype=np.float32)).cuda()
+    taps = g.standard_normal((k, k)).astype(np.float32)
+    whole = ops.conv2d(x, taps, border, bv)
+    for (y0, y1, e0, e1) in shard.row_bands(517, 4, (k - 1) // 2):
+        band = ops.conv2d(x[e0:e1].contiguous(), taps, border, bv)
+        assert torch.equal(band[y0 - e0:y1 - e0], whole[y0:y1]), (y0, y1)
