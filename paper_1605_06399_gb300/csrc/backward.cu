@@ -111,10 +111,11 @@ static imcl_status fold_1d(float* dst, int64_t dst_pitch, const float* g, int64_
     return cuda_fail(cudaGetLastError(), "fold 1d");
 }
 
-// CTAs of a tap-gradient launch: two per SM (the kernel's residency), at most one per
-// tile and at most kWgMaxParts; fixed for a device and an image size.
-static int wgrad_launch_grid(int W, int H, const DeviceInfo* dev) {
-    const int resident = 2 * (dev ? dev->sm_count : 1);
+// CTAs of a tap-gradient launch: the kernel's residency per SM (three for tap rows of up
+// to 5, else two), at most the partial sets the workspace holds (one per full-height
+// tile, at most kWgMaxParts); fixed for a device, an image size and a tap-row length.
+static int wgrad_launch_grid(int W, int H, const DeviceInfo* dev, int kw) {
+    const int resident = (kw <= 5 ? 3 : 2) * (dev ? dev->sm_count : 1);   // WgLaunch<KW>::MIN_CTAS
     return std::max(1, std::min(wgrad_grid(W, H), resident));
 }
 
@@ -191,7 +192,7 @@ imcl_status conv2d_backward_run(const BwdArgs& b, cudaStream_t s) {
     float* ws = static_cast<float*>(b.workspace);
     float* tap_slot = ws;
     float* partials = ws + kTapScratch;
-    const int wgrid = wgrad_launch_grid(W, H, f.dev);
+    const int wgrid = wgrad_launch_grid(W, H, f.dev, f.kw);
     if (b.dx) {
         TapSet t;
         IMCL_TRY(make_taps(static_cast<const float*>(f.taps), n, f.taps_mem, tap_slot, s, &t));
@@ -223,7 +224,7 @@ imcl_status sepconv_backward_run(const BwdArgs& b, cudaStream_t s) {
     float* DT = ws + pf;
     float* tap_slot = ws + 2 * pf;
     float* partials = tap_slot + kTapScratch;
-    const int wgrid = wgrad_launch_grid(W, H, f.dev);
+    const int wgrid_r = wgrad_launch_grid(W, H, f.dev, nr), wgrid_c = wgrad_launch_grid(W, H, f.dev, 1);
     const float* one = nullptr;
     IMCL_TRY(unit_tap(f.taps_mem, tap_slot + 4 * kMaxAdjTaps, s, &one));
     TapSet tr, tc;
@@ -257,8 +258,8 @@ imcl_status sepconv_backward_run(const BwdArgs& b, cudaStream_t s) {
     }
     if (b.dw0) {  // drow[i] = sum dt(p) x_b(p + i - rr)
         IMCL_TRY(wgrad_any(DT, pp_b / 4, f.in, f.in_dtype, f.in_pitch_b, W, H, nr, 1, f.border,
-                           (float)f.border_value, partials, wgrid, s));
-        IMCL_TRY(finalize(partials, wgrid, nr, b.dw0, s));
+                           (float)f.border_value, partials, wgrid_r, s));
+        IMCL_TRY(finalize(partials, wgrid_r, nr, b.dw0, s));
     }
     if (b.dw1) {  // dcol[j] = sum g(p) t_b(p + j - rc), t the forward row pass
         ConvCall t = f;
@@ -271,8 +272,8 @@ imcl_status sepconv_backward_run(const BwdArgs& b, cudaStream_t s) {
         t.ws_bytes = 0;
         IMCL_TRY(sep_run_fused(t, s));
         IMCL_TRY(wgrad_any(b.g, b.g_pitch_b / 4, T, IMCL_F32, pp_b, W, H, 1, nc, f.border, (float)f.border_value,
-                           partials, wgrid, s));
-        IMCL_TRY(finalize(partials, wgrid, nc, b.dw1, s));
+                           partials, wgrid_c, s));
+        IMCL_TRY(finalize(partials, wgrid_c, nc, b.dw1, s));
     }
     return IMCL_OK;
 }
@@ -320,7 +321,7 @@ imcl_status harris_backward_run(const BwdArgs& b, cudaStream_t s) {
     const float* sx = static_cast<const float*>(f.taps);
     const float* sy = static_cast<const float*>(f.taps2);
     const float* gw = static_cast<const float*>(f.taps3);
-    const int grid = wgrad_launch_grid(W, H, f.dev);
+    const int grid = wgrad_launch_grid(W, H, f.dev, wk), grid_s = wgrad_launch_grid(W, H, f.dev, 3);
     dim3 eg((W + 255) / 256, H);
     // an even window runs as the next odd one with a zero last row and column; its
     // gradient is the top-left src x src block of that window's gradient
@@ -430,13 +431,13 @@ imcl_status harris_backward_run(const BwdArgs& b, cudaStream_t s) {
     }
     if (b.dw0) {
         IMCL_TRY(wgrad_partials(S[0], pp, f.in, IMCL_F32, f.in_pitch_b / 4, W, H, 3, 3, IMCL_BORDER_CLAMP, 0.f,
-                                partials, grid, s));
-        IMCL_TRY(finalize(partials, grid, 9, b.dw0, s));
+                                partials, grid_s, s));
+        IMCL_TRY(finalize(partials, grid_s, 9, b.dw0, s));
     }
     if (b.dw1) {
         IMCL_TRY(wgrad_partials(S[1], pp, f.in, IMCL_F32, f.in_pitch_b / 4, W, H, 3, 3, IMCL_BORDER_CLAMP, 0.f,
-                                partials, grid, s));
-        IMCL_TRY(finalize(partials, grid, 9, b.dw1, s));
+                                partials, grid_s, s));
+        IMCL_TRY(finalize(partials, grid_s, 9, b.dw1, s));
     }
     return IMCL_OK;
 }

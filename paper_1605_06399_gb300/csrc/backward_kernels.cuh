@@ -21,7 +21,15 @@
 
 namespace imcl {
 
-constexpr int kWgTileW = 128, kWgTileH = 64;  // tile of the tap-gradient reduction
+constexpr int kWgTileW = 128, kWgTileH = 64;  // tile of the tap-gradient reduction (largest)
+
+// Short tap rows are memory-bound: half-height tiles and three resident CTAs per SM keep
+// more loads in flight.
+template <int KW>
+struct WgLaunch {
+    static constexpr int TH = KW <= 5 ? kWgTileH / 2 : kWgTileH;
+    static constexpr int MIN_CTAS = KW <= 5 ? 3 : 2;
+};
 constexpr int kWgMaxParts = 1024;             // CTAs (partial sums per tap) at most
 constexpr int kMaxAdjTaps = 33 * 33;
 
@@ -114,8 +122,9 @@ __global__ void __launch_bounds__(256)
 // deterministic.
 template <int KW>
 constexpr int wgrad_smem_bytes(int kh, int nth) {
-    return 4 * ((kWgTileW * kWgTileH + wg_xpitch<KW>(kWgTileW) * (kWgTileH + kh - 1)) > nth * WgCfg<KW>::JR * KW
-                    ? (kWgTileW * kWgTileH + wg_xpitch<KW>(kWgTileW) * (kWgTileH + kh - 1))
+    return 4 * ((kWgTileW * WgLaunch<KW>::TH + wg_xpitch<KW>(kWgTileW) * (WgLaunch<KW>::TH + kh - 1)) >
+                        nth * WgCfg<KW>::JR * KW
+                    ? (kWgTileW * WgLaunch<KW>::TH + wg_xpitch<KW>(kWgTileW) * (WgLaunch<KW>::TH + kh - 1))
                     : nth * WgCfg<KW>::JR * KW);
 }
 
@@ -127,16 +136,16 @@ __device__ __forceinline__ float load_px_f32(const void* x, int x_dt, long long 
 }
 
 template <int KW>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, WgLaunch<KW>::MIN_CTAS)
     k_wgrad_partial(const float* g, long long g_pitch, const void* x, int x_dt, long long x_pitch, int W, int H,
                     int kh, int border, float bvf, int vec, float* partials) {
     extern __shared__ __align__(16) float wsm[];
-    constexpr int JR = WgCfg<KW>::JR, XW = wg_xpitch<KW>(kWgTileW);
+    constexpr int JR = WgCfg<KW>::JR, XW = wg_xpitch<KW>(kWgTileW), TH_ = WgLaunch<KW>::TH;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int rx = (KW - 1) / 2, ry = (kh - 1) / 2;
-    const int XH = kWgTileH + kh - 1;
-    float* gs = wsm;                                  // kWgTileH x kWgTileW
-    float* xs = gs + kWgTileW * kWgTileH;             // XH x XW
+    const int XH = TH_ + kh - 1;
+    float* gs = wsm;                                  // TH_ x kWgTileW
+    float* xs = gs + kWgTileW * TH_;             // XH x XW
     const int G = (kh + JR - 1) / JR;                 // tap-row groups
     const int T = nth / G;                            // threads per group
     const int grp = tid / T, lt = tid - grp * T;
@@ -147,20 +156,20 @@ __global__ void __launch_bounds__(256, 2)
     for (int jr = 0; jr < JR; ++jr)
 #pragma unroll
         for (int i = 0; i < KW; ++i) acc[jr][i] = 0.f;
-    const int tiles_x = (W + kWgTileW - 1) / kWgTileW, tiles_y = (H + kWgTileH - 1) / kWgTileH;
+    const int tiles_x = (W + kWgTileW - 1) / kWgTileW, tiles_y = (H + TH_ - 1) / TH_;
     for (int t = blockIdx.x; t < tiles_x * tiles_y; t += gridDim.x) {
-        const int x0 = (t % tiles_x) * kWgTileW, y0 = (t / tiles_x) * kWgTileH;
+        const int x0 = (t % tiles_x) * kWgTileW, y0 = (t / tiles_x) * TH_;
         __syncthreads();
-        if (vec && x0 + kWgTileW <= W && y0 + kWgTileH <= H) {
+        if (vec && x0 + kWgTileW <= W && y0 + TH_ <= H) {
             // whole g tile inside: 16-byte loads, several in flight per thread
             // all of a thread's loads first, then its stores: 4 in flight per thread
             constexpr int NC = kWgTileW / 4, NB4 = 4;
-            for (int k0 = 0; k0 < NC * kWgTileH; k0 += NB4 * nth) {
+            for (int k0 = 0; k0 < NC * TH_; k0 += NB4 * nth) {
                 float4 q[NB4];
 #pragma unroll
                 for (int u = 0; u < NB4; ++u) {
                     const int k = k0 + u * nth + tid;
-                    if (k < NC * kWgTileH) {
+                    if (k < NC * TH_) {
                         const int r = k / NC, c = (k - r * NC) * 4;
                         q[u] = __ldg(reinterpret_cast<const float4*>(g + (long long)(y0 + r) * g_pitch + x0 + c));
                     }
@@ -168,14 +177,14 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
                 for (int u = 0; u < NB4; ++u) {
                     const int k = k0 + u * nth + tid;
-                    if (k < NC * kWgTileH) {
+                    if (k < NC * TH_) {
                         const int r = k / NC, c = (k - r * NC) * 4;
                         *reinterpret_cast<float4*>(gs + r * kWgTileW + c) = q[u];
                     }
                 }
             }
         } else {
-            for (int k = tid; k < kWgTileW * kWgTileH; k += nth) {
+            for (int k = tid; k < kWgTileW * TH_; k += nth) {
                 const int r = k / kWgTileW, c = k - r * kWgTileW;
                 gs[k] = (x0 + c < W && y0 + r < H) ? g[(long long)(y0 + r) * g_pitch + x0 + c] : 0.f;
             }
@@ -236,7 +245,7 @@ __global__ void __launch_bounds__(256, 2)
             }
         }
         __syncthreads();
-        if (active) wgrad_accumulate<KW>(gs, kWgTileW, xs, XW, kWgTileW, kWgTileH, kh, j0, lt, T, acc);
+        if (active) wgrad_accumulate<KW>(gs, kWgTileW, xs, XW, kWgTileW, TH_, kh, j0, lt, T, acc);
     }
     // combine the threads of each tap-row group in a fixed order (the staging area is free)
     wgrad_combine<KW>(acc, active, wsm, kh, T, partials + (long long)blockIdx.x * KW * kh, tid, nth);

@@ -22,7 +22,9 @@ constexpr int kWgLx = 4, kWgLy = 8;           // pixels of a thread's block (x, 
 
 template <int KW>
 struct WgCfg {
-    static constexpr int JR = KW > 15 ? 1 : (48 / KW < 8 ? 48 / KW : 8);   // tap rows per thread
+    // tap rows per thread: JR x KW accumulators (at most 48; 20 for the short rows, whose
+    // kernels run three CTAs per SM)
+    static constexpr int JR = KW > 15 ? 1 : (KW <= 5 ? 4 : (48 / KW < 8 ? 48 / KW : 8));
     static constexpr int XQ = (kWgLx + KW - 1 + 3) / 4;                    // float4s per x row
 };
 
