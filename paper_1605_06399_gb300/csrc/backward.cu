@@ -133,6 +133,27 @@ static imcl_status wgrad_launch(const float* g, int64_t g_pitch, const void* x, 
     return cuda_fail(cudaGetLastError(), "tap gradient partials");
 }
 
+// The TMA-staged form (f32 operands with 16-byte aligned rows, tap rows of up to 5).
+template <int KW>
+static imcl_status wgrad_launch_tma(const float* g, int64_t g_pitch, const float* x, int64_t x_pitch, int W, int H,
+                                    int kh, int border, float bv, float* partials, int grid, cudaStream_t s) {
+    DeviceInfo* dev = nullptr;
+    imcl_status st = device_info(&dev);
+    if (st != IMCL_OK) return st;
+    const int TH = WgLaunch<KW>::TH;
+    CUtensorMap gmap, xmap;
+    memset(&gmap, 0, sizeof gmap);
+    memset(&xmap, 0, sizeof xmap);
+    if ((st = encode_tmap_2d(&gmap, IMCL_F32, g, W, H, g_pitch * 4, kWgTileW, TH)) != IMCL_OK) return st;
+    if ((st = encode_tmap_2d(&xmap, IMCL_F32, x, W, H, x_pitch * 4, WgTma<KW>::XW, TH + kh - 1)) != IMCL_OK)
+        return st;
+    const int smem = 128 + 2 * wgrad_tma_stage_bytes<KW>(kh);
+    auto kfn = k_wgrad_tma<KW>;
+    if ((st = set_smem_limit((const void*)kfn, smem)) != IMCL_OK) return st;
+    kfn<<<grid, 256, smem, s>>>(gmap, xmap, W, H, kh, border, bv, partials, dev->status);
+    return cuda_fail(cudaGetLastError(), "tap gradient partials (TMA)");
+}
+
 // Per-CTA partial sums of a kw x kh tap gradient; x of type x_dt with pitch in elements.
 // `grid` CTAs write partials[0 .. grid * kw * kh).
 static imcl_status wgrad_partials(const float* g, int64_t g_pitch, const void* x, int x_dt, int64_t x_pitch, int W,
@@ -140,6 +161,17 @@ static imcl_status wgrad_partials(const float* g, int64_t g_pitch, const void* x
                                   cudaStream_t s) {
     if (kw % 2 == 0 || kw > 33 || kh < 1 || kh > 33)
         return fail(IMCL_ERR_UNSUPPORTED, "tap gradient: odd kw and kh up to 33");
+    const bool aligned16 = ((reinterpret_cast<uintptr_t>(g) | reinterpret_cast<uintptr_t>(x) |
+                             (uintptr_t)(g_pitch * 4) | (uintptr_t)(x_pitch * 4)) & 15) == 0;
+    if (x_dt == IMCL_F32 && aligned16 && kh + WgLaunch<1>::TH - 1 <= 256) {
+        const float* xf = static_cast<const float*>(x);
+        switch (kw) {
+            case 1: return wgrad_launch_tma<1>(g, g_pitch, xf, x_pitch, W, H, kh, border, bv, partials, grid, s);
+            case 3: return wgrad_launch_tma<3>(g, g_pitch, xf, x_pitch, W, H, kh, border, bv, partials, grid, s);
+            case 5: return wgrad_launch_tma<5>(g, g_pitch, xf, x_pitch, W, H, kh, border, bv, partials, grid, s);
+            default: break;
+        }
+    }
     // the constant as the pixel type reads it back
     float bvf = bv;
     if (x_dt == IMCL_F16) bvf = __half2float(__float2half_rn(bv));

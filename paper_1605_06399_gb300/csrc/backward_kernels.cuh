@@ -251,6 +251,97 @@ __global__ void __launch_bounds__(256, WgLaunch<KW>::MIN_CTAS)
     wgrad_combine<KW>(acc, active, wsm, kh, T, partials + (long long)blockIdx.x * KW * kh, tid, nth);
 }
 
+// The same reduction with both operands staged by TMA (f32 x and g, 16-byte aligned
+// rows) into a double-buffered ring: persistent CTAs prefetch their next tile while they
+// reduce the current one.  The x region starts at column x0 - PADX, PADX = rx rounded up
+// to 4 (TMA x coordinates must be 16-byte aligned), so reads start D = PADX - rx columns
+// in.  TMA zero-fills outside the image, which is g's rule; x tiles at the image's edge
+// are patched to the boundary rule in shared memory.  Waits are bounded (a timeout
+// records IMCL_DEVERR_TIMEOUT and the CTA leaves).
+template <int KW>
+struct WgTma {
+    static constexpr int RX = (KW - 1) / 2;
+    static constexpr int PADX = (RX + 3) / 4 * 4;
+    static constexpr int D = PADX - RX;
+    static constexpr int XQ = WgCfg<KW>::XQ + (D > 0 ? 1 : 0);
+    static constexpr int XW = kWgTileW - kWgLx + 4 * XQ;                    // x region width (box)
+};
+
+template <int KW>
+__host__ __device__ constexpr int wgrad_tma_stage_bytes(int kh) {
+    return round_up(kWgTileW * WgLaunch<KW>::TH * 4, 128) + round_up(WgTma<KW>::XW * (WgLaunch<KW>::TH + kh - 1) * 4, 128);
+}
+
+template <int KW>
+__global__ void __launch_bounds__(256, WgLaunch<KW>::MIN_CTAS)
+    k_wgrad_tma(const __grid_constant__ CUtensorMap gmap, const __grid_constant__ CUtensorMap xmap, int W, int H,
+                int kh, int border, float bvf, float* partials, int* status) {
+    extern __shared__ __align__(128) uint8_t wsm8[];
+    using TM = WgTma<KW>;
+    constexpr int JR = WgCfg<KW>::JR, TH = WgLaunch<KW>::TH, TW = kWgTileW, XW = TM::XW;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int ry = (kh - 1) / 2, XH = TH + kh - 1;
+    const int g_bytes = TW * TH * 4, x_bytes = XW * XH * 4;
+    const int stage = wgrad_tma_stage_bytes<KW>(kh);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(wsm8);
+    auto gbuf = [&](int s) { return reinterpret_cast<float*>(wsm8 + 128 + s * stage); };
+    auto xbuf = [&](int s) { return reinterpret_cast<float*>(wsm8 + 128 + s * stage + round_up(g_bytes, 128)); };
+    const int G = (kh + JR - 1) / JR, T = nth / G;
+    const int grp = tid / T, lt = tid - grp * T;
+    const bool active = grp < G;
+    const int j0 = grp * JR;
+    float acc[JR][KW];
+#pragma unroll
+    for (int jr = 0; jr < JR; ++jr)
+#pragma unroll
+        for (int i = 0; i < KW; ++i) acc[jr][i] = 0.f;
+    const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH, ntiles = tiles_x * tiles_y;
+    auto issue = [&](int t, int s) {
+        const int x0 = (t % tiles_x) * TW, y0 = (t / tiles_x) * TH;
+        mbar_arrive_expect_tx(&bar[s], (uint32_t)(g_bytes + x_bytes));
+        tma_load_2d(gbuf(s), &gmap, x0, y0, &bar[s]);
+        tma_load_2d(xbuf(s), &xmap, x0 - TM::PADX, y0 - ry, &bar[s]);
+    };
+    int t = blockIdx.x, s = 0;
+    uint32_t parity = 0;
+    if (tid == 0) {
+        prefetch_tmap(&gmap);
+        prefetch_tmap(&xmap);
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0 && t < ntiles) issue(t, 0);
+    bool failed = false;
+    for (; t < ntiles; t += gridDim.x) {
+        const int x0 = (t % tiles_x) * TW, y0 = (t / tiles_x) * TH;
+        const int tn = t + gridDim.x;
+        const bool prefetch = tn < ntiles;
+        if (tid == 0 && prefetch) {
+            fence_proxy_async_smem();     // stage s^1 was released by the barrier ending the last tile
+            issue(tn, s ^ 1);
+        }
+        const bool ok = mbar_wait(&bar[s], (parity >> s) & 1u, status);
+        parity ^= (1u << s);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0 && prefetch) mbar_wait(&bar[s ^ 1], (parity >> (s ^ 1)) & 1u, nullptr);
+            failed = true;
+            break;
+        }
+        float* xs = xbuf(s);
+        const int gx0 = x0 - TM::PADX, gy0 = y0 - ry;
+        if (!tile_inside(gx0, gy0, XW, XH, W, H)) patch_tile<float>(xs, XW, XH, gx0, gy0, W, H, border, bvf, tid, nth);
+        if (active) wgrad_accumulate<KW, TM::D>(gbuf(s), TW, xs, XW, TW, TH, kh, j0, lt, T, acc);
+        __syncthreads();              // stage s may be refilled
+        s ^= 1;
+    }
+    if (failed) return;
+    // combine the threads of each tap-row group in a fixed order (the ring is idle now)
+    wgrad_combine<KW>(acc, active, reinterpret_cast<float*>(wsm8 + 128), kh, T,
+                      partials + (long long)blockIdx.x * KW * kh, tid, nth);
+}
+
 // out[tap] = (accumulate ? out[tap] : 0) + sum over nparts partial sums, as a fixed tree.
 __global__ void __launch_bounds__(256)
     k_wgrad_finalize(const float* partials, int nparts, int ntaps, float* out, int accumulate) {

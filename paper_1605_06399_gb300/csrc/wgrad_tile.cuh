@@ -33,12 +33,16 @@ template <int KW>
 __host__ __device__ constexpr int wg_xpitch(int tw) { return tw - kWgLx + 4 * WgCfg<KW>::XQ; }
 
 // Accumulate the blocks lt, lt + T, ... of a tw x th tile (tw % 4 == 0, th % 8 == 0, gs,
-// xs, gsw and xsw 16-byte aligned) into acc, for tap rows j0 .. j0 + JR - 1 (< kh).
-template <int KW>
+// xs, gsw and xsw 16-byte aligned) into acc, for tap rows j0 .. j0 + JR - 1 (< kh).  D:
+// the x region starts D columns further left than the tile's offset -rx (an aligned
+// staging origin); a row's reads then start D columns in, loaded from the aligned column
+// before them.
+template <int KW, int D = 0>
 __device__ __forceinline__ void wgrad_accumulate(const float* gs, int gsw, const float* xs, int xsw, int tw, int th,
                                                  int kh, int j0, int lt, int T,
                                                  float (&acc)[WgCfg<KW>::JR][KW]) {
-    constexpr int JR = WgCfg<KW>::JR, XQ = WgCfg<KW>::XQ, LX = kWgLx, LY = kWgLy;
+    constexpr int JR = WgCfg<KW>::JR, XQ = WgCfg<KW>::XQ + (D > 0 ? 1 : 0), LX = kWgLx, LY = kWgLy;
+    static_assert(D >= 0 && D < 4, "staging offset within one float4");
     const int BX = tw / LX, NB = BX * (th / LY);
     for (int b = lt; b < NB; b += T) {
         const int by = b / BX, bxx = b - by * BX;
@@ -68,7 +72,7 @@ __device__ __forceinline__ void wgrad_accumulate(const float* gs, int gsw, const
 #pragma unroll
                         for (int i = 0; i < KW; ++i)
 #pragma unroll
-                            for (int p = 0; p < LX; ++p) acc[jr][i] = __fmaf_rn(gv[yy][p], xv[p + i], acc[jr][i]);
+                            for (int p = 0; p < LX; ++p) acc[jr][i] = __fmaf_rn(gv[yy][p], xv[D + p + i], acc[jr][i]);
                     }
                 }
             }
