@@ -140,7 +140,7 @@ static imcl_status wgrad_launch_tma(const float* g, int64_t g_pitch, const float
     DeviceInfo* dev = nullptr;
     imcl_status st = device_info(&dev);
     if (st != IMCL_OK) return st;
-    const int TH = WgLaunch<KW>::TH;
+    const int TH = WgTma<KW>::TH;
     CUtensorMap gmap, xmap;
     memset(&gmap, 0, sizeof gmap);
     memset(&xmap, 0, sizeof xmap);
@@ -163,14 +163,15 @@ static imcl_status wgrad_partials(const float* g, int64_t g_pitch, const void* x
         return fail(IMCL_ERR_UNSUPPORTED, "tap gradient: odd kw and kh up to 33");
     const bool aligned16 = ((reinterpret_cast<uintptr_t>(g) | reinterpret_cast<uintptr_t>(x) |
                              (uintptr_t)(g_pitch * 4) | (uintptr_t)(x_pitch * 4)) & 15) == 0;
-    if (x_dt == IMCL_F32 && aligned16 && kh + WgLaunch<1>::TH - 1 <= 256) {
+    if (x_dt == IMCL_F32 && aligned16) {
         const float* xf = static_cast<const float*>(x);
+#define IMCL_WGT(K) \
+    case K: return wgrad_launch_tma<K>(g, g_pitch, xf, x_pitch, W, H, kh, border, bv, partials, grid, s);
         switch (kw) {
-            case 1: return wgrad_launch_tma<1>(g, g_pitch, xf, x_pitch, W, H, kh, border, bv, partials, grid, s);
-            case 3: return wgrad_launch_tma<3>(g, g_pitch, xf, x_pitch, W, H, kh, border, bv, partials, grid, s);
-            case 5: return wgrad_launch_tma<5>(g, g_pitch, xf, x_pitch, W, H, kh, border, bv, partials, grid, s);
+            IMCL_WGT(1) IMCL_WGT(3) IMCL_WGT(5) IMCL_WGT(7) IMCL_WGT(9) IMCL_WGT(11) IMCL_WGT(13) IMCL_WGT(15)
             default: break;
         }
+#undef IMCL_WGT
     }
     // the constant as the pixel type reads it back
     float bvf = bv;

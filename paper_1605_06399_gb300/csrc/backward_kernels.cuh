@@ -260,6 +260,8 @@ __global__ void __launch_bounds__(256, WgLaunch<KW>::MIN_CTAS)
 // records IMCL_DEVERR_TIMEOUT and the CTA leaves).
 template <int KW>
 struct WgTma {
+    static constexpr int TH = 32;                                          // tile rows
+    static constexpr int MIN_CTAS = KW <= 5 ? 3 : 2;
     static constexpr int RX = (KW - 1) / 2;
     static constexpr int PADX = (RX + 3) / 4 * 4;
     static constexpr int D = PADX - RX;
@@ -269,16 +271,16 @@ struct WgTma {
 
 template <int KW>
 __host__ __device__ constexpr int wgrad_tma_stage_bytes(int kh) {
-    return round_up(kWgTileW * WgLaunch<KW>::TH * 4, 128) + round_up(WgTma<KW>::XW * (WgLaunch<KW>::TH + kh - 1) * 4, 128);
+    return round_up(kWgTileW * WgTma<KW>::TH * 4, 128) + round_up(WgTma<KW>::XW * (WgTma<KW>::TH + kh - 1) * 4, 128);
 }
 
 template <int KW>
-__global__ void __launch_bounds__(256, WgLaunch<KW>::MIN_CTAS)
+__global__ void __launch_bounds__(256, WgTma<KW>::MIN_CTAS)
     k_wgrad_tma(const __grid_constant__ CUtensorMap gmap, const __grid_constant__ CUtensorMap xmap, int W, int H,
                 int kh, int border, float bvf, float* partials, int* status) {
     extern __shared__ __align__(128) uint8_t wsm8[];
     using TM = WgTma<KW>;
-    constexpr int JR = WgCfg<KW>::JR, TH = WgLaunch<KW>::TH, TW = kWgTileW, XW = TM::XW;
+    constexpr int JR = WgCfg<KW>::JR, TH = TM::TH, TW = kWgTileW, XW = TM::XW;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int ry = (kh - 1) / 2, XH = TH + kh - 1;
     const int g_bytes = TW * TH * 4, x_bytes = XW * XH * 4;
