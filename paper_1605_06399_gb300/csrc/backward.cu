@@ -94,7 +94,7 @@ static imcl_status edges_2d(float* dx, int64_t dx_pitch, const float* g1, int64_
         w2d = w2;
     }
     const int nedge = (H > 1 ? 2 * W : W) + (W > 1 ? 2 : 1) * std::max(H - 2, 0);
-    k_adjoint_edges_2d<<<(nedge + 255) / 256, 256, 0, s>>>(dx, dx_pitch, g1, g1_pitch, g2, g2_pitch, W, H, kw, kh,
+    k_adjoint_edges_2d<<<(nedge + 7) / 8, 256, 0, s>>>(dx, dx_pitch, g1, g1_pitch, g2, g2_pitch, W, H, kw, kh,
                                                             w1d, w2d, tp);
     return cuda_fail(cudaGetLastError(), "adjoint edges");
 }

@@ -43,15 +43,17 @@ __device__ __forceinline__ float g0_at(const float* g, long long pitch, int x, i
 }
 
 // Recompute dx at every pixel of the first/last row and column: the folded adjoint of
-// one or two clamped correlations (kw x kh taps each, kw, kh <= 15).  Overwrites.
+// one or two clamped correlations (kw x kh taps each, kw, kh <= 15).  Overwrites.  One
+// warp per edge pixel: the lanes split the taps, then add their sums in a fixed tree.
 __global__ void __launch_bounds__(256)
     k_adjoint_edges_2d(float* dx, long long dx_pitch, const float* g1, long long g1_pitch, const float* g2,
                        long long g2_pitch, int W, int H, int kw, int kh, const float* w1_dev, const float* w2_dev,
                        const __grid_constant__ AdjTaps tp) {
     const int ntop = W, nside = H > 2 ? H - 2 : 0;
     const int nedge = (H > 1 ? 2 * ntop : ntop) + (W > 1 ? 2 * nside : nside);
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nedge) return;
+    const int lane = threadIdx.x & 31;
+    const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (e >= nedge) return;                       // whole warps leave together
     int qx, qy;
     const int rows = H > 1 ? 2 * ntop : ntop;
     if (e < rows) {
@@ -70,13 +72,15 @@ __global__ void __launch_bounds__(256)
     float acc = 0.f;
     for (int ey = ylo; ey <= yhi; ++ey)
         for (int ex = xlo; ex <= xhi; ++ex)
-            for (int j = 0; j < kh; ++j)
-                for (int i = 0; i < kw; ++i) {
-                    const int sx = ex - i + rx, sy = ey - j + ry;
-                    acc = __fmaf_rn(w1[j * kw + i], g0_at(g1, g1_pitch, sx, sy, W, H), acc);
-                    if (g2) acc = __fmaf_rn(w2[j * kw + i], g0_at(g2, g2_pitch, sx, sy, W, H), acc);
-                }
-    dx[(long long)qy * dx_pitch + qx] = acc;
+            for (int t = lane; t < kw * kh; t += 32) {
+                const int j = t / kw, i = t - j * kw;
+                const int sx = ex - i + rx, sy = ey - j + ry;
+                acc = __fmaf_rn(w1[t], g0_at(g1, g1_pitch, sx, sy, W, H), acc);
+                if (g2) acc = __fmaf_rn(w2[t], g0_at(g2, g2_pitch, sx, sy, W, H), acc);
+            }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) dx[(long long)qy * dx_pitch + qx] = acc;
 }
 
 // Add the folded contributions of a clamped 1D correlation along one axis (axis 0: x,
