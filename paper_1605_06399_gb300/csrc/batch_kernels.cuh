@@ -141,7 +141,7 @@ __device__ void stage_region(float* st, int sw, int sh, const void* img, int dt,
                              int W, int H, int border, float bv, int zero_outside, int tid, int nth, int vec = 0) {
     if ((gx0 & 7) == 0 && (sw & 7) == 0) {
         const int nch = sw >> 3;
-#pragma unroll 2
+#pragma unroll 4
         for (int idx = tid; idx < nch * sh; idx += nth) {
             const int r = idx / nch, c = (idx - r * nch) << 3;
             const int gx = gx0 + c, gy = gy0 + r;
