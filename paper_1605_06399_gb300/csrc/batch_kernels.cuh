@@ -534,8 +534,16 @@ __device__ void batch_sep_dt_tile(const BImg& im, int x0, int y0, int TW, int TH
         }
         __syncthreads();
         const int tile = (y0 / TH) * im.tiles_x + x0 / TW;
-        // g rows of the tile start at row R of gs; t rows at offset R - rc relative to them
-        tile_wgrad(gs, TW, R, ts, TW, R - rc, TW, TH, 1, nc, red, im.part + (size_t)tile * nc, tid, nth);
+        // column taps: the register-blocked reduction with one tap per row (KW = 1, nc tap
+        // rows); g rows of the tile start at row R of gs, t rows at offset R - rc
+        constexpr int JR = WgCfg<1>::JR;
+        const int G = (nc + JR - 1) / JR, T = nth / G, grp = tid / T, lt = tid - grp * T;
+        const bool active = grp < G;
+        float acc[JR][1];
+#pragma unroll
+        for (int jr = 0; jr < JR; ++jr) acc[jr][0] = 0.f;
+        if (active) wgrad_accumulate<1>(gs + R * TW, TW, ts + (R - rc) * TW, TW, TW, TH, nc, grp * JR, lt, T, acc);
+        wgrad_combine<1>(acc, active, red, nc, T, im.part + (size_t)tile * nc, tid, nth);
     }
 }
 
