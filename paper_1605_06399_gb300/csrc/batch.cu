@@ -99,7 +99,7 @@ size_t batch_bwd_smem_bytes(int py, int bx, int by) {
                                     (size_t)256 * WgCfg<kBatchMaxK>::JR * K + K * K);
     const size_t HH = TH + 2 * R, XW = TW + 16;
     const size_t sep_dt = 2 * TW * HH + XW * HH + 32 + 1024;
-    const size_t sep_dx = 2 * XW * TH + 16 + 1024;
+    const size_t sep_dx = 2 * XW * TH + 16 + 256 * K + 4;   // + the row-tap combine scratch
     return std::max(std::max(conv_dx, conv_wg), std::max(sep_dt, sep_dx)) * sizeof(float);
 }
 
@@ -304,7 +304,7 @@ imcl_status batch_create(const imcl_batch_item* items, int n, double budget_s, B
     // taller (PY = 4) shapes at comparable forward times, so a plan with gradients
     // chooses among those.
     bool with_grads = false;
-    for (const BImg& im : b->himgs) with_grads = with_grads || im.g != nullptr;
+    for (const imcl_batch_item& it : b->items) with_grads = with_grads || it.grad_out.data != nullptr;
     for (int c = 0; c < kNumShapes; ++c) {
         if (with_grads && kShapes[c][0] != 4) continue;
         std::vector<float> ts;

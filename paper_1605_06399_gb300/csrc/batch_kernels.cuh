@@ -547,6 +547,20 @@ __device__ void batch_sep_dt_tile(const BImg& im, int x0, int y0, int TW, int TH
     }
 }
 
+// Row-tap partial sums of a separable tile: out[i] = sum_p dt(p) x(p + (i - rr, 0)), with
+// dt staged at columns PADR.. of ds and x at columns PADR - rr + i of xs (rows XW wide).
+// x reads start PADR - rr columns in: the aligned column below and D = (PADR - rr) % 4.
+template <int NR>
+__device__ void batch_row_wgrad(const float* ds, const float* xs, int XW, int TW, int TH, float* red, float* out,
+                                int tid, int nth) {
+    constexpr int PADR = 8, RR = (NR - 1) / 2, D = (PADR - RR) % 4;
+    float acc[1][NR];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) acc[0][i] = 0.f;
+    wgrad_accumulate<NR, D, 1>(ds + PADR, XW, xs + (PADR - RR - D), XW, TW, TH, 1, 0, tid, nth, acc);
+    wgrad_combine<NR, 1>(acc, true, red, 1, nth, out, tid, nth);
+}
+
 // separable, second backward pass: dx = R^T dt on the tile (with the clamp folds on the
 // first and last columns) and the row-tap partials drow[i] = sum_p dt(p) x(p + (i - rr, 0)).
 __device__ void batch_sep_dx_tile(const BImg& im, int x0, int y0, int TW, int TH, float* sm, int tid, int nth) {
@@ -591,8 +605,17 @@ __device__ void batch_sep_dx_tile(const BImg& im, int x0, int y0, int TW, int TH
         const int tile = (y0 / TH) * im.tiles_x + x0 / TW;
         const int ntiles = im.tiles_x * im.tiles_y;
         // dt rows of the tile are ds rows 0..TH at columns PADR..; x at columns PADR - rr + i
-        tile_wgrad(ds + PADR, XW, 0, xs + PADR - rr, XW, 0, TW, TH, nr, 1, red,
-                   im.part + (size_t)ntiles * im.kh + (size_t)tile * nr, tid, nth);
+        float* out = im.part + (size_t)ntiles * im.kh + (size_t)tile * nr;
+        switch (nr) {   // row taps: the register-blocked reduction, one tap row
+            case 1: batch_row_wgrad<1>(ds, xs, XW, TW, TH, red, out, tid, nth); break;
+            case 3: batch_row_wgrad<3>(ds, xs, XW, TW, TH, red, out, tid, nth); break;
+            case 5: batch_row_wgrad<5>(ds, xs, XW, TW, TH, red, out, tid, nth); break;
+            case 7: batch_row_wgrad<7>(ds, xs, XW, TW, TH, red, out, tid, nth); break;
+            case 9: batch_row_wgrad<9>(ds, xs, XW, TW, TH, red, out, tid, nth); break;
+            case 11: batch_row_wgrad<11>(ds, xs, XW, TW, TH, red, out, tid, nth); break;
+            case 13: batch_row_wgrad<13>(ds, xs, XW, TW, TH, red, out, tid, nth); break;
+            default: batch_row_wgrad<15>(ds, xs, XW, TW, TH, red, out, tid, nth); break;
+        }
     }
 }
 

@@ -37,11 +37,10 @@ __host__ __device__ constexpr int wg_xpitch(int tw) { return tw - kWgLx + 4 * Wg
 // the x region starts D columns further left than the tile's offset -rx (an aligned
 // staging origin); a row's reads then start D columns in, loaded from the aligned column
 // before them.
-template <int KW, int D = 0>
+template <int KW, int D = 0, int JR = WgCfg<KW>::JR>
 __device__ __forceinline__ void wgrad_accumulate(const float* gs, int gsw, const float* xs, int xsw, int tw, int th,
-                                                 int kh, int j0, int lt, int T,
-                                                 float (&acc)[WgCfg<KW>::JR][KW]) {
-    constexpr int JR = WgCfg<KW>::JR, XQ = WgCfg<KW>::XQ + (D > 0 ? 1 : 0), LX = kWgLx, LY = kWgLy;
+                                                 int kh, int j0, int lt, int T, float (&acc)[JR][KW]) {
+    constexpr int XQ = WgCfg<KW>::XQ + (D > 0 ? 1 : 0), LX = kWgLx, LY = kWgLy;
     static_assert(D >= 0 && D < 4, "staging offset within one float4");
     const int BX = tw / LX, NB = BX * (th / LY);
     for (int b = lt; b < NB; b += T) {
@@ -82,10 +81,9 @@ __device__ __forceinline__ void wgrad_accumulate(const float* gs, int gsw, const
 
 // out[j * KW + i] = sum over the T threads of tap-row group j / JR, in thread order.  red:
 // nth * JR * KW floats of shared memory that nothing else uses now.  Ends synchronised.
-template <int KW>
-__device__ void wgrad_combine(const float (&acc)[WgCfg<KW>::JR][KW], bool active, float* red, int kh, int T,
-                              float* out, int tid, int nth) {
-    constexpr int JR = WgCfg<KW>::JR;
+template <int KW, int JR = WgCfg<KW>::JR>
+__device__ void wgrad_combine(const float (&acc)[JR][KW], bool active, float* red, int kh, int T, float* out, int tid,
+                              int nth) {
     __syncthreads();
 #pragma unroll
     for (int jr = 0; jr < JR; ++jr)
