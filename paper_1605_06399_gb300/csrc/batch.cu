@@ -29,12 +29,7 @@ int batch_side(int op, int kw, int kh) {
 }
 
 size_t batch_smem_bytes(int py, int bx, int by) {
-    const int TW = 4 * bx, TH = py * by;
-    const int pad = 16 / 4 * ((kBatchMaxK / 2 + 3) / 4);   // f32 PAD for the largest side
-    const int sw = TW + 2 * pad;
-    const size_t conv = (size_t)sw * (TH + kBatchMaxK - 1) + kBatchMaxK * kBatchMaxK;
-    const size_t sep = (size_t)sw * (TH + 2 * kBatchMaxR) + (size_t)(TH + 2 * kBatchMaxR) * TW + 2 * (2 * kBatchMaxR + 1);
-    return std::max(conv, sep) * sizeof(float);
+    return (size_t)fwd_layout(4 * bx, py * by).total;
 }
 
 static double tile_cost(const BImg& im, int w, int h) {
@@ -44,16 +39,33 @@ static double tile_cost(const BImg& im, int w, int h) {
 }
 
 // Forward work list for a tile shape, costliest tiles first (stable order for equal cost).
-static std::vector<BTile> fwd_tiles(const std::vector<BImg>& imgs, int TW, int TH) {
-    std::vector<std::pair<double, BTile>> v;
+static std::vector<BFwdTile> fwd_tiles(const std::vector<BImg>& imgs, int TW, int TH) {
+    std::vector<std::pair<double, BFwdTile>> v;
     for (int i = 0; i < (int)imgs.size(); ++i) {
         const BImg& im = imgs[i];
+        const int es = im.in_dt == IMCL_F32 ? 4 : 2;
         for (int y = 0; y < im.H; y += TH)
-            for (int x = 0; x < im.W; x += TW)
-                v.push_back({tile_cost(im, std::min(TW, im.W - x), std::min(TH, im.H - y)), BTile{i, BT_FWD, x, y}});
+            for (int x = 0; x < im.W; x += TW) {
+                BFwdTile t{};
+                t.in = im.in;
+                t.taps = im.taps;
+                t.taps2 = im.taps2;
+                t.pitch_b = im.in_pitch * es;
+                t.W = im.W;
+                t.H = im.H;
+                t.K = im.K;
+                t.es = es;
+                t.op = im.op;
+                t.kw = im.kw;
+                t.kh = im.kh;
+                t.img = i;
+                t.x0 = x;
+                t.y0 = y;
+                v.push_back({tile_cost(im, std::min(TW, im.W - x), std::min(TH, im.H - y)), t});
+            }
     }
     std::stable_sort(v.begin(), v.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
-    std::vector<BTile> t;
+    std::vector<BFwdTile> t;
     t.reserve(v.size());
     for (auto& p : v) t.push_back(p.second);
     return t;
@@ -76,15 +88,16 @@ static const void* fwd_kernel(int py) {
     return py == 4 ? (const void*)k_batch_fwd<4> : (const void*)k_batch_fwd<2>;
 }
 
-static imcl_status launch_fwd(const Batch& b, const BTile* tiles, int ntiles, int py, int bx, int by, cudaStream_t s) {
+static imcl_status launch_fwd(const Batch& b, const BFwdTile* tiles, int ntiles, int py, int bx, int by,
+                              cudaStream_t s) {
     const size_t smem = batch_smem_bytes(py, bx, by);
-    const int occ = cached_occupancy(fwd_kernel(py), 256, (int)smem);
+    const int occ = cached_occupancy(fwd_kernel(py), kFwdThreads, (int)smem);
     if (occ <= 0) return fail(IMCL_ERR_UNSUPPORTED, "batch: kernel cannot be resident");
     const int grid = std::max(1, std::min(ntiles, occ * b.dev->sm_count));
     cudaError_t e = cudaMemsetAsync(b.queue, 0, sizeof(int), s);
     if (e != cudaSuccess) return cuda_fail(e, "batch queue reset");
-    if (py == 4) k_batch_fwd<4><<<grid, 256, smem, s>>>(b.dimgs, tiles, ntiles, b.queue, bx, by);
-    else k_batch_fwd<2><<<grid, 256, smem, s>>>(b.dimgs, tiles, ntiles, b.queue, bx, by);
+    if (py == 4) k_batch_fwd<4><<<grid, kFwdThreads, smem, s>>>(b.dimgs, tiles, ntiles, b.queue, bx, by, b.dev->status);
+    else k_batch_fwd<2><<<grid, kFwdThreads, smem, s>>>(b.dimgs, tiles, ntiles, b.queue, bx, by, b.dev->status);
     return cuda_fail(cudaGetLastError(), "batch forward launch");
 }
 
@@ -285,7 +298,7 @@ imcl_status batch_create(const imcl_batch_item* items, int n, double budget_s, B
     b->owned.push_back(b->queue);
 
     // tile shape: time whole-batch launches of each candidate, keep the fastest
-    std::vector<BTile*> cand_tiles(kNumShapes, nullptr);
+    std::vector<BFwdTile*> cand_tiles(kNumShapes, nullptr);
     std::vector<int> cand_n(kNumShapes, 0);
     for (int c = 0; c < kNumShapes; ++c) {
         auto t = fwd_tiles(b->himgs, 4 * kShapes[c][1], kShapes[c][0] * kShapes[c][2]);

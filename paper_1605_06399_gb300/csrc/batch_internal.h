@@ -9,13 +9,14 @@ namespace imcl {
 
 struct BImg;
 struct BTile;
+struct BFwdTile;
 
 struct Batch {
     const DeviceInfo* dev = nullptr;
     std::vector<imcl_batch_item> items;
     std::vector<BImg> himgs;               // host copy of the image descriptors
     BImg* dimgs = nullptr;                 // device copy
-    BTile* tiles = nullptr;                // forward work list (device)
+    BFwdTile* tiles = nullptr;             // forward work list (device)
     int ntiles = 0;
     int* queue = nullptr;                  // work-list counters (device), one per phase
     int py = 4, bx = 32, by = 8;           // chosen tile shape (PX = 4)

@@ -20,8 +20,9 @@ namespace imcl {
 constexpr int kBatchMaxK = 15;    // conv2d side
 constexpr int kBatchMaxR = 7;     // separable radius
 
-// One image operation of the batch (device copy).  Pitches in elements.
-struct BImg {
+// One image operation of the batch (device copy).  Pitches in elements.  16-byte
+// aligned: the forward copies descriptors into shared memory with bulk copies.
+struct alignas(16) BImg {
     const void* in;
     void* out;
     long long in_pitch, out_pitch;
@@ -175,13 +176,64 @@ __device__ __forceinline__ void store_row_any(void* out, int dt, long long pitch
 }
 
 // ------------------------------------------------------------------ forward tiles
-// conv2d tile: sm holds the staged region (TW + 2 PAD) x (TH + K - 1), then K*K taps.
+// conv2d: accumulate one tile from a staged region (rows SW wide, origin (x0 - 8, y0 - R))
+// and K*K taps in shared memory, and store it.  flipped_zero: the backward's dx tiles
+// (edge pixels of a clamped image belong to the edge items).
+template <int K, int PY>
+__device__ __forceinline__ void conv_tile_compute(const BImg& im, int x0, int y0, int bx, int by, const float* st,
+                                                  int SW, const float* w, bool flipped_zero, void* dst,
+                                                  long long dst_pitch, int dst_dt, const int tid) {
+    constexpr int PX = 4;
+    using G = TileGeo<__half, K, PX>;    // halo padded to 8 columns: 16-byte aligned staging
+    if (tid >= bx * by) return;
+    const int tx = tid % bx, ty = tid / bx;
+    float acc[PY][PX];
+#pragma unroll
+    for (int oy = 0; oy < PY; ++oy)
+#pragma unroll
+        for (int ox = 0; ox < PX; ++ox) acc[oy][ox] = 0.f;
+    // filter row j outermost: its K taps stay in registers while the PY output rows
+    // that read input row (oy + j) accumulate (one shared-memory read per tap per tile).
+    // The j loop stays rolled: one batch kernel carries every filter side, and fully
+    // unrolled bodies for all of them would not fit the instruction cache together.
+#pragma unroll 1
+    for (int j = 0; j < K; ++j) {
+        float wr[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) wr[i] = w[j * K + i];
+#pragma unroll
+        for (int oy = 0; oy < PY; ++oy) {
+            float seg[G::SEG];
+            load_seg_smem<float, G>(st + (ty * PY + oy + j) * SW + tx * PX, seg);
+#pragma unroll
+            for (int i = 0; i < K; ++i)
+#pragma unroll
+                for (int ox = 0; ox < PX; ++ox) acc[oy][ox] = __fmaf_rn(wr[i], seg[G::LO + ox + i], acc[oy][ox]);
+        }
+    }
+    const bool skip_edges = flipped_zero && im.border == IMCL_BORDER_CLAMP;   // edge items own those
+#pragma unroll
+    for (int oy = 0; oy < PY; ++oy) {
+        const int gy = y0 + ty * PY + oy;
+        if (gy >= im.H) continue;
+#pragma unroll
+        for (int ox = 0; ox < PX; ++ox) {
+            const int gx = x0 + tx * PX + ox;
+            if (gx >= im.W) continue;
+            if (skip_edges && (gx == 0 || gy == 0 || gx == im.W - 1 || gy == im.H - 1)) continue;
+            store_px(dst, dst_dt, dst_pitch, gx, gy, acc[oy][ox]);
+        }
+    }
+}
+
+// conv2d tile with its own staging (the backward's input-gradient tiles): sm holds the
+// staged region (TW + 16) x (TH + K - 1), then K*K taps.
 template <int K, int PY>
 __device__ void batch_conv_tile(const BImg& im, int x0, int y0, int bx, int by, float* sm, bool flipped_zero,
                                 const float* g_src, long long g_pitch, void* dst, long long dst_pitch, int dst_dt,
                                 const int tid, const int nth) {
     constexpr int PX = 4;
-    using G = TileGeo<__half, K, PX>;    // halo padded to 8 columns: 16-byte aligned staging
+    using G = TileGeo<__half, K, PX>;
     const int TW = bx * PX, TH = by * PY, SW = TW + 2 * G::PAD, SH = TH + K - 1;
     float* st = sm;
     float* w = sm + SW * SH;
@@ -204,71 +256,225 @@ __device__ void batch_conv_tile(const BImg& im, int x0, int y0, int bx, int by, 
         stage_region(st, SW, SH, im.in, im.in_dt, im.in_pitch, x0 - G::PAD, y0 - R, im.W, im.H, im.border, im.bv, 0,
                      tid, nth, im.in_vec);
     __syncthreads();
-    if (tid < bx * by) {
-        const int tx = tid % bx, ty = tid / bx;
-        float acc[PY][PX];
-#pragma unroll
-        for (int oy = 0; oy < PY; ++oy)
-#pragma unroll
-            for (int ox = 0; ox < PX; ++ox) acc[oy][ox] = 0.f;
-        // filter row j outermost: its K taps stay in registers while the PY output rows
-        // that read input row (oy + j) accumulate (one shared-memory read per tap per tile).
-        // The j loop stays rolled: one batch kernel carries every filter side, and fully
-        // unrolled bodies for all of them would not fit the instruction cache together.
-#pragma unroll 1
-        for (int j = 0; j < K; ++j) {
-            float wr[K];
-#pragma unroll
-            for (int i = 0; i < K; ++i) wr[i] = w[j * K + i];
-#pragma unroll
-            for (int oy = 0; oy < PY; ++oy) {
-                float seg[G::SEG];
-                load_seg_smem<float, G>(st + (ty * PY + oy + j) * SW + tx * PX, seg);
-#pragma unroll
-                for (int i = 0; i < K; ++i)
-#pragma unroll
-                    for (int ox = 0; ox < PX; ++ox) acc[oy][ox] = __fmaf_rn(wr[i], seg[G::LO + ox + i], acc[oy][ox]);
-            }
-        }
-        const bool skip_edges = flipped_zero && im.border == IMCL_BORDER_CLAMP;   // edge items own those
-#pragma unroll
-        for (int oy = 0; oy < PY; ++oy) {
-            const int gy = y0 + ty * PY + oy;
-            if (gy >= im.H) continue;
-#pragma unroll
-            for (int ox = 0; ox < PX; ++ox) {
-                const int gx = x0 + tx * PX + ox;
-                if (gx >= im.W) continue;
-                if (skip_edges && (gx == 0 || gy == 0 || gx == im.W - 1 || gy == im.H - 1)) continue;
-                store_px(dst, dst_dt, dst_pitch, gx, gy, acc[oy][ox]);
-            }
-        }
+    conv_tile_compute<K, PY>(im, x0, y0, bx, by, st, SW, w, flipped_zero, dst, dst_pitch, dst_dt, tid);
+}
+
+// The forward runs warp-specialised: 8 consumer warps (256 threads, named barrier 1)
+// convert and compute tiles while one producer warp fetches the next ones.  The producer
+// takes tile indices from the queue two ahead, and for each tile fills one of two slots
+// with bulk asynchronous copies: the image descriptor, and every image row of the tile's
+// region widened to whole 16-byte words (the region is (TW + 16) x (TH + 2R) pixels at
+// (x0 - 8, y0 - R), clipped to the image).  It writes the taps (centred into the compiled
+// side), the per-row byte offsets and the tile origin with plain stores, and arrives on the
+// slot's `full` barrier.  A row whose widened span would leave the image's own bytes (the
+// first or last row of an image whose start or end is not 16-byte aligned) is not copied:
+// its offset is -1 and the consumers read it from global memory.  The consumers convert
+// the raw rows to the f32 region under the image's boundary rule, release the slot on its
+// `empty` barrier, and compute, so the copies of the next tiles overlap the current one.
+constexpr int kFwdConsumers = 256;
+constexpr int kFwdThreads = kFwdConsumers + 32;
+constexpr int kFwdMaxTaps = kBatchMaxK * kBatchMaxK;
+
+// Per-tile record the producer reads (one per forward tile, costliest first).
+struct alignas(16) BFwdTile {
+    const void* in;          // image base
+    const float* taps;       // conv: kh x kw; sep: row taps (kw)
+    const float* taps2;      // sep: column taps (kh)
+    long long pitch_b;       // row pitch in bytes
+    int W, H, K, es;         // size, compiled side, bytes per pixel
+    int op, kw, kh, img;     // operator, caller's tap counts, image index
+    int x0, y0, pad0, pad1;  // tile origin
+};
+
+struct FwdLayout {
+    int rows;        // region rows at the largest radius
+    int rp_max;      // raw row pitch in bytes at 4 bytes per pixel
+    int slot;        // bytes per slot
+    int s_img, s_info, s_row, s_taps, s_raw;   // offsets within a slot
+    int slot0, st, tb, w, img, total;          // offsets from the start of shared memory
+};
+
+__host__ __device__ inline FwdLayout fwd_layout(int TW, int TH) {
+    FwdLayout L;
+    const int sw = TW + 16;
+    L.rows = TH + 2 * kBatchMaxR;
+    L.rp_max = round_up(sw * 4 + 32, 16);
+    int o = 0;
+    L.s_img = o;  o += (int)sizeof(BImg);
+    L.s_info = o; o += 16;
+    L.s_row = o;  o += round_up(L.rows * 4, 16);
+    L.s_taps = o; o += round_up(kFwdMaxTaps * 4, 16);
+    L.s_raw = o;  o += L.rows * L.rp_max;
+    L.slot = round_up(o, 128);
+    L.slot0 = 128;                                   // barriers and flags below
+    L.st = L.slot0 + 2 * L.slot;
+    L.tb = L.st + sw * L.rows * 4;
+    L.w = L.tb + L.rows * TW * 4;
+    L.img = L.w + round_up(kFwdMaxTaps * 4, 16);
+    L.total = L.img + (int)sizeof(BImg);
+    return L;
+}
+
+__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+// True on every consumer thread if `p` holds on any of them (named barrier 1).
+__device__ __forceinline__ bool consumer_any(bool p) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred a, b;\n\t"
+        "setp.ne.u32 a, %1, 0;\n\t"
+        "bar.red.or.pred b, 1, 256, a;\n\t"
+        "selp.u32 %0, 1, 0, b;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)p)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ float raw_px(const uint8_t* p, int dt) {
+    switch (dt) {
+        case IMCL_F16: return __half2float(*reinterpret_cast<const __half*>(p));
+        case IMCL_BF16: return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(p));
+        default: return *reinterpret_cast<const float*>(p);
     }
 }
 
-// separable tile (forward): sm = staged region (TW + 2 PAD) x (TH + 2R), t buffer
-// (TH + 2R) x TW, 2(2R+1) taps.
+// Producer: fill slot `sl` with tile `ft` (all 32 lanes); tv: this lane's taps (entries
+// lane + 32 k of the centred table).  Returns after the arrival on `full`.
+__device__ __forceinline__ void fwd_fill(const BFwdTile& ft, const BImg* imgs, uint8_t* sl, const FwdLayout& L,
+                                         int TW, int TH, const float* tv, uint64_t* full, int lane) {
+    const int R = (ft.K - 1) / 2;
+    const int gx0 = ft.x0 - 8, sw = TW + 16, gy0 = ft.y0 - R, sh = TH + 2 * R;
+    const int cx0 = max(gx0, 0), cx1 = min(gx0 + sw, ft.W);
+    const int cy0 = max(gy0, 0), cy1 = min(gy0 + sh, ft.H);
+    const int rp = round_up(sw * ft.es + 32, 16);
+    const uintptr_t base = reinterpret_cast<uintptr_t>(ft.in);
+    const uintptr_t hi = base + ((uintptr_t)(ft.H - 1) * (uintptr_t)ft.pitch_b + (uintptr_t)ft.W * ft.es);
+    int* rowinfo = reinterpret_cast<int*>(sl + L.s_row);
+    uint32_t total = lane == 0 ? (uint32_t)sizeof(BImg) : 0u;
+    for (int y = cy0 + lane; y < cy1; y += 32) {
+        const uintptr_t row = base + (uintptr_t)y * (uintptr_t)ft.pitch_b;
+        const uintptr_t s = row + (uintptr_t)cx0 * ft.es, e = row + (uintptr_t)cx1 * ft.es;
+        const uintptr_t a0 = s & ~(uintptr_t)15, a1 = (e + 15) & ~(uintptr_t)15;
+        if (a0 >= base && a1 <= hi) total += (uint32_t)(a1 - a0);
+    }
+    total = __reduce_add_sync(0xffffffffu, total);
+    if (lane == 0) {
+        fence_proxy_async_smem();
+        mbar_expect_tx(full, total);
+    }
+    __syncwarp();
+    if (lane == 0) bulk_g2s(sl + L.s_img, imgs + ft.img, (uint32_t)sizeof(BImg), full);
+    for (int y = cy0 + lane; y < cy1; y += 32) {
+        const uintptr_t row = base + (uintptr_t)y * (uintptr_t)ft.pitch_b;
+        const uintptr_t s = row + (uintptr_t)cx0 * ft.es, e = row + (uintptr_t)cx1 * ft.es;
+        const uintptr_t a0 = s & ~(uintptr_t)15, a1 = (e + 15) & ~(uintptr_t)15;
+        const bool ok = a0 >= base && a1 <= hi;
+        if (ok) bulk_g2s(sl + L.s_raw + (y - cy0) * rp, reinterpret_cast<const void*>(a0), (uint32_t)(a1 - a0), full);
+        rowinfo[y - cy0] = ok ? (int)(s - a0) : -1;
+    }
+    float* taps = reinterpret_cast<float*>(sl + L.s_taps);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int i = lane + 32 * k;
+        if (i < kFwdMaxTaps) taps[i] = tv[k];
+    }
+    if (lane == 0) {
+        int* info = reinterpret_cast<int*>(sl + L.s_info);
+        info[0] = ft.x0;
+        info[1] = ft.y0;
+        info[2] = rp;
+        info[3] = 1;
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(full);
+}
+
+// Producer: this lane's entries of the tile's tap table (conv: K x K with the caller's
+// kh x kw centred, zeros elsewhere; sep: NT row taps then NT column taps, centred).
+__device__ __forceinline__ void fwd_load_taps(const BFwdTile& ft, int lane, float* tv) {
+    const int K = ft.K;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int i = lane + 32 * k;
+        float v = 0.f;
+        if (ft.op == IMCL_OP_CONV2D) {
+            if (i < K * K) {
+                const int R = (K - 1) / 2, j = i / K, c = i - j * K;
+                const int sj = j - (R - (ft.kh - 1) / 2), sc = c - (R - (ft.kw - 1) / 2);
+                if (sj >= 0 && sj < ft.kh && sc >= 0 && sc < ft.kw) v = __ldg(ft.taps + sj * ft.kw + sc);
+            }
+        } else if (i < 2 * K) {
+            const int R = (K - 1) / 2;
+            if (i < K) {
+                const int o = i - (R - (ft.kw - 1) / 2);
+                if (o >= 0 && o < ft.kw) v = __ldg(ft.taps + o);
+            } else {
+                const int o = i - K - (R - (ft.kh - 1) / 2);
+                if (o >= 0 && o < ft.kh) v = __ldg(ft.taps2 + o);
+            }
+        }
+        tv[k] = v;
+    }
+}
+
+// Consumers: raw rows of slot `sl` -> the f32 region st ((TW + 16) x (TH + 2R)) with the
+// image's boundary rule; taps -> w; the descriptor -> cur.
+__device__ __forceinline__ void fwd_convert(const uint8_t* sl, const FwdLayout& L, int TW, int TH, float* st,
+                                            float* w, BImg* cur, int tid) {
+    const BImg& im = *reinterpret_cast<const BImg*>(sl + L.s_img);
+    const int* info = reinterpret_cast<const int*>(sl + L.s_info);
+    const int* rowinfo = reinterpret_cast<const int*>(sl + L.s_row);
+    const uint8_t* raw = sl + L.s_raw;
+    const int x0 = info[0], y0 = info[1], rp = info[2];
+    const int R = (im.K - 1) / 2, W = im.W, H = im.H, dt = im.in_dt, es = dt == IMCL_F32 ? 4 : 2;
+    const int gx0 = x0 - 8, sw = TW + 16, gy0 = y0 - R, sh = TH + 2 * R;
+    const int cx0 = max(gx0, 0), cy0 = max(gy0, 0);
+    const bool cst = im.border == IMCL_BORDER_CONSTANT;
+    const int ng = sw >> 2;
+    for (int idx = tid; idx < ng * sh; idx += kFwdConsumers) {
+        const int r = idx / ng, c0 = (idx - r * ng) << 2;
+        const int gy = gy0 + r;
+        float v[4];
+        if (cst && (gy < 0 || gy >= H)) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[e] = im.bv;
+        } else {
+            const int yy = clampi(gy, 0, H - 1);
+            const int off = rowinfo[yy - cy0];
+            const uint8_t* rr = raw + (yy - cy0) * rp + off;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int gx = gx0 + c0 + e;
+                const int xx = clampi(gx, 0, W - 1);
+                float u;
+                if (off >= 0) u = raw_px(rr + (xx - cx0) * es, dt);
+                else u = load_px(im.in, dt, im.in_pitch, xx, yy);
+                v[e] = (cst && xx != gx) ? im.bv : u;
+            }
+        }
+        *reinterpret_cast<float4*>(st + r * sw + c0) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    const float* taps = reinterpret_cast<const float*>(sl + L.s_taps);
+    if (tid < kFwdMaxTaps) w[tid] = taps[tid];
+    static_assert(sizeof(BImg) % 16 == 0, "descriptor copies move whole 16-byte words");
+    if (tid < (int)(sizeof(BImg) / 16))
+        reinterpret_cast<uint4*>(cur)[tid] = reinterpret_cast<const uint4*>(&im)[tid];
+}
+
+// separable tile (forward) from the staged region st ((TW + 16) x (TH + 2R)) and taps w
+// (NT row taps, NT column taps); the row pass goes to tb ((TH + 2R) x TW).
 template <int R, int PY>
-__device__ void batch_sep_tile(const BImg& im, int x0, int y0, int bx, int by, float* sm, const int tid, const int nth) {
+__device__ void sep_tile_compute(const BImg& im, int x0, int y0, int bx, int by, const float* st, float* tb,
+                                 const float* w, const int tid) {
     constexpr int PX = 4, NT = 2 * R + 1;
     using G = TileGeo<__half, NT, PX>;   // halo padded to 8 columns: 16-byte aligned staging
-    const int TW = bx * PX, TH = by * PY, SW = TW + 2 * G::PAD, SH = TH + 2 * R;
-    float* st = sm;
-    float* tb = st + SW * SH;
-    float* w = tb + SH * TW;
-    const int orr = R - (im.kw - 1) / 2, orc = R - (im.kh - 1) / 2;
-    for (int i = tid; i < NT; i += nth) {
-        w[i] = (i >= orr && i < orr + im.kw) ? im.taps[i - orr] : 0.f;
-        w[NT + i] = (i >= orc && i < orc + im.kh) ? im.taps2[i - orc] : 0.f;
-    }
-    stage_region(st, SW, SH, im.in, im.in_dt, im.in_pitch, x0 - G::PAD, y0 - R, im.W, im.H, im.border, im.bv, 0, tid,
-                 nth, im.in_vec);
-    __syncthreads();
+    const int TW = bx * PX, SW = TW + 2 * G::PAD, SH = by * PY + 2 * R;
     float rw[NT], cw[NT];                 // row and column taps, in registers for the tile
 #pragma unroll
     for (int i = 0; i < NT; ++i) { rw[i] = w[i]; cw[i] = w[NT + i]; }
     const int nseg = TW / PX;
-    for (int it = tid; it < SH * nseg; it += nth) {
+    for (int it = tid; it < SH * nseg; it += kFwdConsumers) {
         const int row = it / nseg, c0 = (it - row * nseg) * PX;
         const int gy = y0 - R + row;
         float r4[PX];
@@ -287,7 +493,7 @@ __device__ void batch_sep_tile(const BImg& im, int x0, int y0, int bx, int by, f
         }
         *reinterpret_cast<float4*>(tb + row * TW + c0) = make_float4(r4[0], r4[1], r4[2], r4[3]);
     }
-    __syncthreads();
+    consumer_sync();
     if (tid < bx * by) {
         const int tx = tid % bx, ty = tid / bx;
         float acc[PY][PX];
@@ -315,47 +521,120 @@ __device__ void batch_sep_tile(const BImg& im, int x0, int y0, int bx, int by, f
 }
 
 template <int PY>
-__device__ __forceinline__ void batch_fwd_dispatch(const BImg& im, int x0, int y0, int bx, int by, float* sm, int tid,
-                                                   int nth) {
+__device__ __forceinline__ void batch_fwd_dispatch(const BImg& im, int x0, int y0, int bx, int by, const float* st,
+                                                   float* tb, const float* w, int tid) {
+    const int SW = 4 * bx + 16;
     if (im.op == IMCL_OP_CONV2D) {
         switch (im.K) {
-            case 3: batch_conv_tile<3, PY>(im, x0, y0, bx, by, sm, false, nullptr, 0, im.out, im.out_pitch, im.out_dt, tid, nth); break;
-            case 5: batch_conv_tile<5, PY>(im, x0, y0, bx, by, sm, false, nullptr, 0, im.out, im.out_pitch, im.out_dt, tid, nth); break;
-            case 7: batch_conv_tile<7, PY>(im, x0, y0, bx, by, sm, false, nullptr, 0, im.out, im.out_pitch, im.out_dt, tid, nth); break;
-            case 9: batch_conv_tile<9, PY>(im, x0, y0, bx, by, sm, false, nullptr, 0, im.out, im.out_pitch, im.out_dt, tid, nth); break;
-            case 11: batch_conv_tile<11, PY>(im, x0, y0, bx, by, sm, false, nullptr, 0, im.out, im.out_pitch, im.out_dt, tid, nth); break;
-            case 13: batch_conv_tile<13, PY>(im, x0, y0, bx, by, sm, false, nullptr, 0, im.out, im.out_pitch, im.out_dt, tid, nth); break;
-            default: batch_conv_tile<15, PY>(im, x0, y0, bx, by, sm, false, nullptr, 0, im.out, im.out_pitch, im.out_dt, tid, nth); break;
+            case 3: conv_tile_compute<3, PY>(im, x0, y0, bx, by, st, SW, w, false, im.out, im.out_pitch, im.out_dt, tid); break;
+            case 5: conv_tile_compute<5, PY>(im, x0, y0, bx, by, st, SW, w, false, im.out, im.out_pitch, im.out_dt, tid); break;
+            case 7: conv_tile_compute<7, PY>(im, x0, y0, bx, by, st, SW, w, false, im.out, im.out_pitch, im.out_dt, tid); break;
+            case 9: conv_tile_compute<9, PY>(im, x0, y0, bx, by, st, SW, w, false, im.out, im.out_pitch, im.out_dt, tid); break;
+            case 11: conv_tile_compute<11, PY>(im, x0, y0, bx, by, st, SW, w, false, im.out, im.out_pitch, im.out_dt, tid); break;
+            case 13: conv_tile_compute<13, PY>(im, x0, y0, bx, by, st, SW, w, false, im.out, im.out_pitch, im.out_dt, tid); break;
+            default: conv_tile_compute<15, PY>(im, x0, y0, bx, by, st, SW, w, false, im.out, im.out_pitch, im.out_dt, tid); break;
         }
     } else {
         switch (im.K) {
-            case 3: batch_sep_tile<1, PY>(im, x0, y0, bx, by, sm, tid, nth); break;
-            case 5: batch_sep_tile<2, PY>(im, x0, y0, bx, by, sm, tid, nth); break;
-            case 7: batch_sep_tile<3, PY>(im, x0, y0, bx, by, sm, tid, nth); break;
-            case 9: batch_sep_tile<4, PY>(im, x0, y0, bx, by, sm, tid, nth); break;
-            case 11: batch_sep_tile<5, PY>(im, x0, y0, bx, by, sm, tid, nth); break;
-            case 13: batch_sep_tile<6, PY>(im, x0, y0, bx, by, sm, tid, nth); break;
-            default: batch_sep_tile<7, PY>(im, x0, y0, bx, by, sm, tid, nth); break;
+            case 3: sep_tile_compute<1, PY>(im, x0, y0, bx, by, st, tb, w, tid); break;
+            case 5: sep_tile_compute<2, PY>(im, x0, y0, bx, by, st, tb, w, tid); break;
+            case 7: sep_tile_compute<3, PY>(im, x0, y0, bx, by, st, tb, w, tid); break;
+            case 9: sep_tile_compute<4, PY>(im, x0, y0, bx, by, st, tb, w, tid); break;
+            case 11: sep_tile_compute<5, PY>(im, x0, y0, bx, by, st, tb, w, tid); break;
+            case 13: sep_tile_compute<6, PY>(im, x0, y0, bx, by, st, tb, w, tid); break;
+            default: sep_tile_compute<7, PY>(im, x0, y0, bx, by, st, tb, w, tid); break;
         }
     }
 }
 
-// Persistent forward: CTAs take tiles from the work list until it is exhausted.
+// Persistent forward (kFwdThreads threads: warps 0-7 consume, warp 8 produces).
 template <int PY>
-__global__ void __launch_bounds__(256, 2)
-    k_batch_fwd(const BImg* __restrict__ imgs, const BTile* __restrict__ tiles, int ntiles, int* queue, int bx, int by) {
-    extern __shared__ __align__(16) float bsm[];
-    __shared__ int s_next;
-    const int tid = threadIdx.x, nth = blockDim.x;
-    for (;;) {
-        if (tid == 0) s_next = atomicAdd(queue, 1);
-        __syncthreads();
-        const int t = s_next;
-        if (t >= ntiles) break;
-        const BTile tl = tiles[t];
-        const BImg im = imgs[tl.img];
-        batch_fwd_dispatch<PY>(im, tl.x0, tl.y0, bx, by, bsm, tid, nth);
-        __syncthreads();   // shared memory and s_next are reused by the next tile
+__global__ void __launch_bounds__(kFwdThreads, 2)
+    k_batch_fwd(const BImg* __restrict__ imgs, const BFwdTile* __restrict__ tiles, int ntiles, int* queue, int bx,
+                int by, int* status) {
+    extern __shared__ __align__(128) uint8_t fsm[];
+    const int TW = 4 * bx, TH = PY * by;
+    const FwdLayout L = fwd_layout(TW, TH);
+    uint64_t* full = reinterpret_cast<uint64_t*>(fsm);
+    uint64_t* empty = full + 2;
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(fsm + 64);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init(&empty[0], kFwdConsumers);
+        mbar_init(&empty[1], kFwdConsumers);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (tid >= kFwdConsumers) {
+        // ---------------- producer warp
+        const int lane = tid - kFwdConsumers;
+        int raw_next = lane == 0 ? atomicAdd(queue, 1) : 0;
+        int cur = __shfl_sync(0xffffffffu, raw_next, 0);
+        raw_next = lane == 0 ? atomicAdd(queue, 1) : 0;
+        BFwdTile ft{};
+        if (cur < ntiles) ft = tiles[cur];
+        int issued[2] = {-1, -1};
+        for (int i = 0;; ++i) {
+            const int b = i & 1;
+            const int nxt = __shfl_sync(0xffffffffu, raw_next, 0);
+            BFwdTile ftn{};
+            if (nxt < ntiles) {
+                ftn = tiles[nxt];                               // used next iteration
+                raw_next = lane == 0 ? atomicAdd(queue, 1) : 0; // its index, the one after
+            } else {
+                raw_next = ntiles;
+            }
+            float tv[8];
+            if (cur < ntiles) fwd_load_taps(ft, lane, tv);
+            bool ok = true;
+            if (i >= 2) ok = mbar_wait(&empty[b], ((i >> 1) - 1) & 1u, status) && !*abort_flag;
+            if (!__all_sync(0xffffffffu, ok)) {
+                // consumers gone: wait for this warp's copies still in flight, then leave
+                for (int q = 0; q < 2; ++q)
+                    if (lane == 0 && issued[q] >= 0) mbar_wait(&full[q], issued[q] & 1u, nullptr);
+                break;
+            }
+            uint8_t* sl = fsm + L.slot0 + b * L.slot;
+            if (cur >= ntiles) {
+                if (lane == 0) {
+                    reinterpret_cast<int*>(sl + L.s_info)[3] = 0;
+                    mbar_arrive(&full[b]);
+                }
+                break;
+            }
+            fwd_fill(ft, imgs, sl, L, TW, TH, tv, &full[b], lane);
+            issued[b] = i >> 1;
+            cur = nxt;
+            ft = ftn;
+        }
+        return;
+    }
+
+    // ---------------- consumers
+    float* st = reinterpret_cast<float*>(fsm + L.st);
+    float* tb = reinterpret_cast<float*>(fsm + L.tb);
+    float* w = reinterpret_cast<float*>(fsm + L.w);
+    BImg* cur = reinterpret_cast<BImg*>(fsm + L.img);
+    for (int i = 0;; ++i) {
+        const int b = i & 1;
+        const bool ok = mbar_wait(&full[b], (i >> 1) & 1u, status);
+        if (consumer_any(!ok)) {
+            if (tid == 0) *abort_flag = 1;
+            break;
+        }
+        const uint8_t* sl = fsm + L.slot0 + b * L.slot;
+        const int* info = reinterpret_cast<const int*>(sl + L.s_info);
+        if (info[3] == 0) break;
+        const int x0 = info[0], y0 = info[1];
+        fwd_convert(sl, L, TW, TH, st, w, cur, tid);
+        mbar_arrive(&empty[b]);
+        consumer_sync();
+        batch_fwd_dispatch<PY>(*cur, x0, y0, bx, by, st, tb, w, tid);
+        consumer_sync();   // st, tb, w and cur are reused by the next tile
     }
 }
 

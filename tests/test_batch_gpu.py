@@ -82,6 +82,39 @@ def test_mixed_batch_matches_oracle_and_replays():
     b.close()
 
 
+def test_batch_pitched_views_unaligned():
+    """Images that are column windows of wider buffers: rows start off 16-byte boundaries
+    (the first rows and last rows of such images are read without bulk copies) and the
+    pitch exceeds the width."""
+    g = np.random.default_rng(9100)
+    items, meta = [], []
+    i = 0
+    for st, od in (("f16", torch.float16), ("bf16", torch.float32), ("f32", torch.float32)):
+        for (h, w, o) in ((1, 5, 1), (9, 70, 3), (130, 77, 5), (70, 260, 7), (300, 9, 2)):
+            border, bv = (("clamp", 0.0), ("constant", -0.625))[i % 2]
+            full = synth.to_storage(synth.uniform_f32(g, h, w + o + 11), st).cuda()
+            x = full[:, o:o + w]
+            if i % 2 == 0:
+                k = (3, 7, 15)[i % 3]
+                taps = g.standard_normal((k, k)).astype(np.float32)
+                items.append({"op": "conv", "x": x, "taps": torch.from_numpy(taps).cuda(), "out_dtype": od,
+                              "border": border, "border_value": bv})
+                meta.append(("conv", x.cpu(), taps, None, od, border, bv))
+            else:
+                r = g.standard_normal(2 * (i % 7) + 1).astype(np.float32)
+                c = g.standard_normal(2 * ((i + 3) % 7) + 1).astype(np.float32)
+                items.append({"op": "sep", "x": x, "taps": torch.from_numpy(r).cuda(),
+                              "col_taps": torch.from_numpy(c).cuda(), "out_dtype": od, "border": border,
+                              "border_value": bv})
+                meta.append(("sep", x.cpu(), r, c, od, border, bv))
+            i += 1
+    b = Batch(items, tune_budget_s=0.5)
+    outs = b.run()
+    torch.cuda.synchronize()
+    _check(meta, outs)
+    b.close()
+
+
 def test_workload_256_images_sampled():
     """256 f16 images, sides log-uniform in [64, 2048], each with an N(0,1) conv filter of
     odd side 3..15 or a Gaussian separable pair of radius 1..7: the whole batch in one
