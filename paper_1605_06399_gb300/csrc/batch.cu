@@ -107,7 +107,7 @@ static const void* bwd_kernel(int py) {
 
 size_t batch_bwd_smem_bytes(int py, int bx, int by) {
     const size_t TW = 4 * bx, TH = (size_t)py * by, K = kBatchMaxK, R = kBatchMaxR;
-    const size_t conv_dx = (TW + 16) * (TH + K - 1) + K * K;
+    const size_t conv_dx = (TW + 16) * (TH + K - 1) + K * kTapStride;
     const size_t conv_wg = std::max(TW * TH + (size_t)wg_xpitch<kBatchMaxK>((int)TW) * (TH + K - 1),
                                     (size_t)256 * WgCfg<kBatchMaxK>::JR * K + K * K);
     const size_t HH = TH + 2 * R, XW = TW + 16;

@@ -165,20 +165,60 @@ __device__ void stage_region(float* st, int sw, int sh, const void* img, int dt,
     }
 }
 
-// Store a PX-wide register row of f32 results to an image of any output type.
+// Store 4 f32 results at (gx..gx+3, gy) to an image of any output type: one dtype
+// branch per group, and 16-, 8- or 4-byte stores where the address allows.
+__device__ __forceinline__ uint32_t pack2_out(int dt, float a, float b) {
+    if (dt == IMCL_F16) {
+        const __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<const uint32_t*>(&h);
+    }
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
 template <int PX>
 __device__ __forceinline__ void store_row_any(void* out, int dt, long long pitch, int gx, int gy, int W, int H,
                                               const float* v) {
+    static_assert(PX == 4, "groups of 4 pixels");
     if (gy >= H) return;
+    const long long o = (long long)gy * pitch + gx;
+    const bool full = gx + 4 <= W;
+    if (dt == IMCL_F32) {
+        float* p = static_cast<float*>(out) + o;
+        if (full && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+            *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+        } else {
 #pragma unroll
-    for (int c = 0; c < PX; ++c)
-        if (gx + c < W) store_px(out, dt, pitch, gx + c, gy, v[c]);
+            for (int c = 0; c < 4; ++c)
+                if (full || gx + c < W) p[c] = v[c];
+        }
+        return;
+    }
+    uint16_t* p = static_cast<uint16_t*>(out) + o;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    if (full && (a & 7) == 0) {
+        *reinterpret_cast<uint2*>(p) = make_uint2(pack2_out(dt, v[0], v[1]), pack2_out(dt, v[2], v[3]));
+    } else if (full && (a & 3) == 0) {
+        reinterpret_cast<uint32_t*>(p)[0] = pack2_out(dt, v[0], v[1]);
+        reinterpret_cast<uint32_t*>(p)[1] = pack2_out(dt, v[2], v[3]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (full || gx + c < W)
+                p[c] = dt == IMCL_F16 ? __half_as_ushort(__float2half_rn(v[c]))
+                                      : __bfloat16_as_ushort(__float2bfloat16_rn(v[c]));
+    }
 }
 
 // ------------------------------------------------------------------ forward tiles
+// Tap tables in shared memory hold conv2d filter row j at w + j * kTapStride (16-byte
+// aligned rows, read as broadcast vectors).
+constexpr int kTapStride = 16;
+
 // conv2d: accumulate one tile from a staged region (rows SW wide, origin (x0 - 8, y0 - R))
-// and K*K taps in shared memory, and store it.  flipped_zero: the backward's dx tiles
-// (edge pixels of a clamped image belong to the edge items).
+// and the K x K taps (rows kTapStride apart) in shared memory, and store it.
+// flipped_zero: the backward's dx tiles (edge pixels of a clamped image belong to the
+// edge items).
 template <int K, int PY>
 __device__ __forceinline__ void conv_tile_compute(const BImg& im, int x0, int y0, int bx, int by, const float* st,
                                                   int SW, const float* w, bool flipped_zero, void* dst,
@@ -192,26 +232,38 @@ __device__ __forceinline__ void conv_tile_compute(const BImg& im, int x0, int y0
     for (int oy = 0; oy < PY; ++oy)
 #pragma unroll
         for (int ox = 0; ox < PX; ++ox) acc[oy][ox] = 0.f;
-    // filter row j outermost: its K taps stay in registers while the PY output rows
-    // that read input row (oy + j) accumulate (one shared-memory read per tap per tile).
-    // The j loop stays rolled: one batch kernel carries every filter side, and fully
-    // unrolled bodies for all of them would not fit the instruction cache together.
+    // filter row j outermost: its K taps (broadcast 16-byte loads) stay in registers while
+    // the PY output rows that read input row (oy + j) accumulate.  The j loop stays rolled:
+    // one batch kernel carries every filter side, and fully unrolled bodies for all of
+    // them would not fit the instruction cache together.
+    static_assert(K <= kTapStride, "filter rows wider than the tap table stride");
+    constexpr int KV = (K + 3) / 4;
+    const float* srow = st + ty * PY * SW + tx * PX;
 #pragma unroll 1
     for (int j = 0; j < K; ++j) {
-        float wr[K];
+        float wr[4 * KV];
 #pragma unroll
-        for (int i = 0; i < K; ++i) wr[i] = w[j * K + i];
+        for (int q = 0; q < KV; ++q) {
+            const float4 t4 = *reinterpret_cast<const float4*>(w + j * kTapStride + 4 * q);
+            wr[4 * q] = t4.x; wr[4 * q + 1] = t4.y; wr[4 * q + 2] = t4.z; wr[4 * q + 3] = t4.w;
+        }
 #pragma unroll
         for (int oy = 0; oy < PY; ++oy) {
             float seg[G::SEG];
-            load_seg_smem<float, G>(st + (ty * PY + oy + j) * SW + tx * PX, seg);
+            load_seg_smem<float, G>(srow + (oy + j) * SW, seg);
 #pragma unroll
             for (int i = 0; i < K; ++i)
 #pragma unroll
                 for (int ox = 0; ox < PX; ++ox) acc[oy][ox] = __fmaf_rn(wr[i], seg[G::LO + ox + i], acc[oy][ox]);
         }
     }
-    const bool skip_edges = flipped_zero && im.border == IMCL_BORDER_CLAMP;   // edge items own those
+    if (!flipped_zero) {
+#pragma unroll
+        for (int oy = 0; oy < PY; ++oy)
+            store_row_any<PX>(dst, dst_dt, dst_pitch, x0 + tx * PX, y0 + ty * PY + oy, im.W, im.H, acc[oy]);
+        return;
+    }
+    const bool skip_edges = im.border == IMCL_BORDER_CLAMP;   // edge items own those
 #pragma unroll
     for (int oy = 0; oy < PY; ++oy) {
         const int gy = y0 + ty * PY + oy;
@@ -227,7 +279,7 @@ __device__ __forceinline__ void conv_tile_compute(const BImg& im, int x0, int y0
 }
 
 // conv2d tile with its own staging (the backward's input-gradient tiles): sm holds the
-// staged region (TW + 16) x (TH + K - 1), then K*K taps.
+// staged region (TW + 16) x (TH + K - 1), then the K x kTapStride tap table.
 template <int K, int PY>
 __device__ void batch_conv_tile(const BImg& im, int x0, int y0, int bx, int by, float* sm, bool flipped_zero,
                                 const float* g_src, long long g_pitch, void* dst, long long dst_pitch, int dst_dt,
@@ -239,11 +291,11 @@ __device__ void batch_conv_tile(const BImg& im, int x0, int y0, int bx, int by, 
     float* w = sm + SW * SH;
     const int R = (K - 1) / 2, rx = (im.kw - 1) / 2, ry = (im.kh - 1) / 2;
     // taps, centred into K x K (zero elsewhere); flipped for the adjoint
-    for (int i = tid; i < K * K; i += nth) {
-        const int j = i / K, c = i % K;
+    for (int i = tid; i < K * kTapStride; i += nth) {
+        const int j = i / kTapStride, c = i % kTapStride;
         const int sj = j - (R - ry), sc = c - (R - rx);
         float v = 0.f;
-        if (sj >= 0 && sj < im.kh && sc >= 0 && sc < im.kw) {
+        if (c < K && sj >= 0 && sj < im.kh && sc >= 0 && sc < im.kw) {
             const int o = flipped_zero ? (im.kh - 1 - sj) * im.kw + (im.kw - 1 - sc) : sj * im.kw + sc;
             v = im.taps[o];
         }
@@ -273,7 +325,7 @@ __device__ void batch_conv_tile(const BImg& im, int x0, int y0, int bx, int by, 
 // `empty` barrier, and compute, so the copies of the next tiles overlap the current one.
 constexpr int kFwdConsumers = 256;
 constexpr int kFwdThreads = kFwdConsumers + 32;
-constexpr int kFwdMaxTaps = kBatchMaxK * kBatchMaxK;
+constexpr int kFwdMaxTaps = kBatchMaxK * kTapStride;   // the largest tap table
 
 // Per-tile record the producer reads (one per forward tile, costliest first).
 struct alignas(16) BFwdTile {
@@ -390,8 +442,9 @@ __device__ __forceinline__ void fwd_fill(const BFwdTile& ft, const BImg* imgs, u
     if (lane == 0) mbar_arrive(full);
 }
 
-// Producer: this lane's entries of the tile's tap table (conv: K x K with the caller's
-// kh x kw centred, zeros elsewhere; sep: NT row taps then NT column taps, centred).
+// Producer: this lane's entries of the tile's tap table (conv: K rows kTapStride apart
+// with the caller's kh x kw centred, zeros elsewhere; sep: NT row taps then NT column
+// taps, centred).
 __device__ __forceinline__ void fwd_load_taps(const BFwdTile& ft, int lane, float* tv) {
     const int K = ft.K;
 #pragma unroll
@@ -399,8 +452,9 @@ __device__ __forceinline__ void fwd_load_taps(const BFwdTile& ft, int lane, floa
         const int i = lane + 32 * k;
         float v = 0.f;
         if (ft.op == IMCL_OP_CONV2D) {
-            if (i < K * K) {
-                const int R = (K - 1) / 2, j = i / K, c = i - j * K;
+            const int j = i / kTapStride, c = i % kTapStride;
+            if (j < K && c < K) {
+                const int R = (K - 1) / 2;
                 const int sj = j - (R - (ft.kh - 1) / 2), sc = c - (R - (ft.kw - 1) / 2);
                 if (sj >= 0 && sj < ft.kh && sc >= 0 && sc < ft.kw) v = __ldg(ft.taps + sj * ft.kw + sc);
             }
@@ -418,42 +472,114 @@ __device__ __forceinline__ void fwd_load_taps(const BFwdTile& ft, int lane, floa
     }
 }
 
+// 4 pixels of a raw row at p (converted to f32), with the widest loads p's alignment
+// allows (uniform along a row: the groups of one row are 4 pixels apart).
+template <int DT>
+__device__ __forceinline__ void raw_load4(const uint8_t* p, float* v) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    if constexpr (DT == IMCL_F32) {
+        if ((a & 15) == 0) {
+            const float4 q = *reinterpret_cast<const float4*>(p);
+            v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+        } else if ((a & 7) == 0) {
+            const float2 q0 = reinterpret_cast<const float2*>(p)[0], q1 = reinterpret_cast<const float2*>(p)[1];
+            v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[e] = reinterpret_cast<const float*>(p)[e];
+        }
+    } else {
+        uint32_t u0, u1;
+        if ((a & 7) == 0) {
+            const uint2 q = *reinterpret_cast<const uint2*>(p);
+            u0 = q.x; u1 = q.y;
+        } else if ((a & 3) == 0) {
+            u0 = reinterpret_cast<const uint32_t*>(p)[0];
+            u1 = reinterpret_cast<const uint32_t*>(p)[1];
+        } else {
+            const uint16_t* h = reinterpret_cast<const uint16_t*>(p);
+            u0 = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
+            u1 = (uint32_t)h[2] | ((uint32_t)h[3] << 16);
+        }
+        if constexpr (DT == IMCL_F16) {
+            const float2 f0 = __half22float2(*reinterpret_cast<const __half2*>(&u0));
+            const float2 f1 = __half22float2(*reinterpret_cast<const __half2*>(&u1));
+            v[0] = f0.x; v[1] = f0.y; v[2] = f1.x; v[3] = f1.y;
+        } else {
+            v[0] = __uint_as_float(u0 << 16); v[1] = __uint_as_float(u0 & 0xffff0000u);
+            v[2] = __uint_as_float(u1 << 16); v[3] = __uint_as_float(u1 & 0xffff0000u);
+        }
+    }
+}
+
+template <int DT>
+__device__ __forceinline__ float raw_load1(const uint8_t* p) {
+    if constexpr (DT == IMCL_F32) return *reinterpret_cast<const float*>(p);
+    else if constexpr (DT == IMCL_F16) return __half2float(*reinterpret_cast<const __half*>(p));
+    else return __uint_as_float((uint32_t)*reinterpret_cast<const uint16_t*>(p) << 16);
+}
+
 // Consumers: raw rows of slot `sl` -> the f32 region st ((TW + 16) x (TH + 2R)) with the
-// image's boundary rule; taps -> w; the descriptor -> cur.
+// image's boundary rule, 4 pixels per item, NG items per row; unrolled so that each
+// thread has several rows' loads in flight.
+template <int DT, int NG>
+__device__ __forceinline__ void fwd_convert_rows(const BImg& im, const int* __restrict__ info,
+                                                 const int* __restrict__ rowinfo, const uint8_t* __restrict__ raw,
+                                                 int TH, float* __restrict__ st, int tid) {
+    constexpr int ES = DT == IMCL_F32 ? 4 : 2;
+    constexpr int SW = 4 * NG;
+    const int x0 = info[0], y0 = info[1], rp = info[2];
+    const int R = (im.K - 1) / 2, W = im.W, H = im.H;
+    const int gx0 = x0 - 8, gy0 = y0 - R, sh = TH + 2 * R;
+    const int cx0 = max(gx0, 0), cy0 = max(gy0, 0);
+    const bool cst = im.border == IMCL_BORDER_CONSTANT;
+    const float bv = im.bv;
+#pragma unroll 4
+    for (int idx = tid; idx < NG * sh; idx += kFwdConsumers) {
+        const int r = idx / NG, c0 = (idx - r * NG) * 4;
+        const int gy = gy0 + r, gx = gx0 + c0;
+        float v[4];
+        if (cst && (gy < 0 || gy >= H)) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[e] = bv;
+        } else {
+            const int yy = clampi(gy, 0, H - 1);
+            const int off = rowinfo[yy - cy0];
+            const uint8_t* rr = raw + (yy - cy0) * rp + off;   // pixel x at rr + (x - cx0) * ES
+            if (off >= 0 && gx >= 0 && gx + 4 <= W) {
+                raw_load4<DT>(rr + (gx - cx0) * ES, v);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int xx = clampi(gx + e, 0, W - 1);
+                    const float u = off >= 0 ? raw_load1<DT>(rr + (xx - cx0) * ES)
+                                             : load_px(im.in, DT, im.in_pitch, xx, yy);
+                    v[e] = (cst && xx != gx + e) ? bv : u;
+                }
+            }
+        }
+        *reinterpret_cast<float4*>(st + r * SW + c0) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+}
+
+template <int DT>
+__device__ __forceinline__ void fwd_convert_dt(const BImg& im, const int* info, const int* rowinfo,
+                                               const uint8_t* raw, int TW, int TH, float* st, int tid) {
+    if (TW == 64) fwd_convert_rows<DT, 20>(im, info, rowinfo, raw, TH, st, tid);
+    else fwd_convert_rows<DT, 36>(im, info, rowinfo, raw, TH, st, tid);
+}
+
+// Consumers: the slot's raw rows -> st; taps -> w; the descriptor -> cur.
 __device__ __forceinline__ void fwd_convert(const uint8_t* sl, const FwdLayout& L, int TW, int TH, float* st,
                                             float* w, BImg* cur, int tid) {
     const BImg& im = *reinterpret_cast<const BImg*>(sl + L.s_img);
     const int* info = reinterpret_cast<const int*>(sl + L.s_info);
     const int* rowinfo = reinterpret_cast<const int*>(sl + L.s_row);
     const uint8_t* raw = sl + L.s_raw;
-    const int x0 = info[0], y0 = info[1], rp = info[2];
-    const int R = (im.K - 1) / 2, W = im.W, H = im.H, dt = im.in_dt, es = dt == IMCL_F32 ? 4 : 2;
-    const int gx0 = x0 - 8, sw = TW + 16, gy0 = y0 - R, sh = TH + 2 * R;
-    const int cx0 = max(gx0, 0), cy0 = max(gy0, 0);
-    const bool cst = im.border == IMCL_BORDER_CONSTANT;
-    const int ng = sw >> 2;
-    for (int idx = tid; idx < ng * sh; idx += kFwdConsumers) {
-        const int r = idx / ng, c0 = (idx - r * ng) << 2;
-        const int gy = gy0 + r;
-        float v[4];
-        if (cst && (gy < 0 || gy >= H)) {
-#pragma unroll
-            for (int e = 0; e < 4; ++e) v[e] = im.bv;
-        } else {
-            const int yy = clampi(gy, 0, H - 1);
-            const int off = rowinfo[yy - cy0];
-            const uint8_t* rr = raw + (yy - cy0) * rp + off;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int gx = gx0 + c0 + e;
-                const int xx = clampi(gx, 0, W - 1);
-                float u;
-                if (off >= 0) u = raw_px(rr + (xx - cx0) * es, dt);
-                else u = load_px(im.in, dt, im.in_pitch, xx, yy);
-                v[e] = (cst && xx != gx) ? im.bv : u;
-            }
-        }
-        *reinterpret_cast<float4*>(st + r * sw + c0) = make_float4(v[0], v[1], v[2], v[3]);
+    switch (im.in_dt) {
+        case IMCL_F16: fwd_convert_dt<IMCL_F16>(im, info, rowinfo, raw, TW, TH, st, tid); break;
+        case IMCL_BF16: fwd_convert_dt<IMCL_BF16>(im, info, rowinfo, raw, TW, TH, st, tid); break;
+        default: fwd_convert_dt<IMCL_F32>(im, info, rowinfo, raw, TW, TH, st, tid); break;
     }
     const float* taps = reinterpret_cast<const float*>(sl + L.s_taps);
     if (tid < kFwdMaxTaps) w[tid] = taps[tid];
@@ -562,8 +688,8 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
     if (tid == 0) {
         mbar_init(&full[0], 1);
         mbar_init(&full[1], 1);
-        mbar_init(&empty[0], kFwdConsumers);
-        mbar_init(&empty[1], kFwdConsumers);
+        mbar_init(&empty[0], kFwdConsumers / 32);
+        mbar_init(&empty[1], kFwdConsumers / 32);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -631,7 +757,8 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
         if (info[3] == 0) break;
         const int x0 = info[0], y0 = info[1];
         fwd_convert(sl, L, TW, TH, st, w, cur, tid);
-        mbar_arrive(&empty[b]);
+        __syncwarp();
+        if ((tid & 31) == 0) mbar_arrive(&empty[b]);   // this warp is done with the slot
         consumer_sync();
         batch_fwd_dispatch<PY>(*cur, x0, y0, bx, by, st, tb, w, tid);
         consumer_sync();   // st, tb, w and cur are reused by the next tile
