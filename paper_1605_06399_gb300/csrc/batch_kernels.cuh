@@ -338,6 +338,11 @@ struct alignas(16) BFwdTile {
     int x0, y0, pad0, pad1;  // tile origin
 };
 
+// The forward's staged rows are TW + 16 pixels, stored kFwdPitchPad floats further
+// apart: a row pitch of 20 words modulo 32 spreads a warp's 16-byte loads from several
+// rows over all bank groups.
+constexpr int kFwdPitchPad = 4;
+
 struct FwdLayout {
     int rows;        // region rows at the largest radius
     int rp_max;      // raw row pitch in bytes at 4 bytes per pixel
@@ -360,7 +365,7 @@ __host__ __device__ inline FwdLayout fwd_layout(int TW, int TH) {
     L.slot = round_up(o, 128);
     L.slot0 = 128;                                   // barriers and flags below
     L.st = L.slot0 + 2 * L.slot;
-    L.tb = L.st + sw * L.rows * 4;
+    L.tb = L.st + (sw + kFwdPitchPad) * L.rows * 4;
     L.w = L.tb + L.rows * TW * 4;
     L.img = L.w + round_up(kFwdMaxTaps * 4, 16);
     L.total = L.img + (int)sizeof(BImg);
@@ -519,6 +524,47 @@ __device__ __forceinline__ float raw_load1(const uint8_t* p) {
     else return __uint_as_float((uint32_t)*reinterpret_cast<const uint16_t*>(p) << 16);
 }
 
+// conv2d forward tile from the staged region st (rows SWP apart, origin (x0 - 8, y0 - R))
+// and the tap table w: a thread computes PXC consecutive pixels of one row.  Per filter
+// row j it loads its row segment (PXC + K - 1 pixels) once and the K taps as broadcast
+// vectors, then runs K * PXC independent-accumulator FMAs.
+template <int K, int PXC>
+__device__ __forceinline__ void conv_fwd_compute(const BImg& im, int x0, int y0, int TW, const float* st, int SWP,
+                                                 const float* w, int tid) {
+    constexpr int R = (K - 1) / 2, LO = 8 - R, USED = PXC + K - 1;
+    constexpr int C0 = LO / 4 * 4, NCH = (LO + USED - 1) / 4 - LO / 4 + 1, D = LO - C0;
+    constexpr int KV = (K + 3) / 4;
+    static_assert(K <= kTapStride && PXC % 4 == 0, "tap rows and pixel groups");
+    const int nx = TW / PXC;
+    const int tx = tid % nx, ty = tid / nx;
+    float acc[PXC];
+#pragma unroll
+    for (int ox = 0; ox < PXC; ++ox) acc[ox] = 0.f;
+    const float* srow = st + ty * SWP + tx * PXC + C0;
+#pragma unroll 1
+    for (int j = 0; j < K; ++j) {
+        float wr[4 * KV];
+#pragma unroll
+        for (int q = 0; q < KV; ++q) {
+            const float4 t4 = *reinterpret_cast<const float4*>(w + j * kTapStride + 4 * q);
+            wr[4 * q] = t4.x; wr[4 * q + 1] = t4.y; wr[4 * q + 2] = t4.z; wr[4 * q + 3] = t4.w;
+        }
+        float seg[4 * NCH];
+#pragma unroll
+        for (int q = 0; q < NCH; ++q) {
+            const float4 s4 = *reinterpret_cast<const float4*>(srow + j * SWP + 4 * q);
+            seg[4 * q] = s4.x; seg[4 * q + 1] = s4.y; seg[4 * q + 2] = s4.z; seg[4 * q + 3] = s4.w;
+        }
+#pragma unroll
+        for (int i = 0; i < K; ++i)
+#pragma unroll
+            for (int ox = 0; ox < PXC; ++ox) acc[ox] = __fmaf_rn(wr[i], seg[D + ox + i], acc[ox]);
+    }
+#pragma unroll
+    for (int g = 0; g < PXC / 4; ++g)
+        store_row_any<4>(im.out, im.out_dt, im.out_pitch, x0 + tx * PXC + 4 * g, y0 + ty, im.W, im.H, acc + 4 * g);
+}
+
 // Consumers: raw rows of slot `sl` -> the f32 region st ((TW + 16) x (TH + 2R)) with the
 // image's boundary rule, 4 pixels per item, NG items per row; unrolled so that each
 // thread has several rows' loads in flight.
@@ -527,7 +573,7 @@ __device__ __forceinline__ void fwd_convert_rows(const BImg& im, const int* __re
                                                  const int* __restrict__ rowinfo, const uint8_t* __restrict__ raw,
                                                  int TH, float* __restrict__ st, int tid) {
     constexpr int ES = DT == IMCL_F32 ? 4 : 2;
-    constexpr int SW = 4 * NG;
+    constexpr int SW = 4 * NG + kFwdPitchPad;
     const int x0 = info[0], y0 = info[1], rp = info[2];
     const int R = (im.K - 1) / 2, W = im.W, H = im.H;
     const int gx0 = x0 - 8, gy0 = y0 - R, sh = TH + 2 * R;
@@ -595,7 +641,7 @@ __device__ void sep_tile_compute(const BImg& im, int x0, int y0, int bx, int by,
                                  const float* w, const int tid) {
     constexpr int PX = 4, NT = 2 * R + 1;
     using G = TileGeo<__half, NT, PX>;   // halo padded to 8 columns: 16-byte aligned staging
-    const int TW = bx * PX, SW = TW + 2 * G::PAD, SH = by * PY + 2 * R;
+    const int TW = bx * PX, SW = TW + 2 * G::PAD + kFwdPitchPad, SH = by * PY + 2 * R;
     float rw[NT], cw[NT];                 // row and column taps, in registers for the tile
 #pragma unroll
     for (int i = 0; i < NT; ++i) { rw[i] = w[i]; cw[i] = w[NT + i]; }
@@ -649,16 +695,19 @@ __device__ void sep_tile_compute(const BImg& im, int x0, int y0, int bx, int by,
 template <int PY>
 __device__ __forceinline__ void batch_fwd_dispatch(const BImg& im, int x0, int y0, int bx, int by, const float* st,
                                                    float* tb, const float* w, int tid) {
-    const int SW = 4 * bx + 16;
+    constexpr int PXC = 4 * PY;          // (4 bx / PXC) x (PY by) = bx x by threads
+    const int TW = 4 * bx, SWP = TW + 16 + kFwdPitchPad;
     if (im.op == IMCL_OP_CONV2D) {
         switch (im.K) {
-            case 3: conv_tile_compute<3, PY>(im, x0, y0, bx, by, st, SW, w, false, im.out, im.out_pitch, im.out_dt, tid); break;
-            case 5: conv_tile_compute<5, PY>(im, x0, y0, bx, by, st, SW, w, false, im.out, im.out_pitch, im.out_dt, tid); break;
-            case 7: conv_tile_compute<7, PY>(im, x0, y0, bx, by, st, SW, w, false, im.out, im.out_pitch, im.out_dt, tid); break;
-            case 9: conv_tile_compute<9, PY>(im, x0, y0, bx, by, st, SW, w, false, im.out, im.out_pitch, im.out_dt, tid); break;
-            case 11: conv_tile_compute<11, PY>(im, x0, y0, bx, by, st, SW, w, false, im.out, im.out_pitch, im.out_dt, tid); break;
-            case 13: conv_tile_compute<13, PY>(im, x0, y0, bx, by, st, SW, w, false, im.out, im.out_pitch, im.out_dt, tid); break;
-            default: conv_tile_compute<15, PY>(im, x0, y0, bx, by, st, SW, w, false, im.out, im.out_pitch, im.out_dt, tid); break;
+            // small filters: 4 x PY blocks (contiguous stores; the segment loads are cheap)
+            case 3: conv_tile_compute<3, PY>(im, x0, y0, bx, by, st, SWP, w, false, im.out, im.out_pitch, im.out_dt, tid); break;
+            case 5: conv_tile_compute<5, PY>(im, x0, y0, bx, by, st, SWP, w, false, im.out, im.out_pitch, im.out_dt, tid); break;
+            case 7: conv_tile_compute<7, PY>(im, x0, y0, bx, by, st, SWP, w, false, im.out, im.out_pitch, im.out_dt, tid); break;
+            // larger ones: a row of PXC pixels per thread (fewer shared-memory wavefronts per FMA)
+            case 9: conv_fwd_compute<9, PXC>(im, x0, y0, TW, st, SWP, w, tid); break;
+            case 11: conv_fwd_compute<11, PXC>(im, x0, y0, TW, st, SWP, w, tid); break;
+            case 13: conv_fwd_compute<13, PXC>(im, x0, y0, TW, st, SWP, w, tid); break;
+            default: conv_fwd_compute<15, PXC>(im, x0, y0, TW, st, SWP, w, tid); break;
         }
     } else {
         switch (im.K) {
