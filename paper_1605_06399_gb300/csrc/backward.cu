@@ -9,6 +9,7 @@
 #include "backward_internal.h"
 #include "backward_kernels.cuh"
 #include "harris_bwd_kernels.cuh"
+#include "sepbwd_kernels.cuh"
 
 namespace imcl {
 
@@ -247,10 +248,76 @@ imcl_status conv2d_backward_run(const BwdArgs& b, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ sepconv
+// The fused separable adjoint (equal row and column radii up to kSbMaxR): one persistent
+// launch for dx and both tap-gradient partial sets, then the fixed-order reductions.
+template <int R>
+static imcl_status sep_bwd_fused(const BwdArgs& b, float* ws, size_t ws_floats, cudaStream_t s) {
+    constexpr int NT = 2 * R + 1;
+    const ConvCall& f = b.fwd;
+    const int W = f.W, H = f.H;
+    SbTaps<R> tp;
+    memset(&tp, 0, sizeof tp);
+    SbArgs a{};
+    if (f.taps_mem == IMCL_MEM_HOST) {
+        memcpy(tp.r, f.taps, sizeof tp.r);
+        memcpy(tp.c, f.taps2, sizeof tp.c);
+    } else {
+        a.rdev = static_cast<const float*>(f.taps);
+        a.cdev = static_cast<const float*>(f.taps2);
+    }
+    a.g = b.g;
+    a.gp = b.g_pitch_b / 4;
+    a.x = f.in;
+    a.x_dt = f.in_dtype;
+    a.xp = f.in_pitch_b / dtype_size(f.in_dtype);
+    a.dx = b.dx;
+    a.dxp = b.dx ? b.dx_pitch_b / 4 : 0;
+    a.W = W;
+    a.H = H;
+    a.border = f.border;
+    const float bv = (float)f.border_value;
+    a.bvt = bv;
+    a.bvx = f.in_dtype == IMCL_F16 ? __half2float(__float2half_rn(bv))
+          : f.in_dtype == IMCL_BF16 ? __bfloat162float(__float2bfloat16_rn(bv)) : bv;
+    a.tiles_x = (W + kSbTileW - 1) / kSbTileW;
+    a.ntiles = a.tiles_x * ((H + kSbTileH - 1) / kSbTileH);
+    a.vec = f.in_dtype == IMCL_F32 && ((reinterpret_cast<uintptr_t>(b.g) | reinterpret_cast<uintptr_t>(f.in) |
+                                         (uintptr_t)b.g_pitch_b | (uintptr_t)f.in_pitch_b) & 15) == 0;
+    const int smem = SbGeo<R>::SMEM * (int)sizeof(float);
+    auto kfn = k_sep_bwd_fused<R>;
+    IMCL_TRY(set_smem_limit((const void*)kfn, smem));
+    const int occ = cached_occupancy((const void*)kfn, 256, smem);
+    if (occ <= 0) return fail(IMCL_ERR_UNSUPPORTED, "fused separable backward cannot be resident");
+    int grid = std::min(a.ntiles, occ * f.dev->sm_count);
+    grid = std::max(1, std::min<int>(grid, (int)(ws_floats / (2 * NT))));   // partial sets that fit
+    a.prow = ws;
+    a.pcol = ws + (size_t)grid * NT;
+    kfn<<<grid, 256, smem, s>>>(a, tp);
+    IMCL_TRY(cuda_fail(cudaGetLastError(), "fused separable backward"));
+    if (b.dw0) IMCL_TRY(finalize(a.prow, grid, NT, b.dw0, s));
+    if (b.dw1) IMCL_TRY(finalize(a.pcol, grid, NT, b.dw1, s));
+    return IMCL_OK;
+}
+
 imcl_status sepconv_backward_run(const BwdArgs& b, cudaStream_t s) {
     const ConvCall& f = b.fwd;
     const int W = f.W, H = f.H, nr = f.kw, nc = f.kh;
     const size_t pf = plane_floats(W, H);
+    if (nr == nc && (nr - 1) / 2 <= kSbMaxR) {
+        float* ws0 = static_cast<float*>(b.workspace);
+        const size_t wsf = 2 * pf;   // the two planes the multi-pass form uses hold the partial sums
+        switch ((nr - 1) / 2) {
+            case 0: return sep_bwd_fused<0>(b, ws0, wsf, s);
+            case 1: return sep_bwd_fused<1>(b, ws0, wsf, s);
+            case 2: return sep_bwd_fused<2>(b, ws0, wsf, s);
+            case 3: return sep_bwd_fused<3>(b, ws0, wsf, s);
+            case 4: return sep_bwd_fused<4>(b, ws0, wsf, s);
+            case 5: return sep_bwd_fused<5>(b, ws0, wsf, s);
+            case 6: return sep_bwd_fused<6>(b, ws0, wsf, s);
+            case 7: return sep_bwd_fused<7>(b, ws0, wsf, s);
+            default: return sep_bwd_fused<8>(b, ws0, wsf, s);
+        }
+    }
     const int64_t pp_b = (int64_t)plane_pitch(W) * 4;
     float* ws = static_cast<float*>(b.workspace);
     float* T = ws;

@@ -57,8 +57,9 @@ def test_conv2d_backward_matches_oracle(k, dt):
                 _gate(dw, dw64, sdw, "dw " + what)
 
 
-@pytest.mark.parametrize("nr,nc", [(3, 3), (5, 9), (33, 1), (1, 33), (15, 7)])
-@pytest.mark.parametrize("dt", ["f32", "bf16"])
+# equal sides up to 17 run the fused one-pass adjoint, the others the multi-pass form
+@pytest.mark.parametrize("nr,nc", [(1, 1), (3, 3), (5, 5), (17, 17), (19, 19), (5, 9), (33, 1), (1, 33), (15, 7)])
+@pytest.mark.parametrize("dt", ["f32", "f16", "bf16"])
 def test_sepconv_backward_matches_oracle(nr, nc, dt):
     g = np.random.default_rng(6000 + nr * 40 + nc)
     r = g.standard_normal(nr).astype(np.float32)
@@ -70,10 +71,11 @@ def test_sepconv_backward_matches_oracle(nr, nc, dt):
             dx64, dr64, dc64 = oracle.sepconv_backward(x, r, c, gr, border, bv)
             sdx, sdr, sdc = oracle.sepconv_backward(np.abs(to_f64(x)), np.abs(r), np.abs(c), np.abs(gr), border,
                                                     abs(bv))
-            for mem in ("host", "device"):
+            for mem, layout in (("host", "dense"), ("device", "padded")):
                 rt = torch.from_numpy(r).cuda() if mem == "device" else r
                 ct = torch.from_numpy(c).cuda() if mem == "device" else c
-                dx, dr, dc = ops.sepconv_backward(torch.from_numpy(gr).cuda(), x.cuda(), rt, ct, border, bv)
+                dx, dr, dc = ops.sepconv_backward(place(torch.from_numpy(gr), layout), place(x, layout), rt, ct,
+                                                  border, bv)
                 what = f"{nr}x{nc} {dt} {h}x{wd} {border} {mem}"
                 _gate(dx, dx64, sdx, "dx " + what)
                 _gate(dr, dr64, sdr, "drow " + what)
