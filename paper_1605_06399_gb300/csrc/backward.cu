@@ -283,8 +283,17 @@ static imcl_status sep_bwd_fused(const BwdArgs& b, float* ws, size_t ws_floats, 
     a.ntiles = a.tiles_x * ((H + kSbTileH - 1) / kSbTileH);
     a.vec = f.in_dtype == IMCL_F32 && ((reinterpret_cast<uintptr_t>(b.g) | reinterpret_cast<uintptr_t>(f.in) |
                                          (uintptr_t)b.g_pitch_b | (uintptr_t)f.in_pitch_b) & 15) == 0;
-    const int smem = SbGeo<R>::SMEM * (int)sizeof(float);
-    auto kfn = k_sep_bwd_fused<R>;
+    // f32 operands on 16-byte aligned rows: TMA staging in a two-stage ring
+    CUtensorMap gmap, xmap;
+    memset(&gmap, 0, sizeof gmap);
+    memset(&xmap, 0, sizeof xmap);
+    if (a.vec) {
+        using G = SbGeo<R>;
+        IMCL_TRY(encode_tmap_2d(&gmap, IMCL_F32, b.g, W, H, b.g_pitch_b, G::RW, G::RH));
+        IMCL_TRY(encode_tmap_2d(&xmap, IMCL_F32, f.in, W, H, f.in_pitch_b, G::RW, G::RH));
+    }
+    const int smem = a.vec ? sb_smem_bytes<R, true>() : sb_smem_bytes<R, false>();
+    auto kfn = a.vec ? k_sep_bwd_fused<R, true> : k_sep_bwd_fused<R, false>;
     IMCL_TRY(set_smem_limit((const void*)kfn, smem));
     const int occ = cached_occupancy((const void*)kfn, 256, smem);
     if (occ <= 0) return fail(IMCL_ERR_UNSUPPORTED, "fused separable backward cannot be resident");
@@ -292,7 +301,7 @@ static imcl_status sep_bwd_fused(const BwdArgs& b, float* ws, size_t ws_floats, 
     grid = std::max(1, std::min<int>(grid, (int)(ws_floats / (2 * NT))));   // partial sets that fit
     a.prow = ws;
     a.pcol = ws + (size_t)grid * NT;
-    kfn<<<grid, 256, smem, s>>>(a, tp);
+    kfn<<<grid, 256, smem, s>>>(a, tp, gmap, xmap, f.dev->status);
     IMCL_TRY(cuda_fail(cudaGetLastError(), "fused separable backward"));
     if (b.dw0) IMCL_TRY(finalize(a.prow, grid, NT, b.dw0, s));
     if (b.dw1) IMCL_TRY(finalize(a.pcol, grid, NT, b.dw1, s));

@@ -14,9 +14,12 @@
 //   dx   = the zero-border correlation of dt with the flipped row taps, plus the folds of
 //          clamped columns into columns 0 and W-1 (clamp rule);
 //   drow[i] += dt(s) x_b(sx + i - R, sy);   dcol[j] += g(p) t_b(px, py + j - R).
-// Every pass works on groups of 4 columns with 16-byte shared-memory loads.  The tap sums
-// stay in registers across a CTA's tiles and are reduced per CTA into partial sums, which
-// a second launch adds up in a fixed order.  g and x are read once (plus halos) and dx
+// Every pass works on groups of 4 columns with 16-byte shared-memory loads.  With f32
+// operands on 16-byte aligned rows (TMA = true) the staged regions arrive by 2D TMA into
+// a two-stage mbarrier ring, the next tile's while the current one computes; the
+// zero fill outside the image is g's border, and x's rule is patched in shared memory.
+// The tap sums stay in registers across a CTA's tiles and are reduced per CTA into
+// partial sums, which a second launch adds up in a fixed order.  g and x are read once (plus halos) and dx
 // written once: 12 bytes per pixel for f32 images.
 #pragma once
 
@@ -57,22 +60,35 @@ struct SbGeo {
     static constexpr int P = (R + 3) / 4 * 4;           // staged halo columns per side
     static constexpr int RW = TW + 2 * P, RH = TH + 2 * R;
     static constexpr int NV = (2 * P + 4) / 4;          // float4s covering [c, c + 2P + 4)
-    static constexpr int SMEM = 2 * RH * RW + TH * RW + RH * TW + 2 * NT;   // floats
+    static constexpr int PLANE_B = (RH * RW * 4 + 127) / 128 * 128;        // a staged plane, bytes
+    static constexpr int REST = TH * RW + RH * TW + 2 * NT;                 // dt, t, taps (floats)
 };
+
+// Dynamic shared memory of the kernel: barriers (128 bytes), then (TMA: two) stages of
+// g and x (each plane 128-byte aligned), then dt, t and the taps.
+template <int R, bool TMA>
+__host__ __device__ constexpr int sb_smem_bytes() {
+    return 128 + (TMA ? 2 : 1) * 2 * SbGeo<R>::PLANE_B + SbGeo<R>::REST * 4;
+}
 
 __device__ __forceinline__ void ld4(const float* p, float* v) {
     const float4 q = *reinterpret_cast<const float4*>(p);
     v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
 }
 
-template <int R>
-__global__ void __launch_bounds__(256, 3) k_sep_bwd_fused(const SbArgs a, const __grid_constant__ SbTaps<R> tp) {
+template <int R, bool TMA>
+__global__ void __launch_bounds__(256, 3)
+    k_sep_bwd_fused(const SbArgs a, const __grid_constant__ SbTaps<R> tp, const __grid_constant__ CUtensorMap gmap,
+                    const __grid_constant__ CUtensorMap xmap, int* status) {
     using G = SbGeo<R>;
     constexpr int NT = G::NT, TW = G::TW, TH = G::TH, P = G::P, RW = G::RW, RH = G::RH, NV = G::NV;
-    extern __shared__ __align__(16) float sbm[];
-    float* gs = sbm;                    // RH x RW: g, zero outside; column c is x0 - P + c
-    float* xs = gs + RH * RW;           // RH x RW: x under the forward's rule
-    float* dts = xs + RH * RW;          // TH x RW: dt, same columns
+    constexpr int NSTAGE = TMA ? 2 : 1;
+    constexpr int PB = G::PLANE_B;
+    extern __shared__ __align__(128) uint8_t sbraw[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sbraw);
+    uint8_t* stages = sbraw + 128;
+    // stage k: g at stages + 2 k PB (RH x RW, zero outside; column c is x0 - P + c), x at + PB
+    float* dts = reinterpret_cast<float*>(stages + NSTAGE * 2 * PB);   // TH x RW: dt, same columns
     float* ts = dts + TH * RW;          // RH x TW: t, tile columns, rows y0 - R ..
     float* wr = ts + RH * TW;
     float* wc = wr + NT;
@@ -87,12 +103,54 @@ __global__ void __launch_bounds__(256, 3) k_sep_bwd_fused(const SbArgs a, const 
 #pragma unroll
     for (int k = 0; k < NT; ++k) { accr[k] = 0.f; accc[k] = 0.f; }
 
+    int s = 0;
+    uint32_t parity = 0;
+    if constexpr (TMA) {
+        if (tid == 0) {
+            prefetch_tmap(&gmap);
+            prefetch_tmap(&xmap);
+            mbar_init(&bar[0], 1);
+            mbar_init(&bar[1], 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        const int t0 = blockIdx.x;
+        if (tid == 0 && t0 < a.ntiles) {
+            const int x0 = (t0 % a.tiles_x) * TW, y0 = (t0 / a.tiles_x) * TH;
+            mbar_arrive_expect_tx(&bar[0], (uint32_t)(2 * RH * RW * 4));
+            tma_load_2d(stages, &gmap, x0 - P, y0 - R, &bar[0]);
+            tma_load_2d(stages + PB, &xmap, x0 - P, y0 - R, &bar[0]);
+        }
+    }
+
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const int x0 = (t % a.tiles_x) * TW, y0 = (t / a.tiles_x) * TH;
         const int gx0 = x0 - P, gy0 = y0 - R;
+        float* gs = reinterpret_cast<float*>(stages + s * 2 * PB);
+        float* xs = reinterpret_cast<float*>(stages + s * 2 * PB + PB);
         __syncthreads();   // the previous tile's reads (and the taps) are done
         // ---- stage g and x over [gx0, gx0 + RW) x [gy0, gy0 + RH)
-        if (a.vec && gx0 >= 0 && gy0 >= 0 && gx0 + RW <= W && gy0 + RH <= H) {
+        if constexpr (TMA) {
+            const int tn = t + gridDim.x;
+            const bool prefetch = tn < a.ntiles;
+            if (tid == 0 && prefetch) {
+                const int nx0 = (tn % a.tiles_x) * TW, ny0 = (tn / a.tiles_x) * TH;
+                uint8_t* ng = stages + (s ^ 1) * 2 * PB;
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&bar[s ^ 1], (uint32_t)(2 * RH * RW * 4));
+                tma_load_2d(ng, &gmap, nx0 - P, ny0 - R, &bar[s ^ 1]);
+                tma_load_2d(ng + PB, &xmap, nx0 - P, ny0 - R, &bar[s ^ 1]);
+            }
+            const bool ok = mbar_wait(&bar[s], (parity >> s) & 1u, status);
+            parity ^= (1u << s);
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0 && prefetch) mbar_wait(&bar[s ^ 1], (parity >> (s ^ 1)) & 1u, nullptr);
+                return;
+            }
+            // g: the TMA zero fill is its border; x: the forward's rule
+            if (!tile_inside(gx0, gy0, RW, RH, W, H))
+                patch_tile<float>(xs, RW, RH, gx0, gy0, W, H, a.border, a.bvx, tid, 256);
+        } else if (a.vec && gx0 >= 0 && gy0 >= 0 && gx0 + RW <= W && gy0 + RH <= H) {
             const float* xf = static_cast<const float*>(a.x);
             for (int i = tid; i < RH * (RW / 4); i += 256) {
                 const int r = i / (RW / 4), c = (i - r * (RW / 4)) * 4;
@@ -115,7 +173,7 @@ __global__ void __launch_bounds__(256, 3) k_sep_bwd_fused(const SbArgs a, const 
                 xs[i] = xv;
             }
         }
-        __syncthreads();
+        if constexpr (!TMA) __syncthreads();
         // ---- dt on the tile rows, all staged columns, 4 at a time
         for (int i = tid; i < TH * (RW / 4); i += 256) {
             const int r = i / (RW / 4), c = (i - r * (RW / 4)) * 4;
@@ -223,11 +281,12 @@ __global__ void __launch_bounds__(256, 3) k_sep_bwd_fused(const SbArgs a, const 
                 }
             }
         }
+        if constexpr (TMA) s ^= 1;
     }
 
     // CTA sums of the tap gradients: warps, then the 8 warp sums in a fixed order
     __syncthreads();
-    float* red = sbm;   // 8 warps x 2 NT (the staging buffers are free now)
+    float* red = reinterpret_cast<float*>(stages);   // 8 warps x 2 NT (the staging buffers are free now)
     const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int k = 0; k < NT; ++k) {
