@@ -12,6 +12,7 @@
 // reductions), all recorded in one CUDA graph.
 #pragma once
 
+#include "bulk_copy.cuh"
 #include "tile_common.cuh"
 #include "wgrad_tile.cuh"
 
