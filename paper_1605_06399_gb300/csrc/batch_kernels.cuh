@@ -947,27 +947,41 @@ __device__ void batch_sep_dt_tile(const BImg& im, int x0, int y0, int TW, int TH
     const float* cw = w + 16;
     // dt for the tile's pixels
     if (im.dt) {
-        for (int k = tid; k < TW * TH; k += nth) {
-            const int py = k / TW, px = k % TW;
+        // 4 pixels of a row per item: one 16-byte load of g per column tap
+        const int ng = TW / 4;
+        for (int k = tid; k < ng * TH; k += nth) {
+            const int py = k / ng, px = (k - py * ng) * 4;
             const int gx = x0 + px, gy = y0 + py;
             if (gx >= im.W || gy >= im.H) continue;
-            float acc = 0.f;
-            for (int j = 0; j < nc; ++j) acc = __fmaf_rn(cw[j], gs[(py + R + rc - j) * TW + px], acc);
-            if (im.border == IMCL_BORDER_CLAMP) {
-                if (gy == 0)
-                    for (int e = -rc; e <= -1; ++e)
-                        for (int j = 0; j < nc; ++j) {
-                            const int sy = e - j + rc;   // image row, < rc
-                            if (sy >= 0 && sy < im.H) acc = __fmaf_rn(cw[j], gs[(sy - y0 + R) * TW + px], acc);
-                        }
-                if (gy == im.H - 1)
-                    for (int e = im.H; e <= im.H - 1 + rc; ++e)
-                        for (int j = 0; j < nc; ++j) {
-                            const int sy = e - j + rc;
-                            if (sy >= 0 && sy < im.H) acc = __fmaf_rn(cw[j], gs[(sy - y0 + R) * TW + px], acc);
-                        }
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int j = 0; j < nc; ++j) {
+                const float4 s4 = *reinterpret_cast<const float4*>(gs + (py + R + rc - j) * TW + px);
+                acc[0] = __fmaf_rn(cw[j], s4.x, acc[0]);
+                acc[1] = __fmaf_rn(cw[j], s4.y, acc[1]);
+                acc[2] = __fmaf_rn(cw[j], s4.z, acc[2]);
+                acc[3] = __fmaf_rn(cw[j], s4.w, acc[3]);
             }
-            im.dt[(long long)gy * im.dt_pitch + gx] = acc;
+            if (im.border == IMCL_BORDER_CLAMP && (gy == 0 || gy == im.H - 1)) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (gy == 0)
+                        for (int e = -rc; e <= -1; ++e)
+                            for (int j = 0; j < nc; ++j) {
+                                const int sy = e - j + rc;   // image row, < rc
+                                if (sy >= 0 && sy < im.H) acc[q] = __fmaf_rn(cw[j], gs[(sy - y0 + R) * TW + px + q], acc[q]);
+                            }
+                    if (gy == im.H - 1)
+                        for (int e = im.H; e <= im.H - 1 + rc; ++e)
+                            for (int j = 0; j < nc; ++j) {
+                                const int sy = e - j + rc;
+                                if (sy >= 0 && sy < im.H) acc[q] = __fmaf_rn(cw[j], gs[(sy - y0 + R) * TW + px + q], acc[q]);
+                            }
+                }
+            }
+            float* o = im.dt + (long long)gy * im.dt_pitch + gx;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (gx + q < im.W) o[q] = acc[q];
         }
     }
     if (im.gtaps2) {
@@ -1019,9 +1033,60 @@ __device__ void batch_row_wgrad(const float* ds, const float* xs, int XW, int TW
 
 // separable, second backward pass: dx = R^T dt on the tile (with the clamp folds on the
 // first and last columns) and the row-tap partials drow[i] = sum_p dt(p) x(p + (i - rr, 0)).
+// dx = R^T dt on a separable tile, 4 pixels per item: one 20-float segment of dt (staged at
+// columns PADR = 8 ..) serves the NR taps of all 4; the clamp folds of columns 0 and W-1
+// are added after, as in the per-pixel form (same order of operations).
+template <int NR>
+__device__ __forceinline__ void batch_sep_dx_compute(const BImg& im, const float* ds, int XW, int x0, int y0, int TW,
+                                                     int TH, const float* w, int tid, int nth) {
+    constexpr int RR = (NR - 1) / 2, PADR = 8;
+    float wr[NR];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) wr[i] = w[i];
+    const int ng = TW / 4;
+    for (int k = tid; k < ng * TH; k += nth) {
+        const int py = k / ng, px = (k - py * ng) * 4;
+        const int gx = x0 + px, gy = y0 + py;
+        if (gx >= im.W || gy >= im.H) continue;
+        float seg[20];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const float4 s4 = *reinterpret_cast<const float4*>(ds + py * XW + px + 4 * q);
+            seg[4 * q] = s4.x; seg[4 * q + 1] = s4.y; seg[4 * q + 2] = s4.z; seg[4 * q + 3] = s4.w;
+        }
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < NR; ++i)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = __fmaf_rn(wr[i], seg[PADR + RR - i + q], acc[q]);
+        if (im.border == IMCL_BORDER_CLAMP && (gx == 0 || gx + 3 >= im.W - 1)) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int qx = gx + q;
+                if (qx == 0)
+                    for (int e = -RR; e <= -1; ++e)
+                        for (int i = 0; i < NR; ++i) {
+                            const int sx = e - i + RR;
+                            if (sx >= 0 && sx < im.W) acc[q] = __fmaf_rn(wr[i], ds[py * XW + sx - x0 + PADR], acc[q]);
+                        }
+                if (qx == im.W - 1)
+                    for (int e = im.W; e <= im.W - 1 + RR; ++e)
+                        for (int i = 0; i < NR; ++i) {
+                            const int sx = e - i + RR;
+                            if (sx >= 0 && sx < im.W) acc[q] = __fmaf_rn(wr[i], ds[py * XW + sx - x0 + PADR], acc[q]);
+                        }
+            }
+        }
+        float* o = im.gin + (long long)gy * im.gin_pitch + gx;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (gx + q < im.W) o[q] = acc[q];
+    }
+}
+
 __device__ void batch_sep_dx_tile(const BImg& im, int x0, int y0, int TW, int TH, float* sm, int tid, int nth) {
     constexpr int PADR = 8;
-    const int nr = im.kw, rr = (nr - 1) / 2;
+    const int nr = im.kw;
     const int XW = TW + 2 * PADR;
     float* ds = sm;                                     // XW x TH, columns x0 - PADR ..
     float* xs = ds + XW * TH;                           // XW x TH
@@ -1034,27 +1099,15 @@ __device__ void batch_sep_dx_tile(const BImg& im, int x0, int y0, int TW, int TH
                  im.in_vec);
     __syncthreads();
     if (im.gin) {
-        for (int k = tid; k < TW * TH; k += nth) {
-            const int py = k / TW, px = k % TW;
-            const int gx = x0 + px, gy = y0 + py;
-            if (gx >= im.W || gy >= im.H) continue;
-            float acc = 0.f;
-            for (int i = 0; i < nr; ++i) acc = __fmaf_rn(w[i], ds[py * XW + px + PADR + rr - i], acc);
-            if (im.border == IMCL_BORDER_CLAMP) {
-                if (gx == 0)
-                    for (int e = -rr; e <= -1; ++e)
-                        for (int i = 0; i < nr; ++i) {
-                            const int sx = e - i + rr;
-                            if (sx >= 0 && sx < im.W) acc = __fmaf_rn(w[i], ds[py * XW + sx - x0 + PADR], acc);
-                        }
-                if (gx == im.W - 1)
-                    for (int e = im.W; e <= im.W - 1 + rr; ++e)
-                        for (int i = 0; i < nr; ++i) {
-                            const int sx = e - i + rr;
-                            if (sx >= 0 && sx < im.W) acc = __fmaf_rn(w[i], ds[py * XW + sx - x0 + PADR], acc);
-                        }
-            }
-            im.gin[(long long)gy * im.gin_pitch + gx] = acc;
+        switch (nr) {
+            case 1: batch_sep_dx_compute<1>(im, ds, XW, x0, y0, TW, TH, w, tid, nth); break;
+            case 3: batch_sep_dx_compute<3>(im, ds, XW, x0, y0, TW, TH, w, tid, nth); break;
+            case 5: batch_sep_dx_compute<5>(im, ds, XW, x0, y0, TW, TH, w, tid, nth); break;
+            case 7: batch_sep_dx_compute<7>(im, ds, XW, x0, y0, TW, TH, w, tid, nth); break;
+            case 9: batch_sep_dx_compute<9>(im, ds, XW, x0, y0, TW, TH, w, tid, nth); break;
+            case 11: batch_sep_dx_compute<11>(im, ds, XW, x0, y0, TW, TH, w, tid, nth); break;
+            case 13: batch_sep_dx_compute<13>(im, ds, XW, x0, y0, TW, TH, w, tid, nth); break;
+            default: batch_sep_dx_compute<15>(im, ds, XW, x0, y0, TW, TH, w, tid, nth); break;
         }
     }
     if (im.gtaps) {
