@@ -929,13 +929,49 @@ __device__ void batch_conv_edges(const BImg& im, int chunk, int tid, int nth) {
     }
 }
 
+// The forward row pass t = R x on HH staged rows (x at columns PADR = 8 .. of xs, rows
+// XW wide; image row gy0 + r) into ts (TW wide), 4 pixels per item from one 20-float
+// segment; the constant rule gives t the constant on rows outside the image.
+template <int NR>
+__device__ __forceinline__ void batch_sep_rows_t(const BImg& im, const float* xs, int XW, float* ts, int TW, int HH,
+                                                 int gy0, const float* w, int tid, int nth) {
+    constexpr int RR = (NR - 1) / 2, PADR = 8;
+    float wr[NR];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) wr[i] = w[i];
+    const int ng = TW / 4;
+    for (int k = tid; k < ng * HH; k += nth) {
+        const int r = k / ng, px = (k - r * ng) * 4;
+        const int gy = gy0 + r;
+        float acc[4];
+        if (im.border == IMCL_BORDER_CONSTANT && (gy < 0 || gy >= im.H)) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = im.bv;
+        } else {
+            float seg[20];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                const float4 s4 = *reinterpret_cast<const float4*>(xs + r * XW + px + 4 * q);
+                seg[4 * q] = s4.x; seg[4 * q + 1] = s4.y; seg[4 * q + 2] = s4.z; seg[4 * q + 3] = s4.w;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = 0.f;
+#pragma unroll
+            for (int i = 0; i < NR; ++i)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[q] = __fmaf_rn(wr[i], seg[PADR - RR + i + q], acc[q]);
+        }
+        *reinterpret_cast<float4*>(ts + r * TW + px) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    }
+}
+
 // separable, first backward pass: dt = C^T g on the tile (with the clamp folds on the
 // first and last rows) into the plan's dt plane, and the column-tap partial sums
 // dcol[j] = sum_p g(p) t(p + (0, j - rc)), t the forward row pass.
 template <int R>
 __device__ void batch_sep_dt_tile(const BImg& im, int x0, int y0, int TW, int TH, float* sm, int tid, int nth) {
     constexpr int PADR = 8;                             // >= R, 16 bytes of f32
-    const int nr = im.kw, nc = im.kh, rr = (nr - 1) / 2, rc = (nc - 1) / 2;
+    const int nr = im.kw, nc = im.kh, rc = (nc - 1) / 2;
     const int XW = TW + 2 * PADR, HH = TH + 2 * R;      // R >= rc rows of halo
     float* gs = sm;                                     // TW x HH, rows y0 - R ..
     float* w = gs + TW * HH;                            // row taps [0, 16), column taps [16, 32)
@@ -991,16 +1027,15 @@ __device__ void batch_sep_dt_tile(const BImg& im, int x0, int y0, int TW, int TH
         stage_region(xs, XW, HH, im.in, im.in_dt, im.in_pitch, x0 - PADR, y0 - R, im.W, im.H, im.border, im.bv, 0,
                      tid, nth, im.in_vec);
         __syncthreads();
-        for (int k = tid; k < TW * HH; k += nth) {
-            const int r = k / TW, px = k % TW;
-            const int gy = y0 - R + r;
-            float acc = 0.f;
-            if (im.border == IMCL_BORDER_CONSTANT && (gy < 0 || gy >= im.H)) {
-                acc = im.bv;
-            } else {
-                for (int i = 0; i < nr; ++i) acc = __fmaf_rn(w[i], xs[r * XW + px + PADR - rr + i], acc);
-            }
-            ts[k] = acc;
+        switch (nr) {
+            case 1: batch_sep_rows_t<1>(im, xs, XW, ts, TW, HH, y0 - R, w, tid, nth); break;
+            case 3: batch_sep_rows_t<3>(im, xs, XW, ts, TW, HH, y0 - R, w, tid, nth); break;
+            case 5: batch_sep_rows_t<5>(im, xs, XW, ts, TW, HH, y0 - R, w, tid, nth); break;
+            case 7: batch_sep_rows_t<7>(im, xs, XW, ts, TW, HH, y0 - R, w, tid, nth); break;
+            case 9: batch_sep_rows_t<9>(im, xs, XW, ts, TW, HH, y0 - R, w, tid, nth); break;
+            case 11: batch_sep_rows_t<11>(im, xs, XW, ts, TW, HH, y0 - R, w, tid, nth); break;
+            case 13: batch_sep_rows_t<13>(im, xs, XW, ts, TW, HH, y0 - R, w, tid, nth); break;
+            default: batch_sep_rows_t<15>(im, xs, XW, ts, TW, HH, y0 - R, w, tid, nth); break;
         }
         __syncthreads();
         const int tile = (y0 / TH) * im.tiles_x + x0 / TW;
