@@ -3,13 +3,15 @@
 // one persistent launch.
 //
 // The host sorts every tile of every image into one work list (costliest first) and the
-// CTAs of a persistent grid take tiles from it with an atomic counter (no waits, so no
-// CTA can block another).  Each tile is staged into shared memory as f32 (converting the
-// image's storage type, applying its boundary rule), then the specialised device code
-// for its operator and filter side runs: the same register-blocked conv2d and fused
-// row+column separable computation as the single-image kernels.  The backward runs as
-// a few such persistent phases (input-gradient tiles, separable second pass, tap-gradient
-// reductions), all recorded in one CUDA graph.
+// CTAs of a persistent grid take tiles from it with an atomic counter (no CTA waits on
+// another).  In the forward a producer warp per CTA takes the tiles two ahead and brings
+// each tile's image rows into shared memory with bulk asynchronous copies, while the
+// consumer warps convert the previous tile to f32 (the image's storage type, its boundary
+// rule) and run the specialised device code for its operator and filter side: register-
+// blocked conv2d rows and the fused row+column separable computation.  The backward runs
+// as a few persistent phases of 256-thread CTAs that stage their own tiles
+// (input-gradient tiles, separable second pass, tap-gradient reductions), all recorded
+// in one CUDA graph.
 #pragma once
 
 #include "bulk_copy.cuh"
