@@ -13,8 +13,18 @@
 namespace imcl {
 
 // Tile shapes the plan chooses from: (PY, bx, by) with PX = 4 -> tile (4 bx) x (PY by).
-static const int kShapes[][3] = {{4, 32, 8}, {4, 16, 16}, {2, 32, 8}, {2, 16, 16}};
+constexpr int kShapes[][3] = {{4, 32, 8}, {4, 16, 16}, {2, 32, 8}, {2, 16, 16}};
 constexpr int kNumShapes = 4;
+// The forward kernel's conversion is compiled for tile widths 64 and 128, and its compute
+// maps exactly bx * by = 256 consumer threads onto a tile.
+constexpr bool shapes_supported() {
+    for (int c = 0; c < kNumShapes; ++c) {
+        const int tw = 4 * kShapes[c][1];
+        if ((tw != 64 && tw != 128) || kShapes[c][1] * kShapes[c][2] != kFwdConsumers) return false;
+    }
+    return true;
+}
+static_assert(shapes_supported(), "batch tile shapes outside what the forward kernel is compiled for");
 
 // Byte alignment every row start of an image shares (16, 4, or 0 for less).
 static int row_alignment(const void* base, int64_t pitch_bytes) {
