@@ -286,9 +286,9 @@ void imagecl_batch_destroy(imcl_batch *batch);
  * imagecl_sepconv_noalloc -- the separable correlation for callers that may not
  * allocate device memory.  The paper has no counterpart; this entry point exists for
  * deployment.  Some callers cannot call cudaMalloc (or anything that allocates) while
- * they run: code recording a stream into a CUDA graph, plugins whose host framework
- * owns all device memory through its own allocator, loops that cannot take the
- * synchronisation an allocation may cause.  They still pass their own input and output
+ * they run: plugins whose host framework owns all device memory through its own
+ * allocator, and real-time loops that cannot take the device-wide synchronisation an
+ * allocation or a free may cause.  They still pass their own input and output
  * images; the one intermediate this operation needs (the f32 row pass) lives in a
  * fixed array of IMAGECL_NOALLOC_SCRATCH_BYTES that the library declares in device
  * memory.  Every GPU that loads the library holds that array until the process exits.
@@ -377,6 +377,18 @@ imcl_status imagecl_tune_load(const char *path);
  * independent FMA chains (packed = 0: scalar FMAs; 1: packed f32x2 FMAs).  A measurement
  * helper for the ALU roofline of the stencils, not an operator; synchronises `stream`. */
 imcl_status imagecl_probe_fp32(int32_t packed, double *tflops, void *stream);
+
+/* Integer multiply-add throughput of the current device in tera-operations per second
+ * (2 per wrapping int32 multiply-add), measured with independent chains: the ALU
+ * roofline of the integer (u8 -> i32) correlation.  Synchronises `stream`. */
+imcl_status imagecl_probe_imad(double *tops, void *stream);
+
+/* Failure-path self-test.  Launches one thread that arms an mbarrier for a transfer that
+ * never comes, waits at most `rounds` (1 .. 2^20) try_wait rounds, gives up and records
+ * code 1 (a bounded wait timed out) in the device status word, as every stencil kernel
+ * does when its own wait runs out.  No fault and no hang: the context stays usable, and
+ * imagecl_device_status() then reports 1 (and clears it).  Asynchronous on `stream`. */
+imcl_status imagecl_selftest_wait_timeout(int32_t rounds, void *stream);
 
 /* ------------------------------------------------------------------ status */
 

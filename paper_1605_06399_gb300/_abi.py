@@ -135,6 +135,8 @@ SIGNATURES = {
     "imagecl_tune_save": (c_int32, [ctypes.c_char_p]),
     "imagecl_tune_load": (c_int32, [ctypes.c_char_p]),
     "imagecl_probe_fp32": (c_int32, [c_int32, P(c_double), c_void_p]),
+    "imagecl_probe_imad": (c_int32, [P(c_double), c_void_p]),
+    "imagecl_selftest_wait_timeout": (c_int32, [c_int32, c_void_p]),
     "imagecl_last_error": (ctypes.c_char_p, []),
     "imagecl_device_status": (c_int32, [P(c_int32), c_void_p]),
     "imagecl_version": (ctypes.c_char_p, []),

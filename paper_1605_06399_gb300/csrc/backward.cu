@@ -431,7 +431,7 @@ imcl_status harris_backward_run(const BwdArgs& b, cudaStream_t s) {
     const float* sy = static_cast<const float*>(f.taps2);
     const float* gw = static_cast<const float*>(f.taps3);
     const int grid = wgrad_launch_grid(W, H, f.dev, wk), grid_s = wgrad_launch_grid(W, H, f.dev, 3);
-    dim3 eg((W + 255) / 256, H);
+    const dim3 eg = grid_2d(W, H, 256, 1);
     // an even window runs as the next odd one with a zero last row and column; its
     // gradient is the top-left src x src block of that window's gradient
     std::vector<float> gw_host;

@@ -375,44 +375,52 @@ __global__ void k_flip_taps(const float* src, int kw, int kh, float* dst, float*
 // products of the gradients: P = (Ix^2, Iy^2, Ix Iy), planes of pitch `pitch`
 __global__ void k_harris_products(const float* ix, const float* iy, float* p0, float* p1, float* p2, long long pitch,
                                   int W, int H) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x >= W || y >= H) return;
-    const long long o = (long long)y * pitch + x;
-    const float a = ix[o], b = iy[o];
-    p0[o] = a * a;
-    p1[o] = b * b;
-    p2[o] = a * b;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= W) return;
+    for (int y = blockIdx.y; y < H; y += gridDim.y) {
+        const long long o = (long long)y * pitch + x;
+        const float a = ix[o], b = iy[o];
+        p0[o] = a * a;
+        p1[o] = b * b;
+        p2[o] = a * b;
+    }
 }
 
 // dR/dS: gSxx = gR (Syy - 2k tr), gSyy = gR (Sxx - 2k tr), gSxy = -2 gR Sxy (in place)
 __global__ void k_harris_gs(const float* gR, long long gR_pitch, float* s0, float* s1, float* s2, long long pitch,
                             int W, int H, float k) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x >= W || y >= H) return;
-    const long long o = (long long)y * pitch + x;
-    const float g = gR[(long long)y * gR_pitch + x];
-    const float sxx = s0[o], syy = s1[o], sxy = s2[o], tr = sxx + syy;
-    s0[o] = g * (syy - 2.f * k * tr);
-    s1[o] = g * (sxx - 2.f * k * tr);
-    s2[o] = -2.f * g * sxy;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= W) return;
+    for (int y = blockIdx.y; y < H; y += gridDim.y) {
+        const long long o = (long long)y * pitch + x;
+        const float g = gR[(long long)y * gR_pitch + x];
+        const float sxx = s0[o], syy = s1[o], sxy = s2[o], tr = sxx + syy;
+        s0[o] = g * (syy - 2.f * k * tr);
+        s1[o] = g * (sxx - 2.f * k * tr);
+        s2[o] = -2.f * g * sxy;
+    }
 }
 
 // chain rule through the products: gIx = 2 Ix gPxx + Iy gPxy, gIy = 2 Iy gPyy + Ix gPxy
 __global__ void k_harris_gi(const float* ix, const float* iy, const float* gp0, const float* gp1, const float* gp2,
                             float* gix, float* giy, long long pitch, int W, int H) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x >= W || y >= H) return;
-    const long long o = (long long)y * pitch + x;
-    const float a = ix[o], b = iy[o], pxx = gp0[o], pyy = gp1[o], pxy = gp2[o];
-    gix[o] = __fmaf_rn(2.f * a, pxx, b * pxy);
-    giy[o] = __fmaf_rn(2.f * b, pyy, a * pxy);
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= W) return;
+    for (int y = blockIdx.y; y < H; y += gridDim.y) {
+        const long long o = (long long)y * pitch + x;
+        const float a = ix[o], b = iy[o], pxx = gp0[o], pyy = gp1[o], pxy = gp2[o];
+        gix[o] = __fmaf_rn(2.f * a, pxx, b * pxy);
+        giy[o] = __fmaf_rn(2.f * b, pyy, a * pxy);
+    }
 }
 
 // dst += src (planes)
 __global__ void k_add_plane(float* dst, long long dst_pitch, const float* src, long long src_pitch, int W, int H) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x >= W || y >= H) return;
-    dst[(long long)y * dst_pitch + x] += src[(long long)y * src_pitch + x];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= W) return;
+    for (int y = blockIdx.y; y < H; y += gridDim.y) {
+        dst[(long long)y * dst_pitch + x] += src[(long long)y * src_pitch + x];
+    }
 }
 
 }  // namespace imcl

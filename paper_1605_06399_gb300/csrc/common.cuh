@@ -284,4 +284,13 @@ __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
 
 __host__ __device__ constexpr int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
+// A grid is at most 65535 blocks high.  One-pixel-per-thread kernels over W x H images
+// launch grid_2d(...) and walk their rows with a stride of gridDim.y * blockDim.y, so
+// every height runs.
+constexpr int kMaxGridY = 65535;
+inline dim3 grid_2d(int W, int H, int bx, int by) {
+    const int gy = (H + by - 1) / by;
+    return dim3((unsigned)((W + bx - 1) / bx), (unsigned)(gy < kMaxGridY ? gy : kMaxGridY));
+}
+
 }  // namespace imcl

@@ -35,31 +35,32 @@ __global__ void __launch_bounds__(256)
     k_conv2d_plain(const ConvArgs a, const __grid_constant__ TapsParam<typename AccOf<Tin>::type, kMaxK * kMaxK> tp) {
     using Acc = typename AccOf<Tin>::type;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= a.W || y >= a.H) return;
+    if (x >= a.W) return;
     const Tin* in = static_cast<const Tin*>(a.in);
     const Acc* taps = DEV_TAPS ? static_cast<const Acc*>(a.taps_dev) : tp.w;
     const int rx = (a.kw - 1) / 2, ry = (a.kh - 1) / 2;
     const Acc bv = to_acc(border_pixel<Tin>(a));
-    Acc acc = 0;
+    for (int y = blockIdx.y * blockDim.y + threadIdx.y; y < a.H; y += gridDim.y * blockDim.y) {
+        Acc acc = 0;
 #pragma unroll 1
-    for (int j = 0; j < a.kh; ++j) {
-        const int gy = y + j - ry;
+        for (int j = 0; j < a.kh; ++j) {
+            const int gy = y + j - ry;
 #pragma unroll 1
-        for (int i = 0; i < a.kw; ++i) {
-            const int gx = x + i - rx;
-            Acc v;
-            if (gx >= 0 && gx < a.W && gy >= 0 && gy < a.H) {
-                v = to_acc(in[(long long)gy * a.in_pitch + gx]);
-            } else if (a.border == IMCL_BORDER_CONSTANT) {
-                v = bv;
-            } else {
-                v = to_acc(in[(long long)clampi(gy, 0, a.H - 1) * a.in_pitch + clampi(gx, 0, a.W - 1)]);
+            for (int i = 0; i < a.kw; ++i) {
+                const int gx = x + i - rx;
+                Acc v;
+                if (gx >= 0 && gx < a.W && gy >= 0 && gy < a.H) {
+                    v = to_acc(in[(long long)gy * a.in_pitch + gx]);
+                } else if (a.border == IMCL_BORDER_CONSTANT) {
+                    v = bv;
+                } else {
+                    v = to_acc(in[(long long)clampi(gy, 0, a.H - 1) * a.in_pitch + clampi(gx, 0, a.W - 1)]);
+                }
+                acc = mad(taps[j * a.kw + i], v, acc);
             }
-            acc = mad(taps[j * a.kw + i], v, acc);
         }
+        static_cast<Tout*>(a.out)[(long long)y * a.out_pitch + x] = Store<Tout, Acc>::cvt(acc);
     }
-    static_cast<Tout*>(a.out)[(long long)y * a.out_pitch + x] = Store<Tout, Acc>::cvt(acc);
 }
 
 // ------------------------------------------------------------------ tiled kernel
@@ -223,7 +224,7 @@ imcl_status launch_conv_plain(const ConvCall& c, const imcl_variant& v, cudaStre
     ConvArgs a = make_conv_args(c, v, 1, 1);
     TapsParam<Acc, kMaxK * kMaxK> tp;
     fill_taps(tp, c);
-    dim3 grid((c.W + bx - 1) / bx, (c.H + by - 1) / by), block(bx, by);
+    dim3 grid = grid_2d(c.W, c.H, bx, by), block(bx, by);
     if (c.taps_mem == IMCL_MEM_DEVICE)
         k_conv2d_plain<Tin, Tout, true><<<grid, block, 0, s>>>(a, tp);
     else

@@ -13,7 +13,7 @@ imcl_status launch_harris_plain(const ConvCall& c, const imcl_variant& v, cudaSt
     ConvArgs a = make_conv_args(c, v, 1, 1);
     HarrisTaps<7> tp;
     fill_harris_taps(tp, c);
-    dim3 grid((c.W + bx - 1) / bx, (c.H + by - 1) / by), block(bx, by);
+    dim3 grid = grid_2d(c.W, c.H, bx, by), block(bx, by);
     k_harris_sobel_plain<<<grid, block, 0, s>>>(a, tp);
     k_harris_resp_plain<<<grid, block, 0, s>>>(a, tp);
     return cuda_fail(cudaGetLastError(), "harris plain launch");

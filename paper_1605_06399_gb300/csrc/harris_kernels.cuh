@@ -46,54 +46,56 @@ struct HarrisTaps {
 __global__ void __launch_bounds__(256)
     k_harris_sobel_plain(const ConvArgs a, const __grid_constant__ HarrisTaps<7> tp) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= a.W || y >= a.H) return;
+    if (x >= a.W) return;
     const float* in = static_cast<const float*>(a.in);
     const float* sx = a.taps_dev ? static_cast<const float*>(a.taps_dev) : tp.sx;
     const float* sy = a.taps2_dev ? static_cast<const float*>(a.taps2_dev) : tp.sy;
-    float gx = 0.f, gy = 0.f;
+    for (int y = blockIdx.y * blockDim.y + threadIdx.y; y < a.H; y += gridDim.y * blockDim.y) {
+        float gx = 0.f, gy = 0.f;
 #pragma unroll 1
-    for (int j = 0; j < 3; ++j) {
-        const int yy = clampi(y + j - 1, 0, a.H - 1);
+        for (int j = 0; j < 3; ++j) {
+            const int yy = clampi(y + j - 1, 0, a.H - 1);
 #pragma unroll 1
-        for (int i = 0; i < 3; ++i) {
-            const float v = in[(long long)yy * a.in_pitch + clampi(x + i - 1, 0, a.W - 1)];
-            gx = __fmaf_rn(sx[j * 3 + i], v, gx);
-            gy = __fmaf_rn(sy[j * 3 + i], v, gy);
+            for (int i = 0; i < 3; ++i) {
+                const float v = in[(long long)yy * a.in_pitch + clampi(x + i - 1, 0, a.W - 1)];
+                gx = __fmaf_rn(sx[j * 3 + i], v, gx);
+                gy = __fmaf_rn(sy[j * 3 + i], v, gy);
+            }
         }
+        float* ix = static_cast<float*>(a.work);
+        ix[(long long)y * a.W + x] = gx;
+        ix[(long long)a.W * a.H + (long long)y * a.W + x] = gy;
     }
-    float* ix = static_cast<float*>(a.work);
-    ix[(long long)y * a.W + x] = gx;
-    ix[(long long)a.W * a.H + (long long)y * a.W + x] = gy;
 }
 
 __global__ void __launch_bounds__(256)
     k_harris_resp_plain(const ConvArgs a, const __grid_constant__ HarrisTaps<7> tp) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= a.W || y >= a.H) return;
+    if (x >= a.W) return;
     const float* ix = static_cast<const float*>(a.work);
     const float* iy = ix + (long long)a.W * a.H;
     // a.kw: the (odd) side run; a.kh: the caller's side, the stride of device taps (an
     // even window runs with a zero last row and column)
     const float* gd = static_cast<const float*>(a.taps3_dev);
     const int wk = a.kw, rw = (wk - 1) / 2, src = a.kh;
-    float sxx = 0.f, syy = 0.f, sxy = 0.f;
+    for (int y = blockIdx.y * blockDim.y + threadIdx.y; y < a.H; y += gridDim.y * blockDim.y) {
+        float sxx = 0.f, syy = 0.f, sxy = 0.f;
 #pragma unroll 1
-    for (int j = 0; j < wk; ++j) {
-        const int yy = clampi(y + j - rw, 0, a.H - 1);
+        for (int j = 0; j < wk; ++j) {
+            const int yy = clampi(y + j - rw, 0, a.H - 1);
 #pragma unroll 1
-        for (int i = 0; i < wk; ++i) {
-            const long long o = (long long)yy * a.W + clampi(x + i - rw, 0, a.W - 1);
-            const float w = gd ? ((j < src && i < src) ? gd[j * src + i] : 0.f) : tp.g[j * wk + i];
-            const float gx = ix[o], gy = iy[o];
-            sxx = __fmaf_rn(w, gx * gx, sxx);
-            syy = __fmaf_rn(w, gy * gy, syy);
-            sxy = __fmaf_rn(w, gx * gy, sxy);
+            for (int i = 0; i < wk; ++i) {
+                const long long o = (long long)yy * a.W + clampi(x + i - rw, 0, a.W - 1);
+                const float w = gd ? ((j < src && i < src) ? gd[j * src + i] : 0.f) : tp.g[j * wk + i];
+                const float gx = ix[o], gy = iy[o];
+                sxx = __fmaf_rn(w, gx * gx, sxx);
+                syy = __fmaf_rn(w, gy * gy, syy);
+                sxy = __fmaf_rn(w, gx * gy, sxy);
+            }
         }
+        const float tr = sxx + syy;
+        static_cast<float*>(a.out)[(long long)y * a.out_pitch + x] = sxx * syy - sxy * sxy - a.hk * tr * tr;
     }
-    const float tr = sxx + syy;
-    static_cast<float*>(a.out)[(long long)y * a.out_pitch + x] = sxx * syy - sxy * sxy - a.hk * tr * tr;
 }
 
 // ------------------------------------------------------------------ fused

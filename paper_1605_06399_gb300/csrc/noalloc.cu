@@ -1,13 +1,15 @@
 // noalloc.cu -- imagecl_sepconv_noalloc: the two-pass separable correlation with its
 // intermediate in a fixed, library-owned device array instead of caller memory.
 //
-// Who this is for: code that must not call cudaMalloc or any other allocating routine
-// while it runs.  Examples are a stream that is being captured into a CUDA graph (an
-// allocation there either breaks the capture or forces a device-wide sync), plugins that
-// live inside a host framework which owns every byte of device memory through its own
-// allocator and forbids raw allocations, and latency-critical loops that cannot afford
-// the implicit synchronisation an allocation can bring.  Those callers still own their
-// input and output images; only the row-pass intermediate moves into the array below.
+// Who this is for: callers that must not call cudaMalloc or any other allocating routine
+// while they run.  A plugin inside a host framework that owns every byte of device
+// memory through its own allocator is not allowed raw allocations, and a real-time
+// processing loop cannot take the device-wide synchronisation that cudaMalloc and
+// cudaFree may bring.  Those callers still own their input and output images; only the
+// row-pass intermediate moves into the array below.
+//
+// The kernels walk the image's rows with a grid-stride loop, so any height whose
+// width * height fits the array runs (a grid is at most 65535 blocks high).
 //
 // The array is a file-scope __device__ variable, so every GPU that loads this library
 // holds kNoallocScratchBytes for it until the process exits.  Host code cannot take its
@@ -118,7 +120,7 @@ extern "C" imcl_status imagecl_sepconv_noalloc(const imcl_image* in, const imcl_
     }
     // The row pass writes every pixel of the intermediate before the column pass reads
     // it, so nothing left in the array by an earlier call can leak into this result.
-    dim3 block(16, 16), grid((c.W + 15) / 16, (c.H + 15) / 16);
+    dim3 block(16, 16), grid = grid_2d(c.W, c.H, 16, 16);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     switch (in->dtype * 8 + out->dtype) {
         case IMCL_F32 * 8 + IMCL_F32: noalloc_launch<float, float>(a, tp, grid, block, s); break;

@@ -27,45 +27,47 @@ template <typename Tin>
 __global__ void __launch_bounds__(256)
     k_sep_row_plain(const ConvArgs a, const __grid_constant__ TapsParam<float, 2 * 33> tp) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= a.W || y >= a.H) return;
+    if (x >= a.W) return;
     const Tin* in = static_cast<const Tin*>(a.in);
     const float* row = a.taps_dev ? static_cast<const float*>(a.taps_dev) : tp.w;
     const float bv = to_acc(border_pixel<Tin>(a));
     const int rr = (a.kw - 1) / 2;
-    float acc = 0.f;
+    for (int y = blockIdx.y * blockDim.y + threadIdx.y; y < a.H; y += gridDim.y * blockDim.y) {
+        float acc = 0.f;
 #pragma unroll 1
-    for (int i = 0; i < a.kw; ++i) {
-        const int gx = x + i - rr;
-        float v;
-        if (gx >= 0 && gx < a.W) v = to_acc(in[(long long)y * a.in_pitch + gx]);
-        else if (a.border == IMCL_BORDER_CONSTANT) v = bv;
-        else v = to_acc(in[(long long)y * a.in_pitch + clampi(gx, 0, a.W - 1)]);
-        acc = __fmaf_rn(row[i], v, acc);
+        for (int i = 0; i < a.kw; ++i) {
+            const int gx = x + i - rr;
+            float v;
+            if (gx >= 0 && gx < a.W) v = to_acc(in[(long long)y * a.in_pitch + gx]);
+            else if (a.border == IMCL_BORDER_CONSTANT) v = bv;
+            else v = to_acc(in[(long long)y * a.in_pitch + clampi(gx, 0, a.W - 1)]);
+            acc = __fmaf_rn(row[i], v, acc);
+        }
+        static_cast<float*>(a.work)[(long long)y * a.W + x] = acc;
     }
-    static_cast<float*>(a.work)[(long long)y * a.W + x] = acc;
 }
 
 template <typename Tout>
 __global__ void __launch_bounds__(256)
     k_sep_col_plain(const ConvArgs a, const __grid_constant__ TapsParam<float, 2 * 33> tp) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= a.W || y >= a.H) return;
+    if (x >= a.W) return;
     const float* t = static_cast<const float*>(a.work);
     const float* col = a.taps2_dev ? static_cast<const float*>(a.taps2_dev) : tp.w + 33;
     const int rc = (a.kh - 1) / 2;
-    float acc = 0.f;
+    for (int y = blockIdx.y * blockDim.y + threadIdx.y; y < a.H; y += gridDim.y * blockDim.y) {
+        float acc = 0.f;
 #pragma unroll 1
-    for (int j = 0; j < a.kh; ++j) {
-        const int gy = y + j - rc;
-        float v;
-        if (gy >= 0 && gy < a.H) v = t[(long long)gy * a.W + x];
-        else if (a.border == IMCL_BORDER_CONSTANT) v = a.bv_f;
-        else v = t[(long long)clampi(gy, 0, a.H - 1) * a.W + x];
-        acc = __fmaf_rn(col[j], v, acc);
+        for (int j = 0; j < a.kh; ++j) {
+            const int gy = y + j - rc;
+            float v;
+            if (gy >= 0 && gy < a.H) v = t[(long long)gy * a.W + x];
+            else if (a.border == IMCL_BORDER_CONSTANT) v = a.bv_f;
+            else v = t[(long long)clampi(gy, 0, a.H - 1) * a.W + x];
+            acc = __fmaf_rn(col[j], v, acc);
+        }
+        static_cast<Tout*>(a.out)[(long long)y * a.out_pitch + x] = Store<Tout, float>::cvt(acc);
     }
-    static_cast<Tout*>(a.out)[(long long)y * a.out_pitch + x] = Store<Tout, float>::cvt(acc);
 }
 
 // ------------------------------------------------------------------ fused
@@ -343,7 +345,7 @@ imcl_status launch_sep_plain(const ConvCall& c, const imcl_variant& v, cudaStrea
         for (int i = 0; i < c.kw; ++i) tp.w[i] = static_cast<const float*>(c.taps)[i];
         for (int j = 0; j < c.kh; ++j) tp.w[33 + j] = static_cast<const float*>(c.taps2)[j];
     }
-    dim3 grid((c.W + bx - 1) / bx, (c.H + by - 1) / by), block(bx, by);
+    dim3 grid = grid_2d(c.W, c.H, bx, by), block(bx, by);
     k_sep_row_plain<Tin><<<grid, block, 0, s>>>(a, tp);
     k_sep_col_plain<Tout><<<grid, block, 0, s>>>(a, tp);
     return cuda_fail(cudaGetLastError(), "sepconv plain launch");

@@ -33,17 +33,19 @@ __device__ __forceinline__ uint32_t hash32(uint32_t x) {
 }
 
 __global__ void k_fill_pattern(void* p, int dtype, int W, int H, long long pitch_b, uint32_t seed) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x >= W || y >= H) return;
-    const uint32_t h = hash32((uint32_t)(y * 7919 + x) ^ seed);
-    char* row = static_cast<char*>(p) + (long long)y * pitch_b;
-    const float u = (h >> 8) * (1.0f / 16777216.0f);
-    switch (dtype) {
-        case IMCL_U8: reinterpret_cast<uint8_t*>(row)[x] = (uint8_t)(h & 255u); break;
-        case IMCL_I32: reinterpret_cast<int32_t*>(row)[x] = (int32_t)(h & 1023u) - 512; break;
-        case IMCL_F32: reinterpret_cast<float*>(row)[x] = u; break;
-        case IMCL_F16: reinterpret_cast<__half*>(row)[x] = __float2half_rn(u); break;
-        case IMCL_BF16: reinterpret_cast<__nv_bfloat16*>(row)[x] = __float2bfloat16_rn(u); break;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= W) return;
+    for (int y = blockIdx.y; y < H; y += gridDim.y) {
+        const uint32_t h = hash32((uint32_t)(y * 7919 + x) ^ seed);
+        char* row = static_cast<char*>(p) + (long long)y * pitch_b;
+        const float u = (h >> 8) * (1.0f / 16777216.0f);
+        switch (dtype) {
+            case IMCL_U8: reinterpret_cast<uint8_t*>(row)[x] = (uint8_t)(h & 255u); break;
+            case IMCL_I32: reinterpret_cast<int32_t*>(row)[x] = (int32_t)(h & 1023u) - 512; break;
+            case IMCL_F32: reinterpret_cast<float*>(row)[x] = u; break;
+            case IMCL_F16: reinterpret_cast<__half*>(row)[x] = __float2half_rn(u); break;
+            case IMCL_BF16: reinterpret_cast<__nv_bfloat16*>(row)[x] = __float2bfloat16_rn(u); break;
+        }
     }
 }
 
@@ -60,19 +62,21 @@ __device__ __forceinline__ float load_any(const char* row, int dtype, int x) {
 // res[0] = max |a - b| (as float bits), res[1] = max |b|, res[2] = count of a != b
 __global__ void k_compare(const void* a, const void* b, int dtype, int W, int H, long long pitch_b,
                           unsigned int* res) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x >= W || y >= H) return;
-    const char* ra = static_cast<const char*>(a) + (long long)y * pitch_b;
-    const char* rb = static_cast<const char*>(b) + (long long)y * pitch_b;
-    float va = load_any(ra, dtype, x), vb = load_any(rb, dtype, x);
-    bool differ;
-    if (dtype == IMCL_I32) differ = reinterpret_cast<const int32_t*>(ra)[x] != reinterpret_cast<const int32_t*>(rb)[x];
-    else differ = !(va == vb);
-    float d = fabsf(va - vb);
-    if (!(d == d)) d = 3.0e38f;   // NaN compares as a huge difference
-    atomicMax(&res[0], __float_as_uint(d));
-    atomicMax(&res[1], __float_as_uint(fabsf(vb)));
-    if (differ) atomicAdd(&res[2], 1u);
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= W) return;
+    for (int y = blockIdx.y; y < H; y += gridDim.y) {
+        const char* ra = static_cast<const char*>(a) + (long long)y * pitch_b;
+        const char* rb = static_cast<const char*>(b) + (long long)y * pitch_b;
+        float va = load_any(ra, dtype, x), vb = load_any(rb, dtype, x);
+        bool differ;
+        if (dtype == IMCL_I32) differ = reinterpret_cast<const int32_t*>(ra)[x] != reinterpret_cast<const int32_t*>(rb)[x];
+        else differ = !(va == vb);
+        float d = fabsf(va - vb);
+        if (!(d == d)) d = 3.0e38f;   // NaN compares as a huge difference
+        atomicMax(&res[0], __float_as_uint(d));
+        atomicMax(&res[1], __float_as_uint(fabsf(vb)));
+        if (differ) atomicAdd(&res[2], 1u);
+    }
 }
 
 TuneScratch::~TuneScratch() {
@@ -94,7 +98,7 @@ imcl_status TuneScratch::image(int dtype, int W, int H, uint32_t seed, void** p,
     *pitch_b = ((int64_t)W * sz + 127) / 128 * 128;
     imcl_status st = alloc(p, (size_t)(*pitch_b) * H);
     if (st != IMCL_OK) return st;
-    dim3 grid((W + 255) / 256, H);
+    dim3 grid = grid_2d(W, H, 256, 1);
     k_fill_pattern<<<grid, 256, 0, s>>>(*p, dtype, W, H, *pitch_b, seed);
     return cuda_fail(cudaGetLastError(), "tuner: fill");
 }
@@ -165,7 +169,7 @@ public:
         cudaMemsetAsync(job_.out, 0xff, (size_t)job_.out_pitch_b * job_.H, s_);
         if (job_.run(v, s_) != IMCL_OK) return false;   // shape not valid for this variant
         cudaMemsetAsync(res_, 0, 4 * sizeof(unsigned int), s_);
-        dim3 grid((job_.W + 255) / 256, job_.H);
+        dim3 grid = grid_2d(job_.W, job_.H, 256, 1);
         k_compare<<<grid, 256, 0, s_>>>(job_.out, ref_, job_.out_dtype, job_.W, job_.H, job_.out_pitch_b, res_);
         unsigned int h[4] = {0, 0, 0, 0};
         cudaError_t ce = cudaMemcpyAsync(h, res_, sizeof h, cudaMemcpyDeviceToHost, s_);

@@ -321,6 +321,18 @@ def probe_fp32(packed: bool = False, stream=None) -> float:
     return v.value
 
 
+def probe_imad(stream=None) -> float:
+    """Measured int32 multiply-add throughput of the current GPU in Tops/s (2 per IMAD)."""
+    v = ctypes.c_double(0)
+    check(lib().imagecl_probe_imad(ctypes.byref(v), ctypes.c_void_p(stream_handle(stream))))
+    return v.value
+
+
+def selftest_wait_timeout(rounds: int = 1000, stream=None) -> None:
+    """Launch the bounded-wait self-test (a wait that runs out and records code 1)."""
+    check(lib().imagecl_selftest_wait_timeout(int(rounds), ctypes.c_void_p(stream_handle(stream))))
+
+
 def version() -> str:
     return lib().imagecl_version().decode()
 

@@ -72,25 +72,32 @@ def exchange_halos(ext, bands, rank: int, dist, group=None):
     """Fill the halo rows of this rank's extended band `ext` (rows [e0, e1) of the image,
     own rows already in place) from the ranks that own them, and send the rows of mine
     that other ranks' halos cover.  Usually the two neighbours; more when bands are
-    thinner than the halo.  Every rank calls it.  Blocking."""
+    thinner than the halo.  Every rank calls it.  Blocking.
+
+    All sends and receives of the call are posted together as one batch of
+    point-to-point operations (``batch_isend_irecv``).  NCCL runs such a batch as one
+    group, so a pair of ranks that each receive from and send to the other cannot block
+    one another: posted one at a time, each rank's receive would wait on a send that
+    sits behind the other rank's receive on the pair's stream."""
     y0, y1, e0, e1 = bands[rank]
-    reqs, recvs = [], []
+    ops, recvs = [], []
     for nb, (n0, n1, ne0, ne1) in enumerate(bands):
         if nb == rank:
             continue
         r0, r1 = max(n0, e0), min(n1, e1)          # its own rows inside my extended band
         if r1 > r0 and y1 > y0:
             buf = ext.new_empty((r1 - r0,) + tuple(ext.shape[1:]))
-            reqs.append(dist.irecv(buf, src=nb, group=group))
+            ops.append(dist.P2POp(dist.irecv, buf, nb, group))
             recvs.append((buf, r0, r1))
     for nb, (n0, n1, ne0, ne1) in enumerate(bands):
         if nb == rank:
             continue
         s0, s1 = max(y0, ne0), min(y1, ne1)        # my own rows inside its extended band
         if s1 > s0 and n1 > n0:
-            reqs.append(dist.isend(ext[s0 - e0:s1 - e0].contiguous(), dst=nb, group=group))
-    for rq in reqs:
-        rq.wait()
+            ops.append(dist.P2POp(dist.isend, ext[s0 - e0:s1 - e0].contiguous(), nb, group))
+    if ops:
+        for rq in dist.batch_isend_irecv(ops):
+            rq.wait()
     for buf, r0, r1 in recvs:
         ext[r0 - e0:r1 - e0].copy_(buf)
     return ext

@@ -115,3 +115,46 @@ def check_harris_output(gpu, R64, scale, what=""):
     emax = float(e.max()) if e.size else 0.0
     assert emax <= TOL_HARRIS, f"{what}: max scaled error {emax:.3e} > {TOL_HARRIS}"
     return emax
+
+
+def harris_backward_scale(img, sx, sy, win, gR, k=0.04):
+    """Element-wise scales (sdI, dsx, dsy, dwin) for the Harris adjoint: the adjoint
+    evaluated on absolute values, every product and sum of the chain rule taken with the
+    magnitudes of its terms.  The forward planes are Ax = |Sx| (*) |I| (>= |Ix|, and the
+    same for y), their products, and |G| (*) those; the response derivatives become
+    |gR| (Syy + 2k tr), |gR| (Sxx + 2k tr) and 2 |gR| Sxy; each adjoint step then runs
+    with |taps| on non-negative planes.  The computed gradient's rounding error is
+    bounded by a modest multiple of the unit roundoff times this scale (the first-order
+    forward-error bound of the chain), which is what the 1e-4 gate measures against."""
+    ai = np.abs(to_f64(img))
+    asx, asy, aw = np.abs(to_f64(sx)), np.abs(to_f64(sy)), np.abs(to_f64(win))
+    wk = aw.shape[0]
+    if wk % 2 == 0:   # even window: offsets -wk/2 .. wk/2-1, the centred odd one padded
+        aw = np.pad(aw, ((0, 1), (0, 1)))
+    ag = np.abs(to_f64(gR))
+    ax = oracle.conv2d(ai, asx)
+    ay = oracle.conv2d(ai, asy)
+    p = {"xx": ax * ax, "yy": ay * ay, "xy": ax * ay}
+    s = {c: oracle.conv2d(p[c], aw) for c in p}
+    tr = s["xx"] + s["yy"]
+    gs = {"xx": ag * (s["yy"] + 2 * k * tr), "yy": ag * (s["xx"] + 2 * k * tr), "xy": 2 * ag * s["xy"]}
+    gp, dwin = {}, np.zeros_like(aw)
+    for c in p:
+        gp[c], dw_c = oracle.conv2d_backward(p[c], aw, gs[c])
+        dwin += dw_c
+    gix = 2 * ax * gp["xx"] + ay * gp["xy"]
+    giy = 2 * ay * gp["yy"] + ax * gp["xy"]
+    di_x, dsx = oracle.conv2d_backward(ai, asx, gix)
+    di_y, dsy = oracle.conv2d_backward(ai, asy, giy)
+    return di_x + di_y, dsx, dsy, dwin[:wk, :wk]
+
+
+TOL_GRAD = 1e-4
+
+
+def check_grad(gpu, ref, scale, what="", tol=TOL_GRAD):
+    """Element-wise scaled gradient error, |g - g64| / scale, gated at `tol`; returns the max."""
+    e = np.abs(to_f64(gpu) - ref) / np.maximum(scale, 1e-30)
+    emax = float(e.max()) if e.size else 0.0
+    assert emax <= tol, f"{what}: scaled error {emax:.3e} > {tol}"
+    return emax

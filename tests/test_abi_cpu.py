@@ -102,6 +102,8 @@ def test_validation_rejects_bad_calls_before_any_launch(lib):
     assert _call(lib, u8_in, i32_out, taps_dt=_abi.I32, border=1, bv=300.0) == _abi.ERR_INVALID
     assert _call(lib, u8_in, i32_out, taps_dt=_abi.I32, border=1, bv=2.5) == _abi.ERR_INVALID
     assert b"border_value" in lib.imagecl_last_error()
+    assert lib.imagecl_selftest_wait_timeout(0, None) == _abi.ERR_INVALID          # unbounded wait
+    assert lib.imagecl_selftest_wait_timeout(1 << 21, None) == _abi.ERR_INVALID
 
 
 def test_build_units_cover_every_tiled_side():

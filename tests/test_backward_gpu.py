@@ -12,7 +12,7 @@ import torch
 
 import oracle
 from gpu_util import place
-from metrics import band, to_f64
+from metrics import band, check_grad, harris_backward_scale, to_f64
 from paper_1605_06399_gb300 import _abi, autograd, ops, synth
 
 pytestmark = pytest.mark.gpu
@@ -82,12 +82,6 @@ def test_sepconv_backward_matches_oracle(nr, nc, dt):
                 _gate(dc, dc64, sdc, "dcol " + what)
 
 
-def _normwise(gpu, ref, what, tol=TOL_GRAD):
-    d = float(np.max(np.abs(to_f64(gpu) - ref)))
-    s = float(np.max(np.abs(ref))) + 1e-30
-    assert d / s <= tol, f"{what}: normwise error {d / s:.3e}"
-
-
 @pytest.mark.parametrize("wk", [2, 3, 4, 5, 7])
 def test_harris_backward_matches_oracle(wk):
     g = np.random.default_rng(7000 + wk)
@@ -97,16 +91,14 @@ def test_harris_backward_matches_oracle(wk):
     for (h, wd) in [(1, 1), (3, 7), (16, 16), (45, 60), (100, 133)]:
         img = synth.rectangles_image(g, h, wd, n_rect=10, side_lo=2, side_hi=max(3, min(h, wd)))
         gR = g.standard_normal((h, wd)).astype(np.float32)
-        dI64, dsx64, dsy64, dw64 = oracle.harris_backward(img, sx, sy, win, gR, 0.04)
+        ref = oracle.harris_backward(img, sx, sy, win, gR, 0.04)
+        scale = harris_backward_scale(img, sx, sy, win, gR, 0.04)
         for mem in ("host", "device"):
             taps = [torch.from_numpy(np.ascontiguousarray(t)).cuda() if mem == "device" else t for t in (sx, sy, win)]
             dI, dsx, dsy, dw = ops.harris_backward(torch.from_numpy(gR).cuda(), torch.from_numpy(img).cuda(),
                                                    *taps, k=0.04)
-            what = f"wk={wk} {h}x{wd} {mem}"
-            _normwise(dI, dI64, "dI " + what)
-            _normwise(dsx, dsx64, "dsx " + what)
-            _normwise(dsy, dsy64, "dsy " + what)
-            _normwise(dw, dw64, "dwin " + what)
+            for got, want, s, name in zip((dI, dsx, dsy, dw), ref, scale, ("dI", "dsx", "dsy", "dwin")):
+                check_grad(got, want, s, f"{name} wk={wk} {h}x{wd} {mem}")
 
 
 def test_autograd_wiring():
@@ -116,17 +108,20 @@ def test_autograd_wiring():
     up = torch.from_numpy(g.standard_normal((40, 57)).astype(np.float32)).cuda()
     (autograd.conv2d(x, w) * up).sum().backward()
     dx64, dw64 = oracle.conv2d_backward(x.detach().cpu(), w.detach().cpu(), up.cpu())
-    _normwise(x.grad, dx64, "autograd conv dx", 1e-5)
-    _normwise(w.grad, dw64, "autograd conv dw", 1e-5)
+    sdx, sdw = oracle.conv2d_backward(x.detach().cpu().abs(), w.detach().cpu().abs(), up.cpu().abs())
+    check_grad(x.grad, dx64, sdx, "autograd conv dx")
+    check_grad(w.grad, dw64, sdw, "autograd conv dw")
 
     x.grad = None
     r = torch.from_numpy(synth.gaussian_taps(3)).cuda().requires_grad_(True)
     c = torch.from_numpy(g.standard_normal(5).astype(np.float32)).cuda().requires_grad_(True)
     (autograd.sepconv(x, r, c) * up).sum().backward()
     dx64, dr64, dc64 = oracle.sepconv_backward(x.detach().cpu(), r.detach().cpu(), c.detach().cpu(), up.cpu())
-    _normwise(x.grad, dx64, "autograd sep dx", 1e-5)
-    _normwise(r.grad, dr64, "autograd sep drow", 1e-5)
-    _normwise(c.grad, dc64, "autograd sep dcol", 1e-5)
+    sdx, sdr, sdc = oracle.sepconv_backward(x.detach().cpu().abs(), r.detach().cpu().abs(), c.detach().cpu().abs(),
+                                            up.cpu().abs())
+    check_grad(x.grad, dx64, sdx, "autograd sep dx")
+    check_grad(r.grad, dr64, sdr, "autograd sep drow")
+    check_grad(c.grad, dc64, sdc, "autograd sep dcol")
 
     img = torch.from_numpy(synth.rectangles_image(g, 48, 64, n_rect=8, side_lo=4, side_hi=30)).cuda()
     img.requires_grad_(True)
@@ -135,10 +130,11 @@ def test_autograd_wiring():
     win = torch.from_numpy(synth.gaussian_window(5, 1.0)).cuda().requires_grad_(True)
     upR = torch.from_numpy(g.standard_normal((48, 64)).astype(np.float32)).cuda()
     (autograd.harris(img, sx, sy, win) * upR).sum().backward()
-    ref = oracle.harris_backward(img.detach().cpu(), synth.sobel_x(), synth.sobel_y(),
-                                 synth.gaussian_window(5, 1.0), upR.cpu(), 0.04)
-    for got, want, name in zip((img.grad, sx.grad, sy.grad, win.grad), ref, ("dI", "dsx", "dsy", "dwin")):
-        _normwise(got, want, "autograd harris " + name)
+    args = (img.detach().cpu(), synth.sobel_x(), synth.sobel_y(), synth.gaussian_window(5, 1.0), upR.cpu(), 0.04)
+    ref = oracle.harris_backward(*args)
+    scale = harris_backward_scale(*args)
+    for got, want, s, name in zip((img.grad, sx.grad, sy.grad, win.grad), ref, scale, ("dI", "dsx", "dsy", "dwin")):
+        check_grad(got, want, s, "autograd harris " + name)
 
 
 def test_conv2d_backward_8192_bands_and_identities():
@@ -165,10 +161,10 @@ def test_conv2d_backward_8192_bands_and_identities():
     assert abs(lhs - rhs_w) <= 1e-6 * scale
 
 
-def test_harris_backward_4096_identities_and_bands():
+def test_harris_backward_4096_identities():
     """4096x4096 rectangles: the Euler identities of the degree-4 (image, Sobel taps)
-    and degree-2 (window) homogeneous response hold over the whole image, and dI matches
-    the oracle on row bands (crops with an 8-row margin reproduce the whole image's dI)."""
+    and degree-2 (window) homogeneous response hold over the whole image (the element-wise
+    comparison with the oracle at this size is in the workload tests)."""
     img, sx, sy, win, k = synth.workload_harris()
     g = np.random.default_rng(8200)
     gR = torch.from_numpy(g.standard_normal((4096, 4096), dtype=np.float32)).cuda()
@@ -181,8 +177,3 @@ def test_harris_backward_4096_identities_and_bands():
     assert abs(float(np.sum(dw.cpu().numpy() * win.astype(np.float64))) - 2 * ip) <= 1e-4 * scale
     t = float(np.sum(dsx.cpu().numpy() * sx.astype(np.float64)) + np.sum(dsy.cpu().numpy() * sy.astype(np.float64)))
     assert abs(t - 4 * ip) <= 1e-4 * scale
-    grc = gR.cpu().numpy()
-    for rows in [(0, 3), (2000, 2004), (4093, 4096)]:
-        a, b = max(0, rows[0] - 8), min(4096, rows[1] + 8)
-        dI64, _, _, _ = oracle.harris_backward(img[a:b], sx, sy, win, grc[a:b], k)
-        _normwise(dI[rows[0]:rows[1]], dI64[rows[0] - a:rows[1] - a], f"dI rows={rows}")

@@ -3,6 +3,7 @@ import numpy as np
 import pytest
 import torch
 
+from gpu_util import assert_pads_intact, empty_padded
 from metrics import check_float_output, conv_reference, sep_reference
 from paper_1605_06399_gb300 import Batch, ops, synth
 
@@ -85,7 +86,8 @@ def test_mixed_batch_matches_oracle_and_replays():
 def test_batch_pitched_views_unaligned():
     """Images that are column windows of wider buffers: rows start off 16-byte boundaries
     (the first rows and last rows of such images are read without bulk copies) and the
-    pitch exceeds the width."""
+    pitch exceeds the width.  Outputs are views into padded buffers with guard bands that
+    must stay untouched."""
     g = np.random.default_rng(9100)
     items, meta = [], []
     i = 0
@@ -97,21 +99,23 @@ def test_batch_pitched_views_unaligned():
             if i % 2 == 0:
                 k = (3, 7, 15)[i % 3]
                 taps = g.standard_normal((k, k)).astype(np.float32)
-                items.append({"op": "conv", "x": x, "taps": torch.from_numpy(taps).cuda(), "out_dtype": od,
-                              "border": border, "border_value": bv})
+                items.append({"op": "conv", "x": x, "taps": torch.from_numpy(taps).cuda(),
+                              "out": empty_padded(h, w, od), "border": border, "border_value": bv})
                 meta.append(("conv", x.cpu(), taps, None, od, border, bv))
             else:
                 r = g.standard_normal(2 * (i % 7) + 1).astype(np.float32)
                 c = g.standard_normal(2 * ((i + 3) % 7) + 1).astype(np.float32)
                 items.append({"op": "sep", "x": x, "taps": torch.from_numpy(r).cuda(),
-                              "col_taps": torch.from_numpy(c).cuda(), "out_dtype": od, "border": border,
-                              "border_value": bv})
+                              "col_taps": torch.from_numpy(c).cuda(), "out": empty_padded(h, w, od),
+                              "border": border, "border_value": bv})
                 meta.append(("sep", x.cpu(), r, c, od, border, bv))
             i += 1
     b = Batch(items, tune_budget_s=0.5)
     outs = b.run()
     torch.cuda.synchronize()
     _check(meta, outs)
+    for k, it in enumerate(items):
+        assert_pads_intact(it["out"], f"batch item {k}")
     b.close()
 
 

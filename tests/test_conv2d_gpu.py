@@ -4,7 +4,7 @@ import pytest
 import torch
 
 import oracle
-from gpu_util import empty_padded, padded
+from gpu_util import assert_pads_intact, empty_padded, padded
 from metrics import check_float_output, conv_reference, to_f64
 from paper_1605_06399_gb300 import ImclError, _abi, ops, synth
 
@@ -55,6 +55,8 @@ def _run_all(x_cpu, taps, out_dtype, border, bv, taps_mem, layout):
         except ImclError as e:
             assert e.status in (_abi.ERR_UNSUPPORTED, _abi.ERR_ALIGN), str(e)
             continue
+        if out is not None:
+            assert_pads_intact(out, f"conv2d {v}")
         yield v, y
 
 
@@ -177,12 +179,16 @@ def test_tuner_reports_and_caches(tmp_path):
 def test_row_bands_on_one_gpu_match_whole_image(k, border, bv):
     """The row-band partition of one image (what each rank of a multi-GPU run computes
     after its halo exchange), run band by band on one GPU: the band's own rows of the
-    result on its extended band equal the whole image's rows bit for bit."""
+    result on its extended band equal the whole image's rows bit for bit, and match the
+    oracle on the whole image's rows."""
     from paper_1605_06399_gb300 import shard
     g = np.random.default_rng(6100 + k)
     x = torch.from_numpy(g.random((517, 301), dtype=np.float32)).cuda()
     taps = g.standard_normal((k, k)).astype(np.float32)
     whole = ops.conv2d(x, taps, border, bv)
+    xc = x.cpu().numpy()
     for (y0, y1, e0, e1) in shard.row_bands(517, 4, (k - 1) // 2):
         band = ops.conv2d(x[e0:e1].contiguous(), taps, border, bv)
         assert torch.equal(band[y0 - e0:y1 - e0], whole[y0:y1]), (y0, y1)
+        ref, s = conv_reference(xc, taps, border, bv, rows=(y0, y1), halo=k // 2)
+        check_float_output(band[y0 - e0:y1 - e0], ref, s, torch.float32, f"band rows {y0}..{y1}")

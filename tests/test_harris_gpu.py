@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_util import out_buffer, place
+from gpu_util import assert_pads_intact, out_buffer, place
 from metrics import check_harris_output, harris_reference
 from paper_1605_06399_gb300 import ImclError, _abi, ops, synth
 
@@ -59,6 +59,8 @@ def test_harris_every_variant_matches_oracle(wk):
                 except ImclError as e:
                     assert e.status in (_abi.ERR_UNSUPPORTED, _abi.ERR_ALIGN), str(e)
                     continue
+                if out is not None:
+                    assert_pads_intact(out, f"harris {v}")
                 check_harris_output(y, R64, sc, f"wk={wk} {h}x{w} mem={mem} {layout} {v}")
                 n += 1
     assert n > 0

@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_util import out_buffer, place
+from gpu_util import assert_pads_intact, out_buffer, place
 from metrics import check_float_output, sep_reference
 from paper_1605_06399_gb300 import ImclError, _abi, ops, synth
 
@@ -54,6 +54,8 @@ def test_sepconv_every_variant_matches_oracle(dt, out_dtype, radius):
                     except ImclError as e:
                         assert e.status in (_abi.ERR_UNSUPPORTED, _abi.ERR_ALIGN), str(e)
                         continue
+                    if out is not None:
+                        assert_pads_intact(out, f"sepconv {v}")
                     check_float_output(y, ref, s, out_dtype,
                                        f"{dt}->{out_dtype} R={radius} {h}x{w} {border} mem={mem} {layout} {v}")
                     n += 1

@@ -1,7 +1,7 @@
 """imagecl_sepconv_noalloc: the separable correlation for callers that must not
-allocate device memory (graph-recording code, plugins inside a framework that owns all
-device memory, latency-critical loops).  Its row-pass intermediate lives in a fixed
-library array instead of a caller workspace.
+allocate device memory (plugins inside a framework that owns all device memory,
+real-time loops that cannot take an allocation's synchronisation).  Its row-pass
+intermediate lives in a fixed library array instead of a caller workspace.
 
 This file is named so that pytest collects it last.  Each check calls the entry point
 through the C ABI twice in a row, with different inputs, and compares both results with
@@ -84,3 +84,22 @@ def test_noalloc_rejects_images_beyond_its_scratch():
     x2 = torch.zeros((2048, 2048), device="cuda")           # exactly at the limit
     assert _noalloc(x2, torch.empty_like(x2), t, t) == _abi.OK
     torch.cuda.synchronize()
+
+
+def test_noalloc_images_taller_than_a_grid():
+    """2 x 2,000,000 pixels fit the scratch array but need more row blocks than a grid
+    can be high (65535): the kernels walk the rows, so the result still equals PLAIN."""
+    g = np.random.default_rng(406)
+    x = torch.from_numpy(synth.uniform_f32(g, 2_000_000, 2)).cuda()
+    row, col = synth.gaussian_taps(1), synth.gaussian_taps(3)
+    for _ in range(2):
+        y = torch.full_like(x, float("nan"))
+        assert _noalloc(x, y, row, col) == _abi.OK, _abi.lib().imagecl_last_error()
+        ref = ops.sepconv(x, row, col, variant={"kind": _abi.KIND_PLAIN, "bx": 16, "by": 16})
+        torch.cuda.synchronize()
+        assert torch.equal(y, ref)
+    y64, s = sep_reference(x.cpu(), row, col, rows=(0, 64), halo=3)
+    check_float_output(y[:64], y64, s, torch.float32, "tall no-alloc top rows")
+    y64, s = sep_reference(x.cpu(), row, col, rows=(1_999_936, 2_000_000), halo=3)
+    check_float_output(y[-64:], y64, s, torch.float32, "tall no-alloc bottom rows")
+
