@@ -68,8 +68,12 @@ typedef struct {
     int64_t pitch_bytes; /* bytes between the starts of consecutive rows      */
 } imcl_image;
 
-/* Kernel variant: one point of the tuning space of §5.2 / Table 1. */
-typedef enum { IMCL_KIND_PLAIN = 0, IMCL_KIND_TILED = 1 } imcl_kind;
+/* Kernel variant: one point of the tuning space of §5.2 / Table 1.  TENSOR (conv2d, sides
+ * 9..15, f32 / f16 / bf16 images): the correlation as banded-Toeplitz matrix products on
+ * the tensor cores (split-precision operands, f32 accumulation), bx = 16-column blocks
+ * per work unit; the tuner offers it beside the FP32-pipe variants and keeps it only
+ * when it is faster. */
+typedef enum { IMCL_KIND_PLAIN = 0, IMCL_KIND_TILED = 1, IMCL_KIND_TENSOR = 2 } imcl_kind;
 typedef enum { IMCL_LOAD_GLOBAL = 0, IMCL_LOAD_SMEM = 1, IMCL_LOAD_TMA = 2 } imcl_load;
 typedef enum { IMCL_FILT_PARAM = 0, IMCL_FILT_SMEM = 1 } imcl_filt;
 /* IMCL_MAP_REGISTER (sepconv only): the row pass result stays in each thread's registers

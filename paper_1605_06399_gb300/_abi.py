@@ -25,7 +25,7 @@ BORDER_CLAMP, BORDER_CONSTANT = 0, 1
 MEM_HOST, MEM_DEVICE = 0, 1
 OP_CONV2D, OP_SEPCONV, OP_HARRIS = 0, 1, 2
 # imcl_kind / imcl_load / imcl_filt / imcl_map / imcl_unroll
-KIND_PLAIN, KIND_TILED = 0, 1
+KIND_PLAIN, KIND_TILED, KIND_TENSOR = 0, 1, 2
 LOAD_GLOBAL, LOAD_SMEM, LOAD_TMA = 0, 1, 2
 FILT_PARAM, FILT_SMEM = 0, 1
 MAP_BLOCKED, MAP_INTERLEAVED, MAP_REGISTER = 0, 1, 2

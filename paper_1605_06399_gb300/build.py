@@ -28,7 +28,8 @@ TILED_K = (3, 5, 7, 9, 11, 13, 15)
 TILED_GROUPS = (0, 1, 2, 3)
 SEP_GROUPS = (0, 1, 2)
 SEP_RSETS = (0, 1)
-MULTI = ("conv2d_tiled.cu", "sepconv_fused.cu")
+TC_K = (9, 11, 13, 15)
+MULTI = ("conv2d_tiled.cu", "sepconv_fused.cu", "conv2d_tc.cu")
 
 
 def _nvcc() -> str:
@@ -49,6 +50,8 @@ def units() -> list[tuple[str, list[str], str]]:
             out.append((os.path.join(CSRC, "conv2d_tiled.cu"),
                         [f"-DIMCL_TILED_K={k}", f"-DIMCL_TILED_GROUP={g}"],
                         f"conv2d_tiled_k{k}_g{g}.o"))
+    for k in TC_K:
+        out.append((os.path.join(CSRC, "conv2d_tc.cu"), [f"-DIMCL_TC_K={k}"], f"conv2d_tc_k{k}.o"))
     for g in SEP_GROUPS:
         for r in SEP_RSETS:
             out.append((os.path.join(CSRC, "sepconv_fused.cu"),

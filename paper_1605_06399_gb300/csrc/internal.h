@@ -93,6 +93,12 @@ IMCL_DECL_TILED(13)
 IMCL_DECL_TILED(15)
 #undef IMCL_DECL_TILED
 
+// conv2d_tc.cu is compiled once per side K in {9, 11, 13, 15}: the tensor-core variants.
+void register_conv_tc_k9(std::vector<ConvEntry>& t);
+void register_conv_tc_k11(std::vector<ConvEntry>& t);
+void register_conv_tc_k13(std::vector<ConvEntry>& t);
+void register_conv_tc_k15(std::vector<ConvEntry>& t);
+
 const std::vector<ConvEntry>& conv_table();
 
 // Separable correlation: the same entry type; `k` is the radius R a fused kernel is

@@ -180,6 +180,10 @@ const std::vector<ConvEntry>& conv_table() {
         IMCL_REG_TILED(13)
         IMCL_REG_TILED(15)
 #undef IMCL_REG_TILED
+        register_conv_tc_k9(*t);
+        register_conv_tc_k11(*t);
+        register_conv_tc_k13(*t);
+        register_conv_tc_k15(*t);
         return t;
     }();
     return *table;

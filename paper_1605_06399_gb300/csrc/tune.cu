@@ -110,6 +110,14 @@ std::vector<imcl_variant> expand_shapes(const std::vector<imcl_variant>& base) {
     std::vector<imcl_variant> out;
     for (const imcl_variant& b : base) {
         if (b.kind == IMCL_KIND_PLAIN) { out.push_back(b); continue; }
+        if (b.kind == IMCL_KIND_TENSOR) {   // work-unit widths (16-column blocks)
+            for (int nb : {16, 8, 32, 4}) {
+                imcl_variant v = b;
+                v.bx = nb;
+                out.push_back(v);
+            }
+            continue;
+        }
         out.push_back(b);   // the registered default shape first
         for (auto& sh : kShapes) {
             if (sh[0] == b.bx && sh[1] == b.by) continue;
