@@ -17,30 +17,31 @@
 // epilogue adds the J lane-shifted column blocks, y(x0 + n, y0 + m) =
 // sum_{j'} D[m + j'][(j', n)], with warp shuffles (and a small shared-memory exchange
 // across the four lane quarters), giving 129 - J output rows per 128-row MMA tile.
-// Grouping keeps N at 16 J..32 J, so each MMA reads its 128 x 32-byte A slice once for
-// at least 80 output columns' worth of products (shared-memory bandwidth, not the
-// tensor pipe, bounds an N = 16 Toeplitz MMA).
+// Grouping keeps N at 16 J, so each MMA reads its 128 x 32-byte A slice once for at
+// least 80 columns of products (shared-memory bandwidth, not the tensor pipe, bounds an
+// N = 16 Toeplitz MMA).
 //
 // Precision.  f16 / bf16 images are exact MMA operands; the taps are split into a high
 // and a low part of the same type (f16 taps are scaled by a power of two first so both
-// parts stay normal), and A x [T_hi | T_lo] runs as one MMA whose two column halves
-// are added in the epilogue: each product carries about 2^-17 relative error.  f32
-// images use the tf32 kind with both operands split into tf32 high and low parts
-// (x = x_hi + x_lo, truncated so that each part is exactly a tf32 value):
-// x_hi w_hi + x_hi w_lo + x_lo w_hi, a relative error below 3 * 2^-20 per product, the
-// dropped x_lo w_lo term included.  Both stay inside the 1e-5 scaled tolerance of the
-// f32 results.
+// parts stay normal), and A T_hi and A T_lo accumulate into the same columns: each
+// product carries about 2^-17 relative error.  f32 images use the tf32 kind with both
+// operands split into tf32 high and low parts (x = x_hi + x_lo, truncated so that each
+// part is exactly a tf32 value) and three MMAs, x_hi w_hi + x_hi w_lo + x_lo w_hi: a
+// relative error below 3 * 2^-20 per product, the dropped x_lo w_lo term included.  Both
+// stay inside the 1e-5 scaled tolerance of the f32 results.
 //
-// Pipeline (one persistent CTA per SM, 256 threads, work units = a band of 129 - J
+// Pipeline (one persistent CTA per SM, 384 threads, work units = a band of 129 - J
 // output rows x a segment of 16 NB columns):
-//   warp 0      TMA producer: 16-column slabs of the 128 + J staged rows, one 2D box per
-//               16-byte chunk column, into a ring of S slabs (zero fill outside);
-//   warp 1      allocates the tensor memory and issues the MMAs (one thread): block b
-//               of a unit reads slabs b and b + 1 (the 32-column K window);
-//   warps 2-3   converters: apply the boundary rule to slabs that leave the image and,
-//               for f32, write the tf32 high and low parts;
-//   warps 4-7   epilogue: tensor memory -> registers, shifted sums, global stores; the
-//               accumulator is double-buffered so the MMAs of the next block overlap.
+//   warp 0       TMA producer: 16-column slabs of the 128 + J staged rows, one 2D box
+//                per 16-byte chunk column, into a ring of S slabs (zero fill outside);
+//   warp 1       allocates the tensor memory and issues the MMAs (one thread): block b
+//                of a unit reads slabs b and b + 1 (the 32-column K window);
+//   warps 2-3    converters: apply the boundary rule to slabs that leave the image and,
+//                for f32, write the tf32 high and low parts;
+//   warps 4-11   epilogue, two warps per tensor-memory lane quarter (8 output columns
+//                each): one load of all J column groups, shifted sums, global stores.
+//                The accumulator has four buffers, so the MMAs of the next blocks
+//                overlap the epilogue of this one.
 // Every wait is bounded (the device status word records a timeout); the tensor memory
 // is released on every path.
 #include "conv2d_kernels.cuh"
@@ -62,8 +63,8 @@ struct TcGeo {
     static constexpr int R = (K - 1) / 2;
     static constexpr int J = (K + 1) / 2;          // filter rows per group
     static constexpr int G = 2;                    // groups, G J >= K
-    static constexpr int N1 = 16 * J;              // columns of one tap set (hi or lo)
-    static constexpr int N2 = 2 * N1;              // hi and lo tap sets side by side
+    static constexpr int N1 = 16 * J;              // accumulator columns: (half ch, row j', column n')
+    static constexpr int N2 = 2 * N1;              // B rows: the high tap set, then the low one
     static constexpr int BH = 129 - J;             // output rows per band
     static constexpr int AR = 128 + J;             // staged rows: image rows y0 - R ..
     static constexpr int ARP = (AR + 7) / 8 * 8;   // rows per chunk column (whole core matrices)
@@ -73,22 +74,25 @@ struct TcGeo {
     static constexpr int SLAB = CPS * LBO_A;           // bytes of one slab (one operand copy)
     static constexpr int KCH = 32 / CE;                // chunks of the 32-element K window
     static constexpr int KSTEP = F32 ? 8 : 16;         // K of one MMA
-    static constexpr int NKS = 32 / KSTEP;             // MMAs along K per group
+    static constexpr int NKS = 32 / KSTEP;             // MMAs along K per group and operand pair
     static constexpr int LBO_B = N2 * 16;
     static constexpr int BBYTES = G * KCH * LBO_B;
     static constexpr int S = F32 ? 6 : 8;              // slab ring depth
     static constexpr int NCOPY = F32 ? 2 : 1;          // hi (and lo) copies of a slab
+    static constexpr int NBUF = 4;                     // accumulator buffers
+    static constexpr int NEPI = 8;                     // epilogue warps
     static constexpr int NT = J * (J - 1) / 2;         // exchange entries per warp
-    static constexpr int XBYTES = 2 * 4 * NT * 16 * 4;
+    static constexpr int XBYTES = 2 * NEPI * NT * 8 * 4;
     static constexpr int TMEM_COLS = 512;
-    static_assert(G * J >= K && N2 <= 256 && 4 * N1 <= TMEM_COLS, "tensor tile shape");
+    static constexpr int THREADS = 32 * (4 + NEPI);
+    static_assert(G * J >= K && N1 <= 256 && NBUF * N1 <= TMEM_COLS, "tensor tile shape");
     static_assert(R <= 7, "the 32-column window holds 16 outputs' taps for R <= 7");
     // shared-memory layout (bytes from the 1024-aligned base)
     static constexpr int OFF_A = 0;
     static constexpr int OFF_B = OFF_A + NCOPY * S * SLAB;
     static constexpr int OFF_X = OFF_B + BBYTES;
     static constexpr int OFF_BAR = OFF_X + XBYTES;
-    static constexpr int NBAR = 3 * S + 2 + 2 + 2 + 1;  // full, ready, empty; tfull, tempty, xready; done
+    static constexpr int NBAR = 3 * S + 2 * NBUF + 2 + 1;   // full, ready, empty; tfull, tempty; xready; done
     static constexpr int SMEM = OFF_BAR + NBAR * 8 + 16 + 1024;
 };
 
@@ -98,7 +102,7 @@ struct TcArgs {
     int nsegs, units;  // segments per band, units in the grid
 };
 
-// idx-th chunk (CE elements) of the slab's chunk column c, row r: byte c LBO_A + r 16
+// The chunk (CE elements) of a slab's chunk column c, row r: byte c LBO_A + r 16.
 template <typename G>
 __device__ __forceinline__ int slab_off(int c, int r) { return c * G::LBO_A + r * 16; }
 
@@ -116,11 +120,11 @@ __device__ __forceinline__ void mbar_arrive1(uint64_t* bar) {
 }
 
 template <typename Tin, typename Tout, int K>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(TcGeo<Tin, K>::THREADS, 1)
     k_conv2d_tc(const TcArgs ta, const __grid_constant__ TapsParam<float, K * K> tp,
                 const __grid_constant__ CUtensorMap tmap) {
     using G = TcGeo<Tin, K>;
-    constexpr int R = G::R, J = G::J, S = G::S;
+    constexpr int R = G::R, J = G::J, S = G::S, NBUF = G::NBUF;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // TMA destinations want 128-byte aligned shared addresses: align the base to 1024
     uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -136,8 +140,8 @@ __global__ void __launch_bounds__(256, 1)
     uint64_t* ready = bars + S;
     uint64_t* empty = bars + 2 * S;
     uint64_t* tfull = bars + 3 * S;
-    uint64_t* tempty = tfull + 2;
-    uint64_t* xready = tempty + 2;
+    uint64_t* tempty = tfull + NBUF;
+    uint64_t* xready = tempty + NBUF;
     uint64_t* done = xready + 2;
     uint32_t* tmem_word = reinterpret_cast<uint32_t*>(done + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_word + 1);
@@ -148,11 +152,11 @@ __global__ void __launch_bounds__(256, 1)
             mbar_init(&ready[i], 2);
             mbar_init(&empty[i], 1);
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < NBUF; ++i) {
             mbar_init(&tfull[i], 1);
-            mbar_init(&tempty[i], 4);
-            mbar_init(&xready[i], 4);
+            mbar_init(&tempty[i], G::NEPI);
         }
+        for (int i = 0; i < 2; ++i) mbar_init(&xready[i], G::NEPI);
         mbar_init(done, 1);
         *abort_flag = 0;
         fence_mbar_init();
@@ -162,13 +166,16 @@ __global__ void __launch_bounds__(256, 1)
         tmem_relinquish();
     }
 
-    // the Toeplitz operand: B[(g, chunk c)][n_col][e] for n_col = half * N1 + j' * 16 + n
+    // The Toeplitz operand B[(g, chunk c)][row][e], K-major, rows = half * N1 + within:
+    // within = ch * 8 J + j' * 8 + n' holds output column n = 8 ch + n' of filter row
+    // g J + j', so each epilogue warp (column half ch) reads 8 J consecutive accumulator
+    // columns.
     const float* taps = a.taps_dev ? static_cast<const float*>(a.taps_dev) : tp.w;
-    float wmax = 0.f;
-    for (int i = 0; i < K * K; ++i) wmax = fmaxf(wmax, fabsf(taps[i]));
     float scale = 1.f, inv_scale = 1.f;
     if constexpr (std::is_same<Tin, __half>::value) {
         // f16 taps: a power of two that puts the largest tap in [2^13, 2^14)
+        float wmax = 0.f;
+        for (int i = 0; i < K * K; ++i) wmax = fmaxf(wmax, fabsf(taps[i]));
         if (wmax > 0.f) {
             int e;
             frexpf(wmax, &e);
@@ -179,14 +186,15 @@ __global__ void __launch_bounds__(256, 1)
     constexpr int BELEMS = G::G * G::KCH * G::N2 * G::CE;
     for (int idx = tid; idx < BELEMS; idx += blockDim.x) {
         const int e = idx % G::CE;
-        const int ncol = (idx / G::CE) % G::N2;
+        const int row = (idx / G::CE) % G::N2;
         const int gc = idx / (G::CE * G::N2);          // g * KCH + c
         const int g = gc / G::KCH, c = gc % G::KCH;
         const int k = c * G::CE + e;
-        const int half = ncol / G::N1, jj = (ncol % G::N1) / 16, n = ncol % 16;
+        const int half = row / G::N1, within = row % G::N1;
+        const int ch = within / (8 * J), jj = (within % (8 * J)) / 8, n = 8 * ch + within % 8;
         const int j = g * J + jj, i = k - n - (8 - R);
         const float w = (j < K && i >= 0 && i < K) ? taps[j * K + i] : 0.f;
-        uint8_t* dst = bmat + gc * G::LBO_B + ncol * 16;
+        uint8_t* dst = bmat + gc * G::LBO_B + row * 16;
         if constexpr (G::F32) {
             const uint32_t hi = tf32_part(w);
             const uint32_t lo = tf32_part(w - __uint_as_float(hi));
@@ -242,9 +250,8 @@ __global__ void __launch_bounds__(256, 1)
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issue
         if (lane == 0) {
-            const uint32_t idesc2 = umma_idesc(G::F32 ? UMMA_TF32 : (std::is_same<Tin, __half>::value ? UMMA_F16 : UMMA_BF16),
-                                               128, G::N2);
-            const uint32_t idesc1 = umma_idesc(UMMA_TF32, 128, G::N1);
+            constexpr uint32_t fmt = G::F32 ? UMMA_TF32 : (std::is_same<Tin, __half>::value ? UMMA_F16 : UMMA_BF16);
+            const uint32_t idesc = umma_idesc(fmt, 128, G::N1);
             const uint32_t a_hi_s = smem_u32(a_hi), a_lo_s = smem_u32(a_lo), b_s = smem_u32(bmat);
             uint32_t p = 0, q = 0;
             bool ok = true;
@@ -255,10 +262,13 @@ __global__ void __launch_bounds__(256, 1)
                 for (int b = 0; b < nbu; ++b, ++q) {
                     const uint32_t pn = p + b + 1;
                     if (!mbar_wait(&ready[pn % S], (pn / S) & 1, a.status)) { ok = false; break; }
-                    const int buf = q & 1;
-                    if (q >= 2 && !mbar_wait(&tempty[buf], ((q / 2) - 1) & 1, a.status)) { ok = false; break; }
+                    const int buf = q % NBUF;
+                    if (q >= (uint32_t)NBUF && !mbar_wait(&tempty[buf], ((q / NBUF) - 1) & 1, a.status)) {
+                        ok = false;
+                        break;
+                    }
                     tc_fence_after();
-                    const uint32_t d = tmem_base + buf * G::N2;
+                    const uint32_t d = tmem_base + buf * G::N1;
 #pragma unroll
                     for (int g = 0; g < G::G; ++g) {
 #pragma unroll
@@ -267,14 +277,19 @@ __global__ void __launch_bounds__(256, 1)
                             const int chunk0 = G::F32 ? (ks % 2) * 2 : 0;
                             const uint32_t slot = (p + sidx) % S;
                             const uint32_t aoff = slot * G::SLAB + chunk0 * G::LBO_A + g * J * 16;
-                            const uint64_t bdesc = umma_smem_desc(b_s + (g * G::KCH + ks * 2) * G::LBO_B, G::LBO_B, 128);
-                            const uint64_t adesc = umma_smem_desc(a_hi_s + aoff, G::LBO_A, 128);
+                            const uint32_t boff = b_s + (g * G::KCH + ks * 2) * G::LBO_B;
+                            const uint64_t b_hi = umma_smem_desc(boff, G::LBO_B, 128);
+                            const uint64_t b_lo = umma_smem_desc(boff + G::N1 * 16, G::LBO_B, 128);
+                            const uint64_t a_h = umma_smem_desc(a_hi_s + aoff, G::LBO_A, 128);
                             const uint32_t acc = (g | ks) != 0;
                             if constexpr (G::F32) {
-                                umma_tf32(d, adesc, bdesc, idesc2, acc);
-                                umma_tf32(d, umma_smem_desc(a_lo_s + aoff, G::LBO_A, 128), bdesc, idesc1, 1u);
+                                const uint64_t a_l = umma_smem_desc(a_lo_s + aoff, G::LBO_A, 128);
+                                umma_tf32(d, a_h, b_hi, idesc, acc);
+                                umma_tf32(d, a_h, b_lo, idesc, 1u);
+                                umma_tf32(d, a_l, b_hi, idesc, 1u);
                             } else {
-                                umma_f16(d, adesc, bdesc, idesc2, acc);
+                                umma_f16(d, a_h, b_hi, idesc, acc);
+                                umma_f16(d, a_h, b_lo, idesc, 1u);
                             }
                         }
                     }
@@ -358,7 +373,8 @@ __global__ void __launch_bounds__(256, 1)
         }
     } else {
         // ------------------------------------------------------------ epilogue
-        const int eq = warp - 4;                 // TMEM lane quarter
+        const int ew = warp - 4;                 // epilogue warp 0..7
+        const int eq = ew & 3, ch = ew >> 2;     // TMEM lane quarter, column half
         const int m = 32 * eq + lane;            // accumulator row of this thread
         Tout* out = static_cast<Tout*>(a.out);
         uint32_t q = 0;
@@ -367,66 +383,59 @@ __global__ void __launch_bounds__(256, 1)
             int x0, y0, nbu;
             unit_geo(u, x0, y0, nbu);
             for (int b = 0; b < nbu; ++b, ++q) {
-                const int buf = q & 1;
-                if (!warp_wait(&tfull[buf], (q / 2) & 1, a.status)) { ok = false; break; }
+                const int buf = q % NBUF, xb = q & 1;
+                if (!warp_wait(&tfull[buf], (q / NBUF) & 1, a.status)) { ok = false; break; }
                 tc_fence_after();
-                float acc[16];
-                float* xw = xch + (buf * 4 + eq) * G::NT * 16;
-                const uint32_t trow = tmem_base + ((uint32_t)(32 * eq) << 16) + buf * G::N2;
-#pragma unroll
-                for (int jj = 0; jj < J; ++jj) {
-                    float hh[16], hl[16];
-                    tmem_ld16x2(trow + jj * 16, trow + G::N1 + jj * 16, hh, hl);
-                    if (jj == 0) {
-#pragma unroll
-                        for (int n = 0; n < 16; ++n) acc[n] = hh[n] + hl[n];
-                    } else {
-                        float v[16];
-#pragma unroll
-                        for (int n = 0; n < 16; ++n) v[n] = hh[n] + hl[n];
-                        if (lane < jj) {
-                            float4* dst = reinterpret_cast<float4*>(xw + (jj * (jj - 1) / 2 + lane) * 16);
-#pragma unroll
-                            for (int n = 0; n < 4; ++n) dst[n] = make_float4(v[4 * n], v[4 * n + 1], v[4 * n + 2], v[4 * n + 3]);
-                        }
-                        const bool mine = lane + jj < 32;
-#pragma unroll
-                        for (int n = 0; n < 16; ++n) {
-                            const float t = __shfl_down_sync(0xffffffffu, v[n], jj);
-                            if (mine) acc[n] += t;
-                        }
-                    }
-                }
+                float v[8 * J];
+                tmem_ld8xJ<J>(tmem_base + ((uint32_t)(32 * eq) << 16) + buf * G::N1 + ch * 8 * J, v);
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) {
-                    mbar_arrive1(&tempty[buf]);
-                    mbar_arrive1(&xready[buf]);
+                if (lane == 0) mbar_arrive1(&tempty[buf]);
+                float acc[8];
+#pragma unroll
+                for (int n = 0; n < 8; ++n) acc[n] = v[n];
+                float* xw = xch + (xb * G::NEPI + ew) * G::NT * 8;
+#pragma unroll
+                for (int jj = 1; jj < J; ++jj) {
+                    if (lane < jj) {   // rows the warp of the next lane quarter needs
+                        float4* dst = reinterpret_cast<float4*>(xw + (jj * (jj - 1) / 2 + lane) * 8);
+                        dst[0] = make_float4(v[8 * jj], v[8 * jj + 1], v[8 * jj + 2], v[8 * jj + 3]);
+                        dst[1] = make_float4(v[8 * jj + 4], v[8 * jj + 5], v[8 * jj + 6], v[8 * jj + 7]);
+                    }
+                    const bool mine = lane + jj < 32;
+#pragma unroll
+                    for (int n = 0; n < 8; ++n) {
+                        const float t = __shfl_down_sync(0xffffffffu, v[8 * jj + n], jj);
+                        if (mine) acc[n] += t;
+                    }
                 }
-                if (!warp_wait(&xready[buf], (q / 2) & 1, a.status)) { ok = false; break; }
-                if (eq < 3) {
-                    const float* xn = xch + (buf * 4 + eq + 1) * G::NT * 16;
+                __syncwarp();
+                if (lane == 0) mbar_arrive1(&xready[xb]);
+                if (!warp_wait(&xready[xb], (q / 2) & 1, a.status)) { ok = false; break; }
+                if (eq < 3) {   // rows m + j' past this quarter: the next quarter's first lanes
+                    const float* xn = xch + (xb * G::NEPI + ew + 1) * G::NT * 8;
 #pragma unroll
                     for (int jj = 1; jj < J; ++jj) {
                         if (lane + jj >= 32) {
-                            const float4* src = reinterpret_cast<const float4*>(xn + (jj * (jj - 1) / 2 + lane + jj - 32) * 16);
-#pragma unroll
-                            for (int n = 0; n < 4; ++n) {
-                                const float4 t = src[n];
-                                acc[4 * n] += t.x;
-                                acc[4 * n + 1] += t.y;
-                                acc[4 * n + 2] += t.z;
-                                acc[4 * n + 3] += t.w;
-                            }
+                            const float4* src = reinterpret_cast<const float4*>(xn + (jj * (jj - 1) / 2 + lane + jj - 32) * 8);
+                            const float4 t0 = src[0], t1 = src[1];
+                            acc[0] += t0.x;
+                            acc[1] += t0.y;
+                            acc[2] += t0.z;
+                            acc[3] += t0.w;
+                            acc[4] += t1.x;
+                            acc[5] += t1.y;
+                            acc[6] += t1.z;
+                            acc[7] += t1.w;
                         }
                     }
                 }
                 if constexpr (std::is_same<Tin, __half>::value) {
 #pragma unroll
-                    for (int n = 0; n < 16; ++n) acc[n] *= inv_scale;
+                    for (int n = 0; n < 8; ++n) acc[n] *= inv_scale;
                 }
-                const int gy = y0 + m, gx = x0 + 16 * b;
-                if (m < G::BH && gy < H) store_block_row<Tout, 16>(out, a.out_pitch, gx, gy, W, H, a.vec_out, acc);
+                const int gy = y0 + m, gx = x0 + 16 * b + 8 * ch;
+                if (m < G::BH && gy < H) store_block_row<Tout, 8>(out, a.out_pitch, gx, gy, W, H, a.vec_out, acc);
             }
         }
         if (!ok) *abort_flag = 1;
@@ -446,7 +455,7 @@ imcl_status launch_conv_tc(const ConvCall& c, const imcl_variant& v, cudaStream_
     if (c.kw != K || c.kh != K) return fail(IMCL_ERR_UNSUPPORTED, "tensor-core conv2d: filter side mismatch");
     if ((reinterpret_cast<uintptr_t>(c.in) & 15) || (c.in_pitch_b & 15))
         return fail(IMCL_ERR_ALIGN, "tensor-core conv2d: TMA staging needs a 16-byte aligned input and pitch");
-    const int nb = v.bx > 0 ? v.bx : 16;
+    const int nb = v.bx > 0 ? v.bx : 8;
     if (nb > 64) return fail(IMCL_ERR_UNSUPPORTED, "tensor-core conv2d: at most 64 column blocks per unit");
     // at least half of the SM's shared memory, so one CTA (and one tensor-memory
     // allocation of 512 columns) per SM
@@ -471,7 +480,7 @@ imcl_status launch_conv_tc(const ConvCall& c, const imcl_variant& v, cudaStream_
     if (c.taps_mem == IMCL_MEM_HOST)
         for (int i = 0; i < K * K; ++i) tp.w[i] = static_cast<const float*>(c.taps)[i];
     const int grid = ta.units < c.dev->sm_count ? ta.units : c.dev->sm_count;
-    kfn<<<grid, 256, smem, s>>>(ta, tp, tmap);
+    kfn<<<grid, G::THREADS, smem, s>>>(ta, tp, tmap);
     return cuda_fail(cudaGetLastError(), "tensor-core conv2d launch");
 }
 
@@ -479,7 +488,7 @@ template <typename Tin, typename Tout>
 static ConvEntry tc_entry() {
     imcl_variant v{};
     v.kind = IMCL_KIND_TENSOR;
-    v.bx = 16;   // 16-column blocks per work unit
+    v.bx = 8;    // 16-column blocks per work unit
     v.by = 1;
     v.px = 16;
     v.py = TcGeo<Tin, IMCL_TC_K>::BH;

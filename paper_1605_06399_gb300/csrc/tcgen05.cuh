@@ -114,4 +114,71 @@ __device__ __forceinline__ void tmem_ld16x2(uint32_t taddr0, uint32_t taddr1, fl
     }
 }
 
+// J loads of 8 consecutive 32-bit columns (at taddr + 8 j, j < J, J in 5..8) of the
+// warp's 32 lanes and the wait for all of them, in one asm statement: v[8 j + c] is
+// column 8 j + c of lane base + t for thread t.
+template <int J>
+__device__ __forceinline__ void tmem_ld8xJ(uint32_t taddr, float* v) {
+    static_assert(J >= 5 && J <= 8, "5..8 column groups");
+    uint32_t r[64];
+#define IMCL_O8(b) "=r"(r[b]), "=r"(r[b + 1]), "=r"(r[b + 2]), "=r"(r[b + 3]), "=r"(r[b + 4]), "=r"(r[b + 5]), \
+                   "=r"(r[b + 6]), "=r"(r[b + 7])
+    if constexpr (J == 5) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%40];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%41];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%42];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24, %25, %26, %27, %28, %29, %30, %31}, [%43];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%32, %33, %34, %35, %36, %37, %38, %39}, [%44];\n\t"
+            "tcgen05.wait::ld.sync.aligned;"
+            : IMCL_O8(0), IMCL_O8(8), IMCL_O8(16), IMCL_O8(24), IMCL_O8(32)
+            : "r"(taddr), "r"(taddr + 8), "r"(taddr + 16), "r"(taddr + 24), "r"(taddr + 32)
+            : "memory");
+    } else if constexpr (J == 6) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%48];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%49];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%50];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24, %25, %26, %27, %28, %29, %30, %31}, [%51];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%32, %33, %34, %35, %36, %37, %38, %39}, [%52];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%40, %41, %42, %43, %44, %45, %46, %47}, [%53];\n\t"
+            "tcgen05.wait::ld.sync.aligned;"
+            : IMCL_O8(0), IMCL_O8(8), IMCL_O8(16), IMCL_O8(24), IMCL_O8(32), IMCL_O8(40)
+            : "r"(taddr), "r"(taddr + 8), "r"(taddr + 16), "r"(taddr + 24), "r"(taddr + 32), "r"(taddr + 40)
+            : "memory");
+    } else if constexpr (J == 7) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%56];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%57];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%58];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24, %25, %26, %27, %28, %29, %30, %31}, [%59];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%32, %33, %34, %35, %36, %37, %38, %39}, [%60];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%40, %41, %42, %43, %44, %45, %46, %47}, [%61];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%48, %49, %50, %51, %52, %53, %54, %55}, [%62];\n\t"
+            "tcgen05.wait::ld.sync.aligned;"
+            : IMCL_O8(0), IMCL_O8(8), IMCL_O8(16), IMCL_O8(24), IMCL_O8(32), IMCL_O8(40), IMCL_O8(48)
+            : "r"(taddr), "r"(taddr + 8), "r"(taddr + 16), "r"(taddr + 24), "r"(taddr + 32), "r"(taddr + 40),
+              "r"(taddr + 48)
+            : "memory");
+    } else {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%64];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%65];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%66];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24, %25, %26, %27, %28, %29, %30, %31}, [%67];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%32, %33, %34, %35, %36, %37, %38, %39}, [%68];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%40, %41, %42, %43, %44, %45, %46, %47}, [%69];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%48, %49, %50, %51, %52, %53, %54, %55}, [%70];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%56, %57, %58, %59, %60, %61, %62, %63}, [%71];\n\t"
+            "tcgen05.wait::ld.sync.aligned;"
+            : IMCL_O8(0), IMCL_O8(8), IMCL_O8(16), IMCL_O8(24), IMCL_O8(32), IMCL_O8(40), IMCL_O8(48), IMCL_O8(56)
+            : "r"(taddr), "r"(taddr + 8), "r"(taddr + 16), "r"(taddr + 24), "r"(taddr + 32), "r"(taddr + 40),
+              "r"(taddr + 48), "r"(taddr + 56)
+            : "memory");
+    }
+#undef IMCL_O8
+#pragma unroll
+    for (int i = 0; i < 8 * J; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 }  // namespace imcl

@@ -111,7 +111,7 @@ std::vector<imcl_variant> expand_shapes(const std::vector<imcl_variant>& base) {
     for (const imcl_variant& b : base) {
         if (b.kind == IMCL_KIND_PLAIN) { out.push_back(b); continue; }
         if (b.kind == IMCL_KIND_TENSOR) {   // work-unit widths (16-column blocks)
-            for (int nb : {16, 8, 32, 4}) {
+            for (int nb : {8, 4, 16, 32}) {
                 imcl_variant v = b;
                 v.bx = nb;
                 out.push_back(v);
