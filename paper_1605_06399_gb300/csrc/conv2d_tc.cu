@@ -32,12 +32,14 @@
 //
 // Pipeline (one persistent CTA per SM, 384 threads, work units = a band of 129 - J
 // output rows x a segment of 16 NB columns):
-//   warp 0       TMA producer: 16-column slabs of the 128 + J staged rows, one 2D box
-//                per 16-byte chunk column, into a ring of S slabs (zero fill outside);
+//   warp 0       TMA producer: 16-column slabs of the 128 + J staged rows, one row-major
+//                2D box each, into a ring of eight staging slots (zero fill outside;
+//                the ring is deep because a box takes a few microseconds to land);
 //   warp 1       allocates the tensor memory and issues the MMAs (one thread): block b
-//                of a unit reads slabs b and b + 1 (the 32-column K window);
-//   warps 2-3    converters: apply the boundary rule to slabs that leave the image and,
-//                for f32, write the tf32 high and low parts;
+//                of a unit reads operand slabs b and b + 1 (the 32-column K window);
+//   warps 2-3    converters: copy a staging slot into the chunk-major operand layout of
+//                the MMAs, applying the boundary rule outside the image and, for f32,
+//                writing the tf32 high and low parts;
 //   warps 4-11   epilogue, two warps per tensor-memory lane quarter (8 output columns
 //                each): one load of all J column groups, shifted sums, global stores.
 //                The accumulator has four buffers, so the MMAs of the next blocks
@@ -70,14 +72,19 @@ struct TcGeo {
     static constexpr int ARP = (AR + 7) / 8 * 8;   // rows per chunk column (whole core matrices)
     static constexpr int CE = 16 / (int)sizeof(Tin);   // elements per 16-byte chunk
     static constexpr int CPS = 16 / CE;                // chunk columns per 16-column slab
-    static constexpr int LBO_A = ARP * 16;             // bytes between chunk columns
+    // chunk columns are 2 (f32) or 4 (16-bit) rows more than whole core matrices apart, so
+    // the converters' 16-byte stores of neighbouring rows and chunks fall in distinct banks
+    static constexpr int PADR = F32 ? 2 : 4;
+    static constexpr int LBO_A = (ARP + PADR) * 16;    // bytes between chunk columns
     static constexpr int SLAB = CPS * LBO_A;           // bytes of one slab (one operand copy)
     static constexpr int KCH = 32 / CE;                // chunks of the 32-element K window
     static constexpr int KSTEP = F32 ? 8 : 16;         // K of one MMA
     static constexpr int NKS = 32 / KSTEP;             // MMAs along K per group and operand pair
     static constexpr int LBO_B = N2 * 16;
     static constexpr int BBYTES = G * KCH * LBO_B;
-    static constexpr int S = F32 ? 6 : 8;              // slab ring depth
+    static constexpr int S = 4;                        // operand slab ring depth
+    static constexpr int SS = 8;                       // staging ring depth: TMA boxes in flight
+    static constexpr int STAGE = (AR * 16 * (int)sizeof(Tin) + 127) / 128 * 128;
     static constexpr int NCOPY = F32 ? 2 : 1;          // hi (and lo) copies of a slab
     static constexpr int NBUF = 4;                     // accumulator buffers
     static constexpr int NEPI = 8;                     // epilogue warps
@@ -88,12 +95,14 @@ struct TcGeo {
     static_assert(G * J >= K && N1 <= 256 && NBUF * N1 <= TMEM_COLS, "tensor tile shape");
     static_assert(R <= 7, "the 32-column window holds 16 outputs' taps for R <= 7");
     // shared-memory layout (bytes from the 1024-aligned base)
-    static constexpr int OFF_A = 0;
+    static constexpr int OFF_STAGE = 0;
+    static constexpr int OFF_A = OFF_STAGE + SS * STAGE;
     static constexpr int OFF_B = OFF_A + NCOPY * S * SLAB;
     static constexpr int OFF_X = OFF_B + BBYTES;
     static constexpr int OFF_BAR = OFF_X + XBYTES;
-    static constexpr int NBAR = 3 * S + 2 * NBUF + 2 + 1;   // full, ready, empty; tfull, tempty; xready; done
+    static constexpr int NBAR = 2 * SS + 2 * S + 2 * NBUF + 2 + 1;   // sfull, sempty; ready, empty; tfull, tempty; xready; done
     static constexpr int SMEM = OFF_BAR + NBAR * 8 + 16 + 1024;
+    static_assert(SMEM <= 232448, "shared memory per CTA");
 };
 
 struct TcArgs {
@@ -131,15 +140,17 @@ __global__ void __launch_bounds__(TcGeo<Tin, K>::THREADS, 1)
     const ConvArgs& a = ta.a;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
+    uint8_t* stage = smem + G::OFF_STAGE;
     uint8_t* a_hi = smem + G::OFF_A;
     uint8_t* a_lo = smem + G::OFF_A + S * G::SLAB;   // f32 only
     uint8_t* bmat = smem + G::OFF_B;
     float* xch = reinterpret_cast<float*>(smem + G::OFF_X);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + G::OFF_BAR);
-    uint64_t* full = bars;
-    uint64_t* ready = bars + S;
-    uint64_t* empty = bars + 2 * S;
-    uint64_t* tfull = bars + 3 * S;
+    uint64_t* sfull = bars;                 // a staging slot holds its TMA box
+    uint64_t* sempty = sfull + G::SS;       // the converters have read it
+    uint64_t* ready = sempty + G::SS;       // an operand slab is written
+    uint64_t* empty = ready + S;            // the MMAs reading an operand slab have completed
+    uint64_t* tfull = empty + S;
     uint64_t* tempty = tfull + NBUF;
     uint64_t* xready = tempty + NBUF;
     uint64_t* done = xready + 2;
@@ -147,8 +158,11 @@ __global__ void __launch_bounds__(TcGeo<Tin, K>::THREADS, 1)
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_word + 1);
 
     if (tid == 0) {
+        for (int i = 0; i < G::SS; ++i) {
+            mbar_init(&sfull[i], 1);
+            mbar_init(&sempty[i], 2);
+        }
         for (int i = 0; i < S; ++i) {
-            mbar_init(&full[i], 1);
             mbar_init(&ready[i], 2);
             mbar_init(&empty[i], 1);
         }
@@ -231,21 +245,19 @@ __global__ void __launch_bounds__(TcGeo<Tin, K>::THREADS, 1)
                 int x0, y0, nbu;
                 unit_geo(u, x0, y0, nbu);
                 for (int sl = 0; sl <= nbu; ++sl, ++p) {
-                    const int slot = p % S;
-                    if (p >= (uint32_t)S && !mbar_wait(&empty[slot], ((p / S) - 1) & 1, a.status)) {
+                    const int slot = p % G::SS;
+                    if (p >= (uint32_t)G::SS && !mbar_wait(&sempty[slot], ((p / G::SS) - 1) & 1, a.status)) {
                         *abort_flag = 1;
                         break;
                     }
-                    mbar_arrive_expect_tx(&full[slot], G::CPS * G::AR * 16);
-                    const int xs = x0 - 8 + 16 * sl;
-#pragma unroll
-                    for (int c = 0; c < G::CPS; ++c)
-                        tma_load_2d(a_hi + slot * G::SLAB + c * G::LBO_A, &tmap, xs + c * G::CE, y0 - R, &full[slot]);
+                    // one row-major box: 16 columns x AR rows
+                    mbar_arrive_expect_tx(&sfull[slot], G::AR * 16 * (int)sizeof(Tin));
+                    tma_load_2d(stage + slot * G::STAGE, &tmap, x0 - 8 + 16 * sl, y0 - R, &sfull[slot]);
                 }
             }
             // wait (bounded) for the copies still in flight
-            const uint32_t first = p > (uint32_t)S ? p - S : 0;
-            for (uint32_t q = first; q < p; ++q) mbar_wait(&full[q % S], (q / S) & 1, a.status);
+            const uint32_t first = p > (uint32_t)G::SS ? p - G::SS : 0;
+            for (uint32_t q = first; q < p; ++q) mbar_wait(&sfull[q % G::SS], (q / G::SS) & 1, a.status);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issue
@@ -306,6 +318,8 @@ __global__ void __launch_bounds__(TcGeo<Tin, K>::THREADS, 1)
         }
     } else if (warp < 4) {
         // ------------------------------------------------------------ converters
+        // staging slot (row-major, 16 elements a row) -> operand slab (chunk-major), with
+        // the boundary rule on pixels outside the image and, for f32, the tf32 split
         const int ct = tid - 64;
         const Tin bv = border_pixel<Tin>(a);
         const Tin* in = static_cast<const Tin*>(a.in);
@@ -314,61 +328,64 @@ __global__ void __launch_bounds__(TcGeo<Tin, K>::THREADS, 1)
             int x0, y0, nbu;
             unit_geo(u, x0, y0, nbu);
             for (int sl = 0; sl <= nbu; ++sl, ++p) {
-                const int slot = p % S;
-                if (!warp_wait(&full[slot], (p / S) & 1, a.status)) {
+                const int slot = p % S, ss = p % G::SS;
+                if (!warp_wait(&sfull[ss], (p / G::SS) & 1, a.status) ||
+                    (p >= (uint32_t)S && !warp_wait(&empty[slot], ((p / S) - 1) & 1, a.status))) {
                     *abort_flag = 1;
                     break;
                 }
                 const int xs = x0 - 8 + 16 * sl, ys = y0 - R;
                 const bool inside = xs >= 0 && xs + 16 <= W && ys >= 0 && ys + G::AR <= H;
+                const uint8_t* st = stage + ss * G::STAGE;
                 uint8_t* hi = a_hi + slot * G::SLAB;
-                if constexpr (G::F32) {
-                    uint8_t* lo = a_lo + slot * G::SLAB;
-                    for (int idx = ct; idx < G::CPS * G::AR; idx += 64) {
-                        const int c = idx / G::AR, r = idx % G::AR;
-                        float4 v = *reinterpret_cast<const float4*>(hi + slab_off<G>(c, r));
+                // four 16-byte chunks per thread in flight: loads first, then the conversions
+                constexpr int TOT = G::CPS * G::AR;
+                for (int i0 = ct; i0 < TOT; i0 += 4 * 64) {
+                    uint4 raw[4];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        if (i0 + 64 * t < TOT) raw[t] = *reinterpret_cast<const uint4*>(st + (i0 + 64 * t) * 16);
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int idx = i0 + 64 * t;
+                        if (idx >= TOT) break;
+                        const int r = idx / G::CPS, c = idx % G::CPS;
                         if (!inside) {
-                            float* e = reinterpret_cast<float*>(&v);
+                            Tin* e = reinterpret_cast<Tin*>(&raw[t]);
                             const int gy = ys + r;
 #pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                const int gx = xs + 4 * c + q;
+                            for (int q = 0; q < G::CE; ++q) {
+                                const int gx = xs + G::CE * c + q;
                                 if (gx < 0 || gx >= W || gy < 0 || gy >= H)
                                     e[q] = a.border == IMCL_BORDER_CONSTANT
                                                ? bv
                                                : in[(long long)clampi(gy, 0, H - 1) * a.in_pitch + clampi(gx, 0, W - 1)];
                             }
                         }
-                        uint4 h, l;
-                        h.x = tf32_part(v.x);
-                        h.y = tf32_part(v.y);
-                        h.z = tf32_part(v.z);
-                        h.w = tf32_part(v.w);
-                        l.x = tf32_part(v.x - __uint_as_float(h.x));
-                        l.y = tf32_part(v.y - __uint_as_float(h.y));
-                        l.z = tf32_part(v.z - __uint_as_float(h.z));
-                        l.w = tf32_part(v.w - __uint_as_float(h.w));
-                        *reinterpret_cast<uint4*>(hi + slab_off<G>(c, r)) = h;
-                        *reinterpret_cast<uint4*>(lo + slab_off<G>(c, r)) = l;
-                    }
-                } else if (!inside) {
-                    for (int idx = ct; idx < G::CPS * G::AR; idx += 64) {
-                        const int c = idx / G::AR, r = idx % G::AR;
-                        Tin* e = reinterpret_cast<Tin*>(hi + slab_off<G>(c, r));
-                        const int gy = ys + r;
-#pragma unroll
-                        for (int q = 0; q < G::CE; ++q) {
-                            const int gx = xs + G::CE * c + q;
-                            if (gx < 0 || gx >= W || gy < 0 || gy >= H)
-                                e[q] = a.border == IMCL_BORDER_CONSTANT
-                                           ? bv
-                                           : in[(long long)clampi(gy, 0, H - 1) * a.in_pitch + clampi(gx, 0, W - 1)];
+                        if constexpr (G::F32) {
+                            const uint4 v = raw[t];
+                            uint4 h, l;
+                            h.x = tf32_part(__uint_as_float(v.x));
+                            h.y = tf32_part(__uint_as_float(v.y));
+                            h.z = tf32_part(__uint_as_float(v.z));
+                            h.w = tf32_part(__uint_as_float(v.w));
+                            l.x = tf32_part(__uint_as_float(v.x) - __uint_as_float(h.x));
+                            l.y = tf32_part(__uint_as_float(v.y) - __uint_as_float(h.y));
+                            l.z = tf32_part(__uint_as_float(v.z) - __uint_as_float(h.z));
+                            l.w = tf32_part(__uint_as_float(v.w) - __uint_as_float(h.w));
+                            *reinterpret_cast<uint4*>(hi + slab_off<G>(c, r)) = h;
+                            *reinterpret_cast<uint4*>(a_lo + slot * G::SLAB + slab_off<G>(c, r)) = l;
+                        } else {
+                            *reinterpret_cast<uint4*>(hi + slab_off<G>(c, r)) = raw[t];
                         }
                     }
                 }
                 fence_proxy_async_smem();
                 __syncwarp();
-                if (lane == 0) mbar_arrive1(&ready[slot]);
+                if (lane == 0) {
+                    mbar_arrive1(&ready[slot]);
+                    mbar_arrive1(&sempty[ss]);
+                }
             }
         }
     } else {
@@ -466,7 +483,7 @@ imcl_status launch_conv_tc(const ConvCall& c, const imcl_variant& v, cudaStream_
     if (st != IMCL_OK) return st;
     CUtensorMap tmap;
     memset(&tmap, 0, sizeof tmap);
-    st = encode_tmap_2d(&tmap, c.in_dtype, c.in, c.W, c.H, c.in_pitch_b, G::CE, G::AR);
+    st = encode_tmap_2d(&tmap, c.in_dtype, c.in, c.W, c.H, c.in_pitch_b, 16, G::AR);   // one slab per box
     if (st != IMCL_OK) return st;
     TcArgs ta;
     ta.a = make_conv_args(c, v, 16, 16);
