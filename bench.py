@@ -445,7 +445,18 @@ def _entry(px, tuned_ms, plain_ms, bytes_px, flops_px, hbm_gbs, fp32_peak, varia
     return d
 
 
-def extra_stencils(hbm_gbs, fp32_peak, budget, imad_peak=None):
+def tc_mma_flops(k, dt, W, H):
+    """Flops the tensor-core conv2d variant issues as MMAs for a W x H image: per 128-row
+    tile and 16 output columns, two groups of J = (k+1)/2 filter rows, the 32-element K
+    window, M = 128, N = 16 J, and three (tf32 split) or two (16-bit taps split) products."""
+    J = (k + 1) // 2
+    bh = 129 - J
+    blocks = -(-H // bh) * -(-W // 16)
+    products = 3 if dt == "f32" else 2
+    return blocks * 2 * products * 2 * 128 * 16 * J * 32
+
+
+def extra_stencils(hbm_gbs, fp32_peak, budget, imad_peak=None, bf16_tflops=FALLBACK_BF16_TFS):
     """Tuned vs plain for the other workloads (inputs resident; L2 flushed between runs
     when a working set would fit in L2)."""
     import torch
@@ -485,8 +496,8 @@ def extra_stencils(hbm_gbs, fp32_peak, budget, imad_peak=None):
             out[f"sep_R{R}_8192_{ind}_{outd}"] = _entry(SIDE * SIDE, tt, tp, bpx, 4 * (2 * R + 1), hbm_gbs,
                                                         fp32_peak, res["variant"])
             del x, y, ws
-    del base
 
+    base_large = base
     # the paper's own benchmark shapes (§6): 4096^2 f32 separable 5x5 with the constant
     # border, and 8192^2 u8 non-separable 5x5 with the clamped border
     x = torch.from_numpy(synth.uniform_f32(g, 4096, 4096)).to(dev)
@@ -512,6 +523,37 @@ def extra_stencils(hbm_gbs, fp32_peak, budget, imad_peak=None):
         e["int_frac"] = e["int_tops"] / imad_peak
     out["paper_conv5x5_8192_u8_i32"] = e
     del x, y
+
+    # large filters, where the tensor-core (tcgen05 banded-Toeplitz) variant competes with
+    # the FP32-pipe ones: the tuned pick, and both families timed on the same launch
+    tensor_peak = {"f32": bf16_tflops * 0.5, "f16": bf16_tflops, "bf16": bf16_tflops}   # tf32 = 1/2 of bf16 (nominal)
+    for dt, od, k in (("f32", torch.float32, 13), ("f32", torch.float32, 15), ("bf16", torch.bfloat16, 11),
+                      ("bf16", torch.bfloat16, 15), ("f16", torch.float32, 13)):
+        x = synth.to_storage(base_large, dt).to(dev)
+        y = torch.empty((SIDE, SIDE), dtype=od, device=dev)
+        w = synth.normal_filter_l1(g, k)
+        prob = ops.problem(_abi.OP_CONV2D, dt, od, k, k, SIDE, SIDE)
+        res = ops.tune(prob, budget_s=budget, reps=3)
+        vs = ops.variants(prob)
+        tcv = [v for v in vs if v["kind"] == _abi.KIND_TENSOR][0]
+        tiled = [v for v in vs if v["kind"] == _abi.KIND_TILED][0]
+        tt = _median_ms(lambda: ops.conv2d(x, w, out=y), 7)
+        t_tc = min(_median_ms(lambda nb=nb: ops.conv2d(x, w, out=y, variant=dict(tcv, bx=nb)), 5) for nb in (4, 8))
+        t_fp = _median_ms(lambda: ops.conv2d(x, w, out=y, variant=tiled), 5)
+        bpx = x.element_size() + y.element_size()
+        e = _entry(SIDE * SIDE, tt, None, bpx, 2 * k * k, hbm_gbs, fp32_peak, res["variant"])
+        mma = tc_mma_flops(k, dt, SIDE, SIDE)
+        e["tensor_variant"] = {"ms": t_tc, "mpx_s": SIDE * SIDE / t_tc / 1e3,
+                               "mma_tflops": mma / (t_tc / 1e3) / 1e12,
+                               "mma_frac": mma / (t_tc / 1e3) / 1e12 / tensor_peak[dt],
+                               "mma_flops_per_launch": mma, "algorithmic_flops_per_launch": 2 * k * k * SIDE * SIDE,
+                               "peak": f"{'tf32' if dt == 'f32' else dt} tensor peak {tensor_peak[dt]:.0f} TFLOP/s "
+                                       "(measured bf16 x nominal ratio)"}
+        e["fp32_pipe_variant"] = {"ms": t_fp, "mpx_s": SIDE * SIDE / t_fp / 1e3, "variant": tiled}
+        e["tensor_speedup_vs_fp32_pipe"] = t_fp / t_tc
+        out[f"conv{k}x{k}_8192_{dt}_{str(od)[6:]}"] = e
+        del x, y
+    del base_large
 
     # Harris, 4096x4096 rectangles: forward tuned vs the two-kernel form, and the backward
     img, sx, sy, win, k = synth.workload_harris()
@@ -621,7 +663,7 @@ def run_ours(args):
     rank, world, local, pg = dist_setup(args.gpus)
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    hbm_gbs, _, sm_max_mhz, peak_src = measured_peaks()
+    hbm_gbs, bf16_tflops, sm_max_mhz, peak_src = measured_peaks()
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
     fp32_peak = n_sm * FP32_FMA_PER_SM_CLK * 2 * sm_max_mhz * 1e6 / 1e12   # TFLOP/s
@@ -837,7 +879,8 @@ def run_ours(args):
                 "paper": "about 1700 candidates and 2 hours per device and benchmark (compile-per-candidate)",
             }
     if not args.no_extras:
-        per_stencil.update(extra_stencils(hbm_gbs, fp32_peak, max(2.0, args.tune_budget / 4), probe["imad_tops"]))
+        per_stencil.update(extra_stencils(hbm_gbs, fp32_peak, max(2.0, args.tune_budget / 4), probe["imad_tops"],
+                                          bf16_tflops))
 
     gpu_outs = None
     cpu = None
