@@ -2,7 +2,7 @@
 
     python -m paper_1605_06399_gb300.profile_cases CASE [--variant JSON] [--reps N] ...
 
-CASE: conv (8192x8192 f32, --k), sep (8192x8192, --radius, --in, --out), harris
+CASE: conv (8192x8192, --k, --in, --out), sep (8192x8192, --radius, --in, --out), harris
 (4096x4096 rectangles), batch / batch_bwd (the 256-image ragged batch), conv_bwd,
 sep_bwd, harris_bwd.  No tuning runs, so the kernel launch sequence is fixed: one
 warm-up call, then --reps calls (the batch also times its 4 tile shapes at creation,
@@ -24,7 +24,8 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("case")
     ap.add_argument("--variant", default=None,
-                    help="variant as key=value pairs, e.g. kind=1,bx=32,by=8,px=4,py=8,load=2 "
+                    help="variant as key=value pairs, e.g. kind=1,bx=32,by=8,px=4,py=8,load=2 or "
+                         "kind=2,bx=8,px=16,py=123,load=2,filt=1 (the tensor-core conv2d, 11x11) "
                          "(default: the built-in choice)")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--k", type=int, default=11)
@@ -40,8 +41,8 @@ def main(argv=None):
     c = a.case
     if c in ("conv", "conv_bwd"):
         img, taps = synth.workload_conv_f32(a.k)
-        x = torch.from_numpy(img).to(dev)
-        y = torch.empty_like(x)
+        x = synth.to_storage(img, a.ind).to(dev)
+        y = torch.empty(x.shape, dtype=DT[a.outd], device=dev)
         g = torch.randn_like(x)
         fn = (lambda: ops.conv2d(x, taps, out=y, variant=v)) if c == "conv" else \
             (lambda: ops.conv2d_backward(g, x, taps))
