@@ -516,8 +516,9 @@ def extra_stencils(hbm_gbs, fp32_peak, budget, imad_peak=None, bf16_tflops=FALLB
     tt = _median_ms(lambda: ops.conv2d(x, w5, out=y), 7)
     tp = _median_ms(lambda: ops.conv2d(x, w5, out=y, variant=plain), 5)
     e = _entry(SIDE * SIDE, tt, tp, 5, 50, hbm_gbs, fp32_peak, res["variant"],
-               "50 integer ops per pixel (25 wrapping int32 multiply-adds); int_frac is against the measured "
-               "int32 multiply-add rate (imagecl_probe_imad), fp32_frac against the FP32 pipe")
+               "50 integer ops per pixel (25 multiply-adds); a tuned variant with unroll=3 (F32_EXACT) does them "
+               "as f32 FMAs, exact below 2^24 (fp32_frac is its pipe); int_frac is against the measured int32 "
+               "multiply-add rate (imagecl_probe_imad), the pipe of the integer-accumulating variants")
     if imad_peak:
         e["int_tops"] = 50 * SIDE * SIDE / (tt / 1e3) / 1e12
         e["int_frac"] = e["int_tops"] / imad_peak

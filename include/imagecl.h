@@ -83,8 +83,13 @@ typedef enum { IMCL_MAP_BLOCKED = 0, IMCL_MAP_INTERLEAVED = 1, IMCL_MAP_REGISTER
 /* Loop form of the tap loops.  PACKED (sepconv only) is unrolled like FULL, with each
  * multiply-add instruction doing two adjacent output pixels (f32x2 FMA): the
  * vectorisation that the paper leaves to the OpenCL runtime, as a tuning knob.  It gives
- * the same bits as FULL. */
-typedef enum { IMCL_UNROLL_NONE = 0, IMCL_UNROLL_FULL = 1, IMCL_UNROLL_PACKED = 2 } imcl_unroll;
+ * the same bits as FULL.  F32_EXACT (conv2d, u8 images, host taps) is unrolled like FULL
+ * and accumulates the integer taps and pixels with f32 FMAs: every partial sum is an
+ * integer of magnitude at most sum |w| * 255, exact in f32 while that is below 2^24, so
+ * the int32 result is bit-identical to integer accumulation; for larger taps the call
+ * runs the integer-accumulating form of the same tile. */
+typedef enum { IMCL_UNROLL_NONE = 0, IMCL_UNROLL_FULL = 1, IMCL_UNROLL_PACKED = 2,
+               IMCL_UNROLL_F32_EXACT = 3 } imcl_unroll;
 
 typedef struct {
     int32_t kind;       /* imcl_kind.  PLAIN: the untuned kernel (one pixel per thread,

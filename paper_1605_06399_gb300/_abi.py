@@ -29,7 +29,7 @@ KIND_PLAIN, KIND_TILED, KIND_TENSOR = 0, 1, 2
 LOAD_GLOBAL, LOAD_SMEM, LOAD_TMA = 0, 1, 2
 FILT_PARAM, FILT_SMEM = 0, 1
 MAP_BLOCKED, MAP_INTERLEAVED, MAP_REGISTER = 0, 1, 2
-UNROLL_NONE, UNROLL_FULL, UNROLL_PACKED = 0, 1, 2
+UNROLL_NONE, UNROLL_FULL, UNROLL_PACKED, UNROLL_F32_EXACT = 0, 1, 2, 3
 
 
 class Image(ctypes.Structure):

@@ -47,6 +47,8 @@ template <> __device__ __forceinline__ __half from_acc<__half>(float v) { return
 template <> __device__ __forceinline__ __nv_bfloat16 from_acc<__nv_bfloat16>(float v) {
     return __float2bfloat16_rn(v);
 }
+// integer images accumulated in f32 (exact integers below 2^24): the value is integral
+template <> __device__ __forceinline__ int32_t from_acc<int32_t>(float v) { return __float2int_rn(v); }
 template <typename T> __device__ __forceinline__ T from_acc_i(int32_t v);
 template <> __device__ __forceinline__ int32_t from_acc_i<int32_t>(int32_t v) { return v; }
 

@@ -64,11 +64,19 @@ __global__ void __launch_bounds__(256)
 }
 
 // ------------------------------------------------------------------ tiled kernel
-template <typename Tin, typename Tout, int K, int PX, int PY, int LOAD, int FILT, int MAP>
+// FACC: integer (u8) pixels and taps accumulated with f32 FMAs.  Every product and
+// partial sum is an integer of magnitude at most sum |w| * 255; while that stays below
+// 2^24 all of them are exact in f32, so the int32 result is bit-identical to integer
+// accumulation (the launcher checks the bound) at the FP32 pipe's rate, which is twice
+// the int32 multiply-add rate.
+template <typename Tin, bool FACC>
+using TiledAcc = typename std::conditional<FACC, float, typename AccOf<Tin>::type>::type;
+
+template <typename Tin, typename Tout, int K, int PX, int PY, int LOAD, int FILT, int MAP, bool FACC = false>
 __global__ void __launch_bounds__(256, 2)
-    k_conv2d_tiled(const ConvArgs a, const __grid_constant__ TapsParam<typename AccOf<Tin>::type, K * K> tp,
+    k_conv2d_tiled(const ConvArgs a, const __grid_constant__ TapsParam<TiledAcc<Tin, FACC>, K * K> tp,
                    const __grid_constant__ CUtensorMap tmap) {
-    using Acc = typename AccOf<Tin>::type;
+    using Acc = TiledAcc<Tin, FACC>;
     using G = TileGeo<Tin, K, PX>;
     constexpr int R = G::R;
     extern __shared__ __align__(128) uint8_t smem[];
@@ -232,10 +240,22 @@ imcl_status launch_conv_plain(const ConvCall& c, const imcl_variant& v, cudaStre
     return cuda_fail(cudaGetLastError(), "conv2d plain launch");
 }
 
-template <typename Tin, typename Tout, int K, int PX, int PY, int LOAD, int FILT, int MAP>
+template <typename Tin, typename Tout, int K, int PX, int PY, int LOAD, int FILT, int MAP, bool FACC = false>
 imcl_status launch_conv_tiled(const ConvCall& c, const imcl_variant& v, cudaStream_t s) {
-    using Acc = typename AccOf<Tin>::type;
+    using Acc = TiledAcc<Tin, FACC>;
     using G = TileGeo<Tin, K, PX>;
+    if constexpr (FACC) {
+        static_assert(std::is_same<Tin, uint8_t>::value, "f32 accumulation of integer taps: u8 images only");
+        // exact only while sum |w| * 255 < 2^24; otherwise the integer-accumulating twin
+        if (c.taps_mem != IMCL_MEM_HOST || c.kw != K || c.kh != K)
+            return fail(IMCL_ERR_UNSUPPORTED, "f32-accumulating u8 conv2d takes host taps of its side");
+        int64_t l1 = 0;
+        for (int i = 0; i < K * K; ++i) {
+            const int64_t w = static_cast<const int32_t*>(c.taps)[i];
+            l1 += w < 0 ? -w : w;
+        }
+        if (l1 * 255 >= (int64_t(1) << 24)) return launch_conv_tiled<Tin, Tout, K, PX, PY, LOAD, FILT, MAP, false>(c, v, s);
+    }
     const int bx = v.bx, by = v.by;
     const int nth = bx * by;
     if (bx <= 0 || by <= 0 || nth > 256 || nth % 32 != 0)
@@ -253,7 +273,7 @@ imcl_status launch_conv_tiled(const ConvCall& c, const imcl_variant& v, cudaStre
     const int smem = 128 + nstage * stage_bytes + (FILT == IMCL_FILT_SMEM ? K * K * (int)sizeof(Acc) : 0);
     if (smem > c.dev->max_smem_optin) return fail(IMCL_ERR_UNSUPPORTED, "tiled conv2d: tile too large for shared memory");
 
-    auto kfn = k_conv2d_tiled<Tin, Tout, K, PX, PY, LOAD, FILT, MAP>;
+    auto kfn = k_conv2d_tiled<Tin, Tout, K, PX, PY, LOAD, FILT, MAP, FACC>;
     imcl_status st = set_smem_limit((const void*)kfn, smem);
     if (st != IMCL_OK) return st;
     const int in_align = (LOAD == IMCL_LOAD_GLOBAL) ? G::VB * G::SZ : 16;
@@ -271,7 +291,11 @@ imcl_status launch_conv_tiled(const ConvCall& c, const imcl_variant& v, cudaStre
         if (st != IMCL_OK) return st;
     }
     TapsParam<Acc, K * K> tp;
-    fill_taps(tp, c);
+    if constexpr (FACC) {
+        for (int i = 0; i < K * K; ++i) tp.w[i] = (float)static_cast<const int32_t*>(c.taps)[i];
+    } else {
+        fill_taps(tp, c);
+    }
     int grid = ntiles;
     if (v.persistent || LOAD == IMCL_LOAD_TMA) {
         const int occ = cached_occupancy((const void*)kfn, nth, smem);
@@ -283,7 +307,7 @@ imcl_status launch_conv_tiled(const ConvCall& c, const imcl_variant& v, cudaStre
     return cuda_fail(cudaGetLastError(), "conv2d tiled launch");
 }
 
-template <typename Tin, typename Tout, int K, int PX, int PY, int LOAD, int FILT, int MAP>
+template <typename Tin, typename Tout, int K, int PX, int PY, int LOAD, int FILT, int MAP, bool FACC = false>
 inline ConvEntry conv_entry(int bx, int by, int persistent) {
     imcl_variant v{};
     v.kind = IMCL_KIND_TILED;
@@ -294,10 +318,10 @@ inline ConvEntry conv_entry(int bx, int by, int persistent) {
     v.load = LOAD;
     v.filt = FILT;
     v.map = MAP;
-    v.unroll = 1;
+    v.unroll = FACC ? IMCL_UNROLL_F32_EXACT : IMCL_UNROLL_FULL;
     v.persistent = persistent;
     return ConvEntry{DtypeOf<Tin>::v, DtypeOf<Tout>::v, K, v,
-                     &launch_conv_tiled<Tin, Tout, K, PX, PY, LOAD, FILT, MAP>};
+                     &launch_conv_tiled<Tin, Tout, K, PX, PY, LOAD, FILT, MAP, FACC>};
 }
 
 }  // namespace imcl

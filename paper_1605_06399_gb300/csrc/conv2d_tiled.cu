@@ -53,6 +53,9 @@ void IMCL_REG_NAME(std::vector<ConvEntry>& t) {
         t.push_back(conv_entry<float, float, K, 4, 4, TMA, PARAM, ILV>(32, 8, 1));
     }
 #elif IMCL_TILED_GROUP == 1
+    // f32 accumulation of the integer taps (exact below 2^24, else the integer twin runs)
+    t.push_back(conv_entry<uint8_t, int32_t, K, 4, 4, TMA, PARAM, BLK, true>(32, 8, 1));
+    t.push_back(conv_entry<uint8_t, int32_t, K, 4, 8, TMA, PARAM, BLK, true>(32, 4, 1));
     t.push_back(conv_entry<uint8_t, int32_t, K, 4, 4, TMA, PARAM, BLK>(32, 8, 1));
     t.push_back(conv_entry<uint8_t, int32_t, K, 4, 4, TMA, SFILT, BLK>(32, 8, 1));
     if constexpr (K <= 5) {

@@ -106,11 +106,34 @@ def test_workload_int3x3_bit_exact():
 
 
 def test_int_wraparound_matches_oracle():
+    """Taps far past the f32-exact bound: the F32_EXACT variants run their integer twin,
+    and every variant wraps like the oracle."""
     x = torch.full((20, 24), 255, dtype=torch.uint8)
     taps = np.full((15, 15), 2 ** 25, dtype=np.int32)   # 225 * 255 * 2^25 wraps int32
     ref = oracle.conv2d(x.numpy(), taps)
-    for v in [None, {"kind": _abi.KIND_PLAIN, "bx": 16, "by": 16}]:
-        assert np.array_equal(ops.conv2d(x.cuda(), taps, variant=v).cpu().numpy(), ref)
+    vs = [None] + ops.variants(ops.problem(_abi.OP_CONV2D, "u8", "i32", 15, 15, 24, 20))
+    assert any(v and v["unroll"] == _abi.UNROLL_F32_EXACT for v in vs)
+    for v in vs:
+        assert np.array_equal(ops.conv2d(padded(x), taps, variant=v).cpu().numpy(), ref), v
+
+
+@pytest.mark.parametrize("wval", [292, 293])
+def test_f32_exact_u8_at_the_bound(wval):
+    """225 taps of 292 keep sum |w| * 255 = 16,753,500 below 2^24 (f32 accumulation is
+    exact); 293 crosses it (16,810,875: the integer form runs).  Both bit-exact, on a
+    saturated image and on random pixels with mixed-sign taps."""
+    g = np.random.default_rng(wval)
+    prob = ops.problem(_abi.OP_CONV2D, "u8", "i32", 15, 15, 300, 130)
+    facc = [v for v in ops.variants(prob) if v["unroll"] == _abi.UNROLL_F32_EXACT]
+    assert facc
+    for x in (np.full((130, 300), 255, np.uint8), synth.uniform_u8(g, 130, 300)):
+        taps = (wval * np.where(g.random((15, 15)) < 0.5, -1, 1)).astype(np.int32)
+        if x[0, 0] == 255 and x.min() == 255:
+            taps = np.abs(taps)
+        ref = oracle.conv2d(x, taps)
+        for v in facc:
+            y = ops.conv2d(padded(torch.from_numpy(x)), taps, variant=v)
+            assert np.array_equal(y.cpu().numpy(), ref), (wval, v)
 
 
 @pytest.mark.parametrize("k", [5, 11])
