@@ -354,8 +354,11 @@ imcl_status imagecl_tune(const imcl_problem *problem, double budget_s, int32_t r
  * are checked against the PLAIN kernel and timed; a one-hidden-layer network (16 tanh
  * units) is fitted to their log times from the configuration's axes (one-hot per axis
  * value); the `n_confirm` untimed configurations it predicts fastest are then checked
- * and timed, and the fastest of all timed ones is cached as imagecl_tune would.
- * `report` (nullable) receives the counts, the model's fit and the search's wall time.
+ * and timed; then up to 8 further configurations drawn at random from the untimed ones
+ * are timed as a held-out check of the model (its prediction error on data it did not
+ * train on).  The fastest of all timed ones is cached as imagecl_tune would.
+ * `report` (nullable) receives the counts, the model's fit, its held-out error and the
+ * search's wall time.
  * Synchronises `stream`.
  */
 typedef struct {
@@ -365,6 +368,9 @@ typedef struct {
     int32_t valid;         /* timed configurations that launched and passed the check  */
     double model_rmse;     /* rms error of the fitted log time on the sampled points   */
     double seconds;        /* wall time of the search                                  */
+    int32_t holdout;       /* random untimed configurations timed after training       */
+    int32_t holdout_valid; /* of those, the ones that launched and passed the check    */
+    double holdout_rmse;   /* rms error of the predicted log time on the valid held-out */
 } imcl_tune_report;
 
 imcl_status imagecl_tune_model(const imcl_problem *problem, int32_t n_sample, int32_t n_confirm,

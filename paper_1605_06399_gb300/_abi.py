@@ -79,7 +79,8 @@ class BatchInfo(ctypes.Structure):
 
 class TuneReport(ctypes.Structure):
     _fields_ = [("candidates", c_int32), ("sampled", c_int32), ("confirmed", c_int32), ("valid", c_int32),
-                ("model_rmse", c_double), ("seconds", c_double)]
+                ("model_rmse", c_double), ("seconds", c_double), ("holdout", c_int32), ("holdout_valid", c_int32),
+                ("holdout_rmse", c_double)]
 
     def as_dict(self) -> dict:
         return {n: getattr(self, n) for n, _ in self._fields_}

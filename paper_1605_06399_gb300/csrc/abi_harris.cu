@@ -10,11 +10,15 @@ namespace imcl {
 // last row and column (tap (j, i) keeps its offset (i - wk/2, j - wk/2)).
 int harris_kernel_side(int wk) { return wk % 2 ? wk : wk + 1; }
 
+// The forward has its own kernels for the paper's 2x2 block (and the untuned kernel takes
+// any side): only even windows above 2 run as the next odd one.
+int harris_forward_side(int wk) { return wk == 2 ? 2 : harris_kernel_side(wk); }
+
 ConvCall harris_problem_call(const imcl_problem& p) {
     ConvCall c = problem_call(p);
     c.in_dtype = c.out_dtype = IMCL_F32;
     c.kh = p.kw;
-    c.kw = harris_kernel_side(p.kw);
+    c.kw = harris_forward_side(p.kw);
     return c;
 }
 
@@ -77,7 +81,7 @@ imcl_status harris_prepare(const imcl_image* in, const imcl_image* out, const fl
     c->H = in->height;
     c->in_pitch_b = in->pitch_bytes;
     c->out_pitch_b = out->pitch_bytes;
-    c->kw = harris_kernel_side(wk);
+    c->kw = harris_forward_side(wk);
     c->kh = wk;
     c->taps = sx;
     c->taps2 = sy;

@@ -40,6 +40,7 @@ imcl_status sep_prepare(const imcl_image* in, const imcl_image* out, const float
 imcl_status sep_run(const ConvCall& c, const imcl_variant* variant, cudaStream_t s);
 
 int harris_kernel_side(int wk);
+int harris_forward_side(int wk);
 ConvCall harris_problem_call(const imcl_problem& p);
 imcl_problem harris_problem(const ConvCall& c);
 std::vector<const ConvEntry*> harris_entries_for(int wk, int taps_mem);

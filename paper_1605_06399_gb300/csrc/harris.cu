@@ -41,6 +41,12 @@ const std::vector<ConvEntry>& harris_table() {
         t->push_back(harris_entry<3, 2, TMA, SFILT>(16, 16, 1));
         t->push_back(harris_entry<3, 2, SMEM, PARAM>(16, 16, 0));
         t->push_back(harris_entry<3, 2, SMEM, SFILT>(16, 16, 0));
+        // the paper's 2x2 block (offsets -1, 0): products over TW + 1 columns, 4 window taps
+        t->push_back(harris_entry<2, 2, TMA, PARAM>(16, 16, 1));
+        t->push_back(harris_entry<2, 4, TMA, PARAM>(16, 8, 1));
+        t->push_back(harris_entry<2, 2, TMA, SFILT>(16, 16, 1));
+        t->push_back(harris_entry<2, 2, SMEM, PARAM>(16, 16, 0));
+        t->push_back(harris_entry<2, 2, SMEM, SFILT>(16, 16, 0));
         return t;
     }();
     return *table;

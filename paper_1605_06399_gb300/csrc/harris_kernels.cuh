@@ -8,9 +8,9 @@
 //
 //  * k_harris_sobel_plain + k_harris_resp_plain: the untuned two-kernel form (Ix, Iy in
 //    a caller workspace; one pixel per thread; clamped global loads; rolled loops).
-//  * k_harris_fused: one kernel per tile.  The image tile plus a (RW+1)-pixel halo is
-//    staged in shared memory (TMA ring or cooperative loads) and patched to the clamp
-//    rule; the three products are formed for the tile plus the RW window halo, each at
+//  * k_harris_fused: one kernel per tile.  The image tile plus a (WK/2 + 1)-pixel halo
+//    is staged in shared memory (TMA ring or cooperative loads) and patched to the clamp
+//    rule; the three products are formed for the tile plus the window halo, each at
 //    the clamped position of its pixel (so a product outside the image equals the
 //    product at the nearest pixel inside, which is what the clamped window reads); the
 //    window sums run on a register-blocked PX x PY layout over the three planes and the
@@ -21,17 +21,19 @@
 
 namespace imcl {
 
-// Window-pass geometry: the product buffer's column c holds region column c (image column
-// x0 - RW + c), so a thread's segment starts at its own first output column, 16-byte
-// aligned, and holds exactly the PX + 2 RW products it needs (rounded up to whole float4s).
+// Window tap (j, i) of a WK x WK window reads offset (i - WK/2, j - WK/2): centred for
+// odd WK, offsets {-1, 0} for the 2x2 block.  Window-pass geometry: the product buffer's
+// column c holds region column c (image column x0 - WK/2 + c), so a thread's segment
+// starts at its own first output column, 16-byte aligned, and holds exactly the
+// PX + WK - 1 products it needs (rounded up to whole float4s).
 template <int WK>
 struct HarrisWindowGeo {
     static constexpr int PX = 4;
-    static constexpr int R = (WK - 1) / 2;
+    static constexpr int WLO = WK / 2;
     static constexpr int VB = 4;
-    static constexpr int SEG = round_up(PX + 2 * R, 4);
+    static constexpr int SEG = round_up(PX + WK - 1, 4);
     static constexpr int LO = 0;
-    static constexpr int USED = PX + 2 * R;
+    static constexpr int USED = PX + WK - 1;
 };
 
 // taps of the Harris operator as they travel in the launch parameters
@@ -77,7 +79,7 @@ __global__ void __launch_bounds__(256)
     // a.kw: the (odd) side run; a.kh: the caller's side, the stride of device taps (an
     // even window runs with a zero last row and column)
     const float* gd = static_cast<const float*>(a.taps3_dev);
-    const int wk = a.kw, rw = (wk - 1) / 2, src = a.kh;
+    const int wk = a.kw, rw = wk / 2, src = a.kh;   // tap j reads offset j - wk/2
     for (int y = blockIdx.y * blockDim.y + threadIdx.y; y < a.H; y += gridDim.y * blockDim.y) {
         float sxx = 0.f, syy = 0.f, sxy = 0.f;
 #pragma unroll 1
@@ -104,19 +106,19 @@ __global__ void __launch_bounds__(256, 2)
     k_harris_fused(const ConvArgs a, const __grid_constant__ HarrisTaps<WK> tp,
                    const __grid_constant__ CUtensorMap tmap) {
     constexpr int PX = 4;
-    constexpr int RW = (WK - 1) / 2;
-    constexpr int HALO = RW + 1;                       // input rows/cols beyond the tile
+    constexpr int WLO = WK / 2;                        // window rows / columns before the pixel
+    constexpr int HALO = WLO + 1;                      // input rows/cols before the tile
     constexpr int PADI = 4;                            // staged input halo columns (16 B)
-    static_assert(HALO <= PADI, "window radius too large for the staged halo");
+    static_assert(HALO <= PADI && WK - WLO <= PADI, "window too large for the staged halo");
     using GW = HarrisWindowGeo<WK>;                   // window pass: region column == buffer column
     extern __shared__ __align__(128) uint8_t smem[];
 
     const int tid = threadIdx.x, nth = blockDim.x;
     const int bx = a.bx, by = a.by;
     const int TW = bx * PX, TH = by * PY;
-    const int SW = TW + 2 * PADI, SH = TH + 2 * HALO;
-    const int NG = (TW + 2 * RW + 3) / 4;              // product groups of 4 columns per row
-    const int PH = TH + 2 * RW, PW = 4 * NG;
+    const int SW = TW + 2 * PADI, SH = TH + WK + 1;
+    const int NG = (TW + WK - 1 + 3) / 4;              // product groups of 4 columns per row
+    const int PH = TH + WK - 1, PW = 4 * NG;
     const int stage_bytes = round_up(SW * SH * 4, 128);
     constexpr int kStages = LOAD == IMCL_LOAD_TMA ? 2 : 1;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
@@ -195,17 +197,18 @@ __global__ void __launch_bounds__(256, 2)
             __syncthreads();
         }
 
-        // products for the (TW + 2RW) x (TH + 2RW) window region, 4 columns per item.
-        // Product column pc (region-local, 0 = image column x0 - RW) lives at pbuf column
+        // products for the (TW + WK - 1) x (TH + WK - 1) window region, 4 columns per item.
+        // Product column pc (region-local, 0 = image column x0 - WLO) lives at pbuf column
         // pc, so a group of 4 is one aligned float4 per plane.  Each product is taken at
         // the clamped position of its pixel.
-        const bool interior = x0 - RW >= 0 && y0 - RW >= 0 && x0 - RW + 4 * NG <= a.W && y0 + TH + RW <= a.H;
+        const bool interior = x0 - WLO >= 0 && y0 - WLO >= 0 && x0 - WLO + 4 * NG <= a.W &&
+                              y0 - WLO + PH <= a.H;
         for (int it = tid; it < PH * NG; it += nth) {
             const int pr = it / NG, pc0 = (it - pr * NG) * 4;
             float gx[4], gy[4];
             if (interior) {
-                // input column of region column pc is pc + PADI - RW; the Sobel reads -1..+1
-                const float* r0 = st + pr * SW + pc0;   // aligned chunk holding column pc0 + PADI-RW-1
+                // input column of region column pc is pc + PADI - WLO; the Sobel reads -1..+1
+                const float* r0 = st + pr * SW + pc0;   // aligned chunk holding column pc0 + PADI-WLO-1
 #pragma unroll
                 for (int e = 0; e < 4; ++e) { gx[e] = 0.f; gy[e] = 0.f; }
 #pragma unroll
@@ -220,7 +223,7 @@ __global__ void __launch_bounds__(256, 2)
                         const float wx = sxw[j * 3 + i], wy = syw[j * 3 + i];
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
-                            const float u = v[PADI - RW - 1 + e + i];
+                            const float u = v[PADI - WLO - 1 + e + i];
                             gx[e] = __fmaf_rn(wx, u, gx[e]);
                             gy[e] = __fmaf_rn(wy, u, gy[e]);
                         }
@@ -230,8 +233,8 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     // clamped pixel of this product, in input-tile coordinates
-                    const int px = clampi(x0 - RW + pc0 + e, 0, a.W - 1) - gx0;
-                    const int py = clampi(y0 - RW + pr, 0, a.H - 1) - gy0;
+                    const int px = clampi(x0 - WLO + pc0 + e, 0, a.W - 1) - gx0;
+                    const int py = clampi(y0 - WLO + pr, 0, a.H - 1) - gy0;
                     float ax = 0.f, ay = 0.f;
                     if (px >= 1 && px < SW - 1 && py >= 1 && py < SH - 1) {
 #pragma unroll
@@ -313,7 +316,7 @@ imcl_status launch_harris_plain(const ConvCall& c, const imcl_variant& v, cudaSt
 
 template <int WK, int PY, int LOAD, int FILT>
 imcl_status launch_harris_fused(const ConvCall& c, const imcl_variant& v, cudaStream_t s) {
-    constexpr int PX = 4, RW = (WK - 1) / 2, HALO = RW + 1, PADI = 4;
+    constexpr int PX = 4, PADI = 4;
     const int bx = v.bx, by = v.by, nth = bx * by;
     if (bx <= 0 || by <= 0 || nth > 256 || nth % 32 != 0)
         return fail(IMCL_ERR_UNSUPPORTED, "fused harris: bx*by must be a multiple of 32, at most 256");
@@ -321,10 +324,10 @@ imcl_status launch_harris_fused(const ConvCall& c, const imcl_variant& v, cudaSt
     if (c.taps_mem == IMCL_MEM_DEVICE && FILT != IMCL_FILT_SMEM)
         return fail(IMCL_ERR_UNSUPPORTED, "device-resident taps need a FILT_SMEM variant");
     const int TW = bx * PX, TH = by * PY;
-    const int SW = TW + 2 * PADI, SH = TH + 2 * HALO;
+    const int SW = TW + 2 * PADI, SH = TH + WK + 1;
     if (LOAD == IMCL_LOAD_TMA && (SW > 256 || SH > 256))
         return fail(IMCL_ERR_UNSUPPORTED, "fused harris: TMA box larger than 256 in a dimension");
-    const int PH = TH + 2 * RW, PW = 4 * ((TW + 2 * RW + 3) / 4);
+    const int PH = TH + WK - 1, PW = 4 * ((TW + WK - 1 + 3) / 4);
     const int stage_bytes = round_up(SW * SH * 4, 128);
     const int nstage = LOAD == IMCL_LOAD_TMA ? 2 : 1;
     const int smem = 128 + nstage * stage_bytes + 3 * PH * PW * 4 + (18 + WK * WK) * 4;

@@ -104,7 +104,12 @@ imcl_status TuneScratch::image(int dtype, int W, int H, uint32_t seed, void** p,
 }
 
 // ------------------------------------------------------------------ the search
-static const int kShapes[][2] = {{32, 8}, {32, 4}, {16, 16}, {16, 8}, {64, 4}, {64, 2}, {8, 16}, {32, 2}};
+// Work-group shapes swept for every tiled variant: every (bx, by) with bx in 4..128,
+// by in 1..64 (powers of two) and 32..256 threads (the launcher rejects the shapes a
+// variant's row alignment cannot take; they count as invalid candidates).
+static const int kShapes[][2] = {{32, 8}, {32, 4}, {16, 16}, {16, 8}, {64, 4}, {64, 2}, {8, 16}, {32, 2},
+                                 {4, 8}, {4, 16}, {4, 32}, {4, 64}, {8, 4}, {8, 8}, {8, 32}, {16, 2},
+                                 {16, 4}, {32, 1}, {64, 1}, {128, 1}, {128, 2}};
 
 std::vector<imcl_variant> expand_shapes(const std::vector<imcl_variant>& base) {
     std::vector<imcl_variant> out;
@@ -361,6 +366,8 @@ private:
     double b2_ = 0.0;
 };
 
+constexpr int kHoldout = 8;   // random configurations timed after training, to measure the model
+
 imcl_status tune_model_search(TuneJob& job, int n_sample, int n_confirm, int reps, uint64_t seed, cudaStream_t s,
                               imcl_variant* best, double* best_ms, double* plain_ms, imcl_tune_report* report) {
     const auto t_start = std::chrono::steady_clock::now();
@@ -405,6 +412,8 @@ imcl_status tune_model_search(TuneJob& job, int n_sample, int n_confirm, int rep
     }
     // the model, on standardised log times, then the untimed configurations it ranks best
     std::vector<std::pair<double, int>> ranked;
+    std::vector<double> pred(space.size(), 0.0);   // the model's log time of every configuration
+    bool have_model = false;
     if (X.size() >= 3) {
         double mean = 0, var = 0;
         for (double v : y) mean += v;
@@ -421,8 +430,10 @@ imcl_status tune_model_search(TuneJob& job, int n_sample, int n_confirm, int rep
             se += d * d;
         }
         rep.model_rmse = std::sqrt(se / (double)X.size());
+        for (size_t i = 0; i < space.size(); ++i) pred[i] = net.predict(enc.encode(space[i])) * sd + mean;
+        have_model = true;
         for (size_t i = 0; i < space.size(); ++i)
-            if (!timed[i]) ranked.push_back({net.predict(enc.encode(space[i])), (int)i});
+            if (!timed[i]) ranked.push_back({pred[i], (int)i});
         std::sort(ranked.begin(), ranked.end());
     } else {   // too few valid samples for a model: confirm further random draws
         for (size_t k = (size_t)ns; k < order.size(); ++k) ranked.push_back({0.0, order[k]});
@@ -430,6 +441,24 @@ imcl_status tune_model_search(TuneJob& job, int n_sample, int n_confirm, int rep
     for (int k = 0; k < n_confirm && k < (int)ranked.size(); ++k) {
         if ((st = try_one(ranked[(size_t)k].second)) != IMCL_OK) return st;
         ++rep.confirmed;
+    }
+    // held-out check of the model: configurations it neither trained on nor picked, drawn
+    // at random, timed, and compared with the model's prediction (they may also win)
+    if (have_model) {
+        double se = 0;
+        for (size_t k = (size_t)ns; k < order.size() && rep.holdout < kHoldout; ++k) {
+            const int idx = order[k];
+            if (timed[(size_t)idx]) continue;
+            const size_t before = y.size();
+            if ((st = try_one(idx)) != IMCL_OK) return st;
+            ++rep.holdout;
+            if (y.size() > before) {
+                const double d = pred[(size_t)idx] - y.back();
+                se += d * d;
+                ++rep.holdout_valid;
+            }
+        }
+        rep.holdout_rmse = rep.holdout_valid ? std::sqrt(se / rep.holdout_valid) : 0.0;
     }
     *best = win;
     if (best_ms) *best_ms = t_win;

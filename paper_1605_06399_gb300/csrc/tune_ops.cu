@@ -27,7 +27,7 @@ imcl_status list_variants(const imcl_problem& p, std::vector<imcl_variant>* out)
         return IMCL_OK;
     }
     if (p.op == IMCL_OP_HARRIS) {
-        for (const ConvEntry* e : harris_entries_for(harris_kernel_side(p.kw), p.taps_mem)) out->push_back(e->v);
+        for (const ConvEntry* e : harris_entries_for(harris_forward_side(p.kw), p.taps_mem)) out->push_back(e->v);
         return IMCL_OK;
     }
     return fail(IMCL_ERR_UNSUPPORTED, "unknown op");
