@@ -82,6 +82,27 @@ __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a_desc, uint6
         : "memory");
 }
 
+// The same with the A operand in tensor memory (M lanes x K columns at a_tmem; tf32: one
+// element per 32-bit column, f16/bf16: two): only B is read from shared memory.
+__device__ __forceinline__ void umma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                             uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void umma_f16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 // Arrive once on `bar` when every MMA this thread issued so far has completed.
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -112,6 +133,108 @@ __device__ __forceinline__ void tmem_ld16x2(uint32_t taddr0, uint32_t taddr1, fl
         v0[i] = __uint_as_float(r[i]);
         v1[i] = __uint_as_float(r[16 + i]);
     }
+}
+
+// 4 J consecutive 32-bit columns (J in 5..8) of the warp's 32 lanes from taddr, loaded as
+// x16 / x8 / x4 / x32 pieces behind one wait: v[c] is column c.
+template <int J>
+__device__ __forceinline__ void tmem_ld4xJ(uint32_t taddr, float* v) {
+    static_assert(J >= 5 && J <= 8, "5..8 column groups of 4");
+    uint32_t r[32];
+#define IMCL_O4(b) "=r"(r[b]), "=r"(r[b + 1]), "=r"(r[b + 2]), "=r"(r[b + 3])
+    if constexpr (J == 5) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%20];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%16, %17, %18, %19}, [%21];\n\t"
+            "tcgen05.wait::ld.sync.aligned;"
+            : IMCL_O4(0), IMCL_O4(4), IMCL_O4(8), IMCL_O4(12), IMCL_O4(16)
+            : "r"(taddr), "r"(taddr + 16)
+            : "memory");
+    } else if constexpr (J == 6) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%24];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%25];\n\t"
+            "tcgen05.wait::ld.sync.aligned;"
+            : IMCL_O4(0), IMCL_O4(4), IMCL_O4(8), IMCL_O4(12), IMCL_O4(16), IMCL_O4(20)
+            : "r"(taddr), "r"(taddr + 16)
+            : "memory");
+    } else if constexpr (J == 7) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%28];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%29];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%24, %25, %26, %27}, [%30];\n\t"
+            "tcgen05.wait::ld.sync.aligned;"
+            : IMCL_O4(0), IMCL_O4(4), IMCL_O4(8), IMCL_O4(12), IMCL_O4(16), IMCL_O4(20), IMCL_O4(24)
+            : "r"(taddr), "r"(taddr + 16), "r"(taddr + 24)
+            : "memory");
+    } else {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+            "tcgen05.wait::ld.sync.aligned;"
+            : IMCL_O4(0), IMCL_O4(4), IMCL_O4(8), IMCL_O4(12), IMCL_O4(16), IMCL_O4(20), IMCL_O4(24), IMCL_O4(28)
+            : "r"(taddr)
+            : "memory");
+    }
+#undef IMCL_O4
+#pragma unroll
+    for (int i = 0; i < 4 * J; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// N (1..3) loads of 8 consecutive 32-bit columns (at taddr + 8 j, j < N) and their wait.
+template <int N>
+__device__ __forceinline__ void tmem_ld8xN(uint32_t taddr, float* v) {
+    static_assert(N >= 1 && N <= 3, "1..3 column groups");
+    uint32_t r[24];
+#define IMCL_O8N(b) "=r"(r[b]), "=r"(r[b + 1]), "=r"(r[b + 2]), "=r"(r[b + 3]), "=r"(r[b + 4]), "=r"(r[b + 5]), \
+                    "=r"(r[b + 6]), "=r"(r[b + 7])
+    if constexpr (N == 1) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
+            "tcgen05.wait::ld.sync.aligned;"
+            : IMCL_O8N(0)
+            : "r"(taddr)
+            : "memory");
+    } else if constexpr (N == 2) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%16];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%17];\n\t"
+            "tcgen05.wait::ld.sync.aligned;"
+            : IMCL_O8N(0), IMCL_O8N(8)
+            : "r"(taddr), "r"(taddr + 8)
+            : "memory");
+    } else {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%24];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%25];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%26];\n\t"
+            "tcgen05.wait::ld.sync.aligned;"
+            : IMCL_O8N(0), IMCL_O8N(8), IMCL_O8N(16)
+            : "r"(taddr), "r"(taddr + 8), "r"(taddr + 16)
+            : "memory");
+    }
+#undef IMCL_O8N
+#pragma unroll
+    for (int i = 0; i < 8 * N; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Four loads of 8 consecutive 32-bit columns (at taddr + 8 j, j < 4) and their wait.
+__device__ __forceinline__ void tmem_ld8x4(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%32];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%33];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%34];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24, %25, %26, %27, %28, %29, %30, %31}, [%35];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr), "r"(taddr + 8), "r"(taddr + 16), "r"(taddr + 24)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // J loads of 8 consecutive 32-bit columns (at taddr + 8 j, j < J, J in 5..8) of the
@@ -179,6 +302,25 @@ __device__ __forceinline__ void tmem_ld8xJ(uint32_t taddr, float* v) {
 #undef IMCL_O8
 #pragma unroll
     for (int i = 0; i < 8 * J; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Registers -> tensor memory: 16 (or 8) consecutive 32-bit columns of the warp's 32
+// lanes (thread t writes lane base + t), then the wait for the stores to complete.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* r) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                 "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 }  // namespace imcl
