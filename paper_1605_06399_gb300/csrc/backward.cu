@@ -29,7 +29,7 @@ size_t sepconv_backward_ws(int W, int H, int nr, int nc) {
 }
 // CTAs (tap-gradient partial sets) of the fused Harris adjoint at most
 static int harris_fused_parts(int W, int H) {
-    const int tiles = ((W + kHbTile - 1) / kHbTile) * ((H + kHbTile - 1) / kHbTile);
+    const int tiles = ((W + kHbTileW - 1) / kHbTileW) * ((H + kHbTileH - 1) / kHbTileH);
     return std::min(tiles, kWgMaxParts);
 }
 size_t harris_backward_ws(int W, int H, int wk) {
@@ -405,11 +405,11 @@ static imcl_status harris_bwd_fused(const BwdArgs& b, const float* sx, const flo
         gwd = gw;
     }
     constexpr int smem = HbGeo<WK>::TOTAL * (int)sizeof(float);
-    static_assert(HbGeo<WK>::TOTAL >= 256 * HbGeo<WK>::NTAP, "the tap combine reuses the tile buffers");
+    static_assert(HbGeo<WK>::TOTAL >= kHbThreads * HbGeo<WK>::NTAP, "the tap combine reuses the tile buffers");
     auto kfn = k_harris_bwd_fused<WK>;
     imcl_status st = set_smem_limit((const void*)kfn, smem);
     if (st != IMCL_OK) return st;
-    kfn<<<grid, 256, smem, s>>>(static_cast<const float*>(f.in), f.in_pitch_b / 4, b.g, b.g_pitch_b / 4, b.dx,
+    kfn<<<grid, kHbThreads, smem, s>>>(static_cast<const float*>(f.in), f.in_pitch_b / 4, b.g, b.g_pitch_b / 4, b.dx,
                                 b.dx_pitch_b / 4, f.W, f.H, f.hk, sxd, syd, gwd, tp, pw, psx, psy);
     return cuda_fail(cudaGetLastError(), "harris backward (fused)");
 }

@@ -9,22 +9,29 @@
 //   gIx = 2 Ix gPxx + Iy gPxy,  gIy = 2 Iy gPyy + Ix gPxy
 //   dI(q) = sum_{p, o: b(p+o) = q} Sx[o] gIx(p) + Sy[o] gIy(p)
 //   dSx[o] = sum_p gIx(p) I(b(p+o)),  dSy[o] likewise
-// A CTA owns a TB x TB tile of dI and recomputes what it needs on shrinking halos:
+// A CTA owns a TW x TH tile of dI and recomputes what it needs on shrinking halos:
 // I on halo 2 + 2RW, (Ix, Iy, P) on 1 + 2RW (taken at the clamped position outside the
 // image, as the window reads them), gS on 1 + RW (zero outside), (gP, gI) on 1 (zero
 // outside), dI on the tile.  Inside the image the adjoint sums are the plain
 // correlations with reversed offsets (b(p+o) = q with p = q - o); on the image's first
 // and last rows and columns they also collect the offsets that were clamped onto q (the
-// transpose of the clamp), added by explicit loops there.  Tap gradients are per-thread
-// sums over the CTA's tiles, combined in a fixed order into per-CTA partials (then
-// reduced by k_wgrad_finalize): deterministic.
+// transpose of the clamp), added by explicit loops there.
+//
+// The two window passes and the window-gradient pass work on items of one channel x
+// 4 rows x 4 columns: each row of the input plane read (16-byte loads, quad-aligned
+// columns) feeds up to four output rows from registers.  Items run columns fastest and
+// the quad pitches of those planes are odd, so the eight lanes of a quarter warp read
+// distinct bank quads.  The channel-mixing steps (gS from the window sums, gI from gP)
+// are separate element-wise passes.  Tap gradients are per-thread sums over the CTA's
+// tiles, combined in a fixed order into per-CTA partials (then reduced by
+// k_wgrad_finalize): deterministic.
 #pragma once
 
 #include "tile_common.cuh"
 
 namespace imcl {
 
-constexpr int kHbTile = 32;                       // output tile side
+constexpr int kHbTileW = 64, kHbTileH = 32;       // output tile (columns, rows)
 
 // taps as kernel parameters (host taps): window, Sobel x, Sobel y
 template <int WK>
@@ -34,55 +41,110 @@ struct HbTaps {
     float sy[9];
 };
 
+__host__ __device__ constexpr int hb_max(int a, int b) { return a > b ? a : b; }
+// a quad pitch (multiple of 4 floats) with an odd number of quads
+__host__ __device__ constexpr int hb_odd_quads(int v) { return (round_up(v, 4) / 4) % 2 ? round_up(v, 4) : round_up(v, 4) + 4; }
+
 template <int WK>
 struct HbGeo {
     static constexpr int RW = (WK - 1) / 2;
-    static constexpr int TB = kHbTile;
-    static constexpr int HI = 2 + 2 * RW, HP = 1 + 2 * RW, HS = 1 + RW, HG = 1;
-    static constexpr int WI = TB + 2 * HI;                                  // I region rows
-    static constexpr int XI = HI;                                           // I region's left halo
-    static constexpr int WIX = TB + 2 * XI;                                 // I region columns
-    static constexpr int WP = TB + 2 * HP;                                  // P region side
-    static constexpr int WS = TB + 2 * HS;                                  // gS region side
-    static constexpr int WG = TB + 2 * HG;                                  // gI region side
-    static constexpr int NSI = (WS + 3) / 4;                                // 4-wide items per gS row
-    static constexpr int NGI = (WG + 3) / 4;                                // 4-wide items per gI row
-    // row pitches (floats): odd, so that threads walking down a column of items (the
-    // mapping of steps 3 to 5) touch distinct banks
-    static constexpr int PPI = WIX;
-    static constexpr int PPP = (4 * NSI + 2 * RW) | 1;
-    static constexpr int PPS = ((4 * NGI + 2 * RW) > 4 * NSI ? (4 * NGI + 2 * RW) : 4 * NSI) | 1;
-    static constexpr int PPG = (4 * NGI) | 1;
+    static constexpr int TW = kHbTileW, TH = kHbTileH;
+    static constexpr int HI = 2 + 2 * RW, HP = 1 + 2 * RW, HS = 1 + RW;
+    // regions (rows x columns): I, P (and Ix, Iy), gS, gI; each starts at its halo
+    static constexpr int RI = TH + 2 * HI, CI = TW + 2 * HI;
+    static constexpr int RP = TH + 2 * HP, CP = TW + 2 * HP;
+    static constexpr int RS = TH + 2 * HS, CS = TW + 2 * HS;
+    static constexpr int RG = TH + 2, CG = TW + 2;
+    // 4 x 4 item grids of the window pass (gS region), its adjoint (gI region), the
+    // window-gradient pass (tile) and the 4-row column items of the Sobel passes
+    static constexpr int NRS = (RS + 3) / 4, NCS = (CS + 3) / 4;
+    static constexpr int NRG = (RG + 3) / 4, NCG = (CG + 3) / 4;
+    static constexpr int NRT = TH / 4, NCT = TW / 4;
+    static constexpr int NRP = (RP + 3) / 4;
+    // float4 loads per item row: window passes (4 + 2RW columns from the item's quad),
+    // window gradient (4 + 2RW columns from HP - RW past it)
+    static constexpr int NV = (4 + 2 * RW + 3) / 4;
+    static constexpr int OFF4 = HP - RW;
+    static constexpr int NV4 = (OFF4 + 4 + 2 * RW + 3) / 4;
+    // stored rows and pitches (floats), each covering every index its passes touch
+    static constexpr int SRI = hb_max(RI, 4 * NRP + 2);
+    static constexpr int PPI = CI;
+    static constexpr int SRP = hb_max(hb_max(RP, 4 * NRP), hb_max(4 * NRS + 2 * RW, 4 * NRG));
+    static constexpr int PPP = hb_odd_quads(hb_max(hb_max(CP, 4 * NCG), hb_max(4 * (NCS - 1) + 4 * NV, 4 * (NCT - 1) + 4 * NV4)));
+    static constexpr int SRS = hb_max(4 * NRS, 4 * NRG + 2 * RW);
+    static constexpr int PPS = hb_odd_quads(hb_max(4 * NCS, 4 * (NCG - 1) + 4 * NV));
+    static constexpr int PPG = CG;
     static constexpr int NTAP = WK * WK + 18;                               // window, Sobel x, Sobel y
-    // shared memory (floats): taps, I, Ix Iy Pxx Pyy Pxy, gSxx gSyy gSxy, gIx gIy
+    // shared memory (floats): taps, I, Pxx Pyy Pxy (later gPxx gPyy gPxy),
+    // gSxx gSyy gSxy (first the window sums), Ix Iy (later gIx gIy)
     static constexpr int O_TAP = 0;
     static constexpr int O_I = round_up(NTAP, 4);
-    static constexpr int O_X = O_I + PPI * WI;                              // after the I rows
-    static constexpr int PLANE_P = PPP * WP;
-    static constexpr int O_S = O_X + 5 * PLANE_P;
-    static constexpr int PLANE_S = PPS * WS;
+    static constexpr int PLANE_P = PPP * SRP;
+    static constexpr int O_P = round_up(O_I + PPI * SRI, 4);
+    static constexpr int PLANE_S = PPS * SRS;
+    static constexpr int O_S = O_P + 3 * PLANE_P;
+    static constexpr int PLANE_G = PPG * RG;
     static constexpr int O_G = O_S + 3 * PLANE_S;
-    static constexpr int PLANE_G = PPG * WG;
     static constexpr int TOTAL = O_G + 2 * PLANE_G;
+    static_assert(PLANE_P % 4 == 0 && PLANE_S % 4 == 0, "quad-aligned planes");
 };
 
+constexpr int kHbThreads = 256;                   // threads per CTA (the launch uses exactly this)
+
+// The transpose of the clamp at an image-edge pixel q = (gx, gy) for a correlation of
+// radius R: every source u outside the image that the clamp maps onto q, and each offset
+// o = (i - R, j - R) whose output p = u - o lies inside the image; f(j, i, py, px) gets
+// the tap and p.  (Along x, b(u) = gx exactly for u = gx, and for u < 0 when gx = 0 and
+// u > W - 1 when gx = W - 1; likewise along y.)
+template <int R, typename F>
+__device__ __forceinline__ void hb_clamp_fold(int gx, int gy, int W, int H, F&& f) {
+    const int ux0 = gx == 0 ? -R : gx, ux1 = gx == W - 1 ? W - 1 + R : gx;
+    const int uy0 = gy == 0 ? -R : gy, uy1 = gy == H - 1 ? H - 1 + R : gy;
+    for (int uy = uy0; uy <= uy1; ++uy)
+        for (int ux = ux0; ux <= ux1; ++ux) {
+            if (ux >= 0 && ux < W && uy >= 0 && uy < H) continue;
+            for (int j = 0; j < 2 * R + 1; ++j) {
+                const int py = uy - (j - R);
+                if (py < 0 || py >= H) continue;
+                for (int i = 0; i < 2 * R + 1; ++i) {
+                    const int px = ux - (i - R);
+                    if (px >= 0 && px < W) f(j, i, py, px);
+                }
+            }
+        }
+}
+
+// Store the products at P-region pixel (r, c), and Ix, Iy where the gI region covers it
 template <int WK>
-__global__ void __launch_bounds__(256, 2)
+__device__ __forceinline__ void hb_store_p(float* Ps, float* gIs, int r, int c, float ix, float iy) {
+    using G = HbGeo<WK>;
+    const int o = r * G::PPP + c;
+    Ps[o] = ix * ix;
+    Ps[G::PLANE_P + o] = iy * iy;
+    Ps[2 * G::PLANE_P + o] = ix * iy;
+    const int gr = r - (G::HP - 1), gc = c - (G::HP - 1);          // gI-region coordinates
+    if (gr >= 0 && gr < G::RG && gc >= 0 && gc < G::CG) {
+        gIs[gr * G::PPG + gc] = ix;
+        gIs[G::PLANE_G + gr * G::PPG + gc] = iy;
+    }
+}
+
+template <int WK>
+__global__ void __launch_bounds__(kHbThreads, 2)
     k_harris_bwd_fused(const float* __restrict__ I, long long i_pitch, const float* __restrict__ gR, long long g_pitch,
                        float* dI, long long d_pitch, int W, int H, float k, const float* sx_dev, const float* sy_dev,
                        const float* gw_dev, const __grid_constant__ HbTaps<WK> tp, float* part_w, float* part_sx,
                        float* part_sy) {
     using G = HbGeo<WK>;
-    constexpr int RW = G::RW, TB = G::TB, HI = G::HI, HP = G::HP, HS = G::HS, XI = G::XI;
+    constexpr int RW = G::RW, TW = G::TW, TH = G::TH, HI = G::HI, HP = G::HP, HS = G::HS;
     extern __shared__ __align__(16) float hsm[];
     float* taps = hsm + G::O_TAP;                 // window (WK*WK), Sobel x (9), Sobel y (9)
     float* Is = hsm + G::O_I;
-    float* Ixs = hsm + G::O_X;
-    float* Iys = Ixs + G::PLANE_P;
-    float* Ps = Iys + G::PLANE_P;                 // Pxx, Pyy, Pxy planes
-    float* gSs = hsm + G::O_S;                    // gSxx, gSyy, gSxy planes
-    float* gIs = hsm + G::O_G;                    // gIx, gIy planes
-    const int tid = threadIdx.x, nth = blockDim.x;
+    float* Ps = hsm + G::O_P;                     // Pxx, Pyy, Pxy planes; later gP
+    float* gSs = hsm + G::O_S;                    // window sums, then gSxx, gSyy, gSxy planes
+    float* gIs = hsm + G::O_G;                    // Ix, Iy planes; later gIx, gIy
+    const int tid = threadIdx.x;
+    constexpr int nth = kHbThreads;
     for (int q = tid; q < G::NTAP; q += nth) {
         float v;
         if (q < WK * WK) v = gw_dev ? gw_dev[q] : tp.g[q];
@@ -100,212 +162,296 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
     for (int q = 0; q < 9; ++q) { asx[q] = 0.f; asy[q] = 0.f; }
 
-    const int tiles_x = (W + TB - 1) / TB, tiles_y = (H + TB - 1) / TB;
+    const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH;
     for (int t = blockIdx.x; t < tiles_x * tiles_y; t += gridDim.x) {
-        const int x0 = (t % tiles_x) * TB, y0 = (t / tiles_x) * TB;
-        const bool border_tile = x0 - HI < 0 || y0 - HI < 0 || x0 + TB + HI > W || y0 + TB + HI > H;
+        const int x0 = (t % tiles_x) * TW, y0 = (t / tiles_x) * TH;
+        const bool border_tile = x0 - HI < 0 || y0 - HI < 0 || x0 + TW + HI > W || y0 + TH + HI > H;
         __syncthreads();   // taps staged / the previous tile's planes are no longer read
-        // (1) I on the I region (rows from y0 - HI, columns from x0 - XI), at clamped positions
-        for (int q = tid; q < G::WI * G::WIX; q += nth) {
-            const int r = q / G::WIX, c = q - r * G::WIX;
-            const int gy = clampi(y0 - HI + r, 0, H - 1), gx = clampi(x0 - XI + c, 0, W - 1);
-            Is[r * G::PPI + c] = I[(long long)gy * i_pitch + gx];
-        }
-        __syncthreads();
-        // (2) Ix, Iy and the products on the P region, each at its clamped pixel
-        for (int q = tid; q < G::WP * G::WP; q += nth) {
-            const int r = q / G::WP, c = q - r * G::WP;
-            int ir = r + (HI - HP), ic = c + (XI - HP);       // I-region coordinates of the pixel
-            if (border_tile) {
-                ir = clampi(y0 - HP + r, 0, H - 1) - (y0 - HI);
-                ic = clampi(x0 - HP + c, 0, W - 1) - (x0 - XI);
+        // (1) I on the I region (rows from y0 - HI, columns from x0 - HI), at clamped positions
+        //     (all of a thread's loads issued before its first store)
+        {
+            constexpr int N = G::RI * G::CI, NQ = (N + kHbThreads - 1) / kHbThreads;
+            float v[NQ];
+#pragma unroll
+            for (int n = 0; n < NQ; ++n) {
+                const int q = tid + n * kHbThreads, r = q / G::CI, c = q - r * G::CI;
+                const int gy = clampi(y0 - HI + r, 0, H - 1), gx = clampi(x0 - HI + c, 0, W - 1);
+                v[n] = q < N ? I[(long long)gy * i_pitch + gx] : 0.f;
             }
-            float ix = 0.f, iy = 0.f;
 #pragma unroll
-            for (int j = 0; j < 3; ++j)
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    const float u = Is[(ir - 1 + j) * G::PPI + ic - 1 + i];
-                    ix = __fmaf_rn(sxw[j * 3 + i], u, ix);
-                    iy = __fmaf_rn(syw[j * 3 + i], u, iy);
-                }
-            const int o = r * G::PPP + c;
-            Ixs[o] = ix;
-            Iys[o] = iy;
-            Ps[o] = ix * ix;
-            Ps[G::PLANE_P + o] = iy * iy;
-            Ps[2 * G::PLANE_P + o] = ix * iy;
+            for (int n = 0; n < NQ; ++n) {
+                const int q = tid + n * kHbThreads, r = q / G::CI, c = q - r * G::CI;
+                if (q < N) Is[r * G::PPI + c] = v[n];
+            }
         }
         __syncthreads();
-        // (3) window sums and gS on the gS region, 4 columns per item (zero outside)
-        for (int it = tid; it < G::WS * G::NSI; it += nth) {
-            const int c0 = (it / G::WS) * 4, r = it - (c0 / 4) * G::WS;   // rows fastest
-            float s[3][4];
+        // (2) Ix, Iy and the products on the P region, each at its clamped pixel; Ix and
+        //     Iy also into the gI planes where the gI region covers the pixel
+        if (border_tile) {
+            for (int q = tid; q < G::RP * G::CP; q += nth) {
+                const int r = q / G::CP, c = q - r * G::CP;
+                const int ir = clampi(y0 - HP + r, 0, H - 1) - (y0 - HI);
+                const int ic = clampi(x0 - HP + c, 0, W - 1) - (x0 - HI);
+                float ix = 0.f, iy = 0.f;
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch)
+                for (int j = 0; j < 3; ++j)
 #pragma unroll
-                for (int e = 0; e < 4; ++e) s[ch][e] = 0.f;
+                    for (int i = 0; i < 3; ++i) {
+                        const float u = Is[(ir - 1 + j) * G::PPI + ic - 1 + i];
+                        ix = __fmaf_rn(sxw[j * 3 + i], u, ix);
+                        iy = __fmaf_rn(syw[j * 3 + i], u, iy);
+                    }
+                hb_store_p<WK>(Ps, gIs, r, c, ix, iy);
+            }
+        } else {
+            // columns fastest, 4 rows per item: the I-region rows r0 .. r0 + 5 around them
+            for (int q = tid; q < G::NRP * G::CP; q += nth) {
+                const int r0 = (q / G::CP) * 4, c = q - (r0 / 4) * G::CP;
+                float u[6][3];
 #pragma unroll
-            for (int j = 0; j < WK; ++j) {
+                for (int jj = 0; jj < 6; ++jj)
 #pragma unroll
-                for (int ch = 0; ch < 3; ++ch) {
-                    // P-region row r + j, columns c0 .. c0 + 3 + 2RW (offset (i - RW, j - RW))
-                    const float* pr = Ps + ch * G::PLANE_P + (r + j) * G::PPP + c0;
-                    float v[4 + 2 * RW];
+                    for (int i = 0; i < 3; ++i) u[jj][i] = Is[(r0 + jj + (HI - HP) - 1) * G::PPI + c + (HI - HP) - 1 + i];
 #pragma unroll
-                    for (int q = 0; q < 4 + 2 * RW; ++q) v[q] = pr[q];
+                for (int py = 0; py < 4; ++py) {
+                    if (r0 + py >= G::RP) break;
+                    float ix = 0.f, iy = 0.f;
 #pragma unroll
-                    for (int i = 0; i < WK; ++i) {
-                        const float w = gw[j * WK + i];
+                    for (int j = 0; j < 3; ++j)
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) s[ch][e] = __fmaf_rn(w, v[e + i], s[ch][e]);
+                        for (int i = 0; i < 3; ++i) {
+                            ix = __fmaf_rn(sxw[j * 3 + i], u[py + j][i], ix);
+                            iy = __fmaf_rn(syw[j * 3 + i], u[py + j][i], iy);
+                        }
+                    hb_store_p<WK>(Ps, gIs, r0 + py, c, ix, iy);
+                }
+            }
+        }
+        __syncthreads();
+        // (3) window sums S_c on the gS region: items of one channel x 4 rows x 4 columns,
+        //     P rows r0 .. r0 + 3 + 2RW each feeding the item rows it lies under
+        {
+            float wr[WK * WK];
+#pragma unroll
+            for (int q = 0; q < WK * WK; ++q) wr[q] = gw[q];
+            for (int it = tid; it < 3 * G::NRS * G::NCS; it += nth) {
+                const int ch = it / (G::NRS * G::NCS), rem = it - ch * (G::NRS * G::NCS);
+                const int r0 = (rem / G::NCS) * 4, c0 = (rem % G::NCS) * 4;
+                float s[4][4];
+#pragma unroll
+                for (int py = 0; py < 4; ++py)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) s[py][e] = 0.f;
+                const float* pr = Ps + ch * G::PLANE_P + r0 * G::PPP + c0;
+#pragma unroll
+                for (int jr = 0; jr < WK + 3; ++jr) {
+                    float v[4 * G::NV];
+#pragma unroll
+                    for (int q = 0; q < G::NV; ++q) {
+                        const float4 f = *reinterpret_cast<const float4*>(pr + jr * G::PPP + 4 * q);
+                        v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+                    }
+#pragma unroll
+                    for (int py = 0; py < 4; ++py) {
+                        const int j = jr - py;                 // window row of this P row for item row py
+                        if (j < 0 || j >= WK) continue;
+#pragma unroll
+                        for (int i = 0; i < WK; ++i)
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) s[py][e] = __fmaf_rn(wr[j * WK + i], v[e + i], s[py][e]);
                     }
                 }
-            }
-            const int gy = y0 - HS + r;
+                float* sr = gSs + ch * G::PLANE_S + r0 * G::PPS + c0;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int gx = x0 - HS + c0 + e;
+                for (int py = 0; py < 4; ++py)
+                    *reinterpret_cast<float4*>(sr + py * G::PPS) = make_float4(s[py][0], s[py][1], s[py][2], s[py][3]);
+            }
+        }
+        __syncthreads();
+        // (3b) gS from the window sums and gR, in place (zero outside the image); all of a
+        //     thread's gR loads issued first
+        {
+            constexpr int N = G::RS * G::CS, NQ = (N + kHbThreads - 1) / kHbThreads;
+            float gv[NQ];
+#pragma unroll
+            for (int n = 0; n < NQ; ++n) {
+                const int q = tid + n * kHbThreads, r = q / G::CS, c = q - r * G::CS;
+                const int gy = y0 - HS + r, gx = x0 - HS + c;
+                gv[n] = q < N && gx >= 0 && gx < W && gy >= 0 && gy < H ? gR[(long long)gy * g_pitch + gx] : 0.f;
+            }
+#pragma unroll
+            for (int n = 0; n < NQ; ++n) {
+                const int q = tid + n * kHbThreads, r = q / G::CS, c = q - r * G::CS;
+                if (q >= N) continue;
+                const int gy = y0 - HS + r, gx = x0 - HS + c;
+                const int o = r * G::PPS + c;
                 float gxx = 0.f, gyy = 0.f, gxy = 0.f;
-                if (c0 + e < G::WS && gx >= 0 && gx < W && gy >= 0 && gy < H) {
-                    const float g = gR[(long long)gy * g_pitch + gx];
-                    const float tr = s[0][e] + s[1][e];
-                    gxx = g * (s[1][e] - 2.f * k * tr);
-                    gyy = g * (s[0][e] - 2.f * k * tr);
-                    gxy = -2.f * g * s[2][e];
+                if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+                    const float g = gv[n];
+                    const float sxx = gSs[o], syy = gSs[G::PLANE_S + o], sxy = gSs[2 * G::PLANE_S + o];
+                    const float tr = sxx + syy;
+                    gxx = g * (syy - 2.f * k * tr);
+                    gyy = g * (sxx - 2.f * k * tr);
+                    gxy = -2.f * g * sxy;
                 }
-                const int o = r * G::PPS + c0 + e;
                 gSs[o] = gxx;
                 gSs[G::PLANE_S + o] = gyy;
                 gSs[2 * G::PLANE_S + o] = gxy;
             }
         }
         __syncthreads();
-        // (4) window-tap gradient: dG[o] += sum_c gS_c(p) P_c(b(p + o)) over the tile's pixels
-        for (int it = tid; it < TB * (TB / 4); it += nth) {
-            const int tx0 = (it / TB) * 4, ty = it - (tx0 / 4) * TB;     // rows fastest
-            if (y0 + ty >= H) continue;
-            float g[3][4];
+        // (4) window-tap gradient: dG[o] += gS_c(p) P_c(b(p + o)) over the tile's pixels
+        //     (gS is zero outside the image), items of one channel x 4 rows x 4 columns
+        for (int it = tid; it < 3 * G::NRT * G::NCT; it += nth) {
+            const int ch = it / (G::NRT * G::NCT), rem = it - ch * (G::NRT * G::NCT);
+            const int r0 = (rem / G::NCT) * 4, c0 = (rem % G::NCT) * 4;
+            float g[4][4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const bool in = x0 + tx0 + e < W;
-                const int o = (ty + HS) * G::PPS + tx0 + e + HS;
+            for (int py = 0; py < 4; ++py)
 #pragma unroll
-                for (int ch = 0; ch < 3; ++ch) g[ch][e] = in ? gSs[ch * G::PLANE_S + o] : 0.f;
-            }
+                for (int e = 0; e < 4; ++e) g[py][e] = gSs[ch * G::PLANE_S + (r0 + py + HS) * G::PPS + c0 + e + HS];
+            const float* pr = Ps + ch * G::PLANE_P + (r0 + G::OFF4) * G::PPP + c0;
 #pragma unroll
-            for (int j = 0; j < WK; ++j) {
+            for (int jr = 0; jr < WK + 3; ++jr) {
+                float v[4 * G::NV4];
 #pragma unroll
-                for (int ch = 0; ch < 3; ++ch) {
-                    const float* pr = Ps + ch * G::PLANE_P + (ty + HP + j - RW) * G::PPP + tx0 + HP - RW;
-                    float v[4 + 2 * RW];
+                for (int q = 0; q < G::NV4; ++q) {
+                    const float4 f = *reinterpret_cast<const float4*>(pr + jr * G::PPP + 4 * q);
+                    v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+                }
 #pragma unroll
-                    for (int q = 0; q < 4 + 2 * RW; ++q) v[q] = pr[q];
+                for (int py = 0; py < 4; ++py) {
+                    const int j = jr - py;
+                    if (j < 0 || j >= WK) continue;
 #pragma unroll
                     for (int i = 0; i < WK; ++i)
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) aw[j * WK + i] = __fmaf_rn(g[ch][e], v[e + i], aw[j * WK + i]);
+                        for (int e = 0; e < 4; ++e) aw[j * WK + i] = __fmaf_rn(g[py][e], v[e + i + G::OFF4], aw[j * WK + i]);
                 }
             }
         }
-        // (5) gP (window adjoint, with the clamp folds on the image's edges) and gI on the
-        //     gI region, 4 columns per item (zero outside)
-        for (int it = tid; it < G::WG * G::NGI; it += nth) {
-            const int c0 = (it / G::WG) * 4, r = it - (c0 / 4) * G::WG;   // rows fastest
-            float gp[3][4];
+        __syncthreads();   // P is no longer read: (5) writes gP over it
+        // (5) gP_c on the gI region (window adjoint; the clamp folds follow in (5b)), items
+        //     of one channel x 4 rows x 4 columns over gS rows r0 .. r0 + 3 + 2RW
+        {
+            float wr[WK * WK];
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch)
+            for (int q = 0; q < WK * WK; ++q) wr[q] = gw[q];
+            for (int it = tid; it < 3 * G::NRG * G::NCG; it += nth) {
+                const int ch = it / (G::NRG * G::NCG), rem = it - ch * (G::NRG * G::NCG);
+                const int r0 = (rem / G::NCG) * 4, c0 = (rem % G::NCG) * 4;
+                float gp[4][4];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) gp[ch][e] = 0.f;
+                for (int py = 0; py < 4; ++py)
 #pragma unroll
-            for (int j = 0; j < WK; ++j) {
+                    for (int e = 0; e < 4; ++e) gp[py][e] = 0.f;
+                const float* gs = gSs + ch * G::PLANE_S;
 #pragma unroll
-                for (int ch = 0; ch < 3; ++ch) {
-                    // gS at q - o: gS-region row r + 2RW - j, columns c0 + e + 2RW - i
-                    const float* sr = gSs + ch * G::PLANE_S + (r + 2 * RW - j) * G::PPS + c0;
-                    float v[4 + 2 * RW];
+                for (int jr = 0; jr < WK + 3; ++jr) {
+                    float v[4 * G::NV];
 #pragma unroll
-                    for (int q = 0; q < 4 + 2 * RW; ++q) v[q] = sr[q];
+                    for (int q = 0; q < G::NV; ++q) {
+                        const float4 f = *reinterpret_cast<const float4*>(gs + (r0 + jr) * G::PPS + c0 + 4 * q);
+                        v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+                    }
 #pragma unroll
-                    for (int i = 0; i < WK; ++i) {
-                        const float w = gw[j * WK + i];
+                    for (int py = 0; py < 4; ++py) {
+                        const int j = py + 2 * RW - jr;        // gS at q - o: row r0 + py + 2RW - j
+                        if (j < 0 || j >= WK) continue;
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) gp[ch][e] = __fmaf_rn(w, v[e + 2 * RW - i], gp[ch][e]);
+                        for (int i = 0; i < WK; ++i)
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) gp[py][e] = __fmaf_rn(wr[j * WK + i], v[e + 2 * RW - i], gp[py][e]);
                     }
                 }
-            }
-            const int gy = y0 - 1 + r;
+                float* gq = Ps + ch * G::PLANE_P + r0 * G::PPP + c0;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int gx = x0 - 1 + c0 + e;
-                float gix = 0.f, giy = 0.f;
-                if (c0 + e < G::WG && gx >= 0 && gx < W && gy >= 0 && gy < H) {
-                    if (gx == 0 || gy == 0 || gx == W - 1 || gy == H - 1) {
-                        // offsets clamped onto this edge pixel: p + o outside, b(p + o) = q
-                        for (int py = max(gy - RW, 0); py <= min(gy + RW, H - 1); ++py)
-                            for (int px = max(gx - RW, 0); px <= min(gx + RW, W - 1); ++px)
-                                for (int j = 0; j < WK; ++j)
-                                    for (int i = 0; i < WK; ++i) {
-                                        const int qy = py + j - RW, qx = px + i - RW;
-                                        if (qx >= 0 && qx < W && qy >= 0 && qy < H) continue;
-                                        if (clampi(qx, 0, W - 1) != gx || clampi(qy, 0, H - 1) != gy) continue;
-                                        const int o = (py - (y0 - HS)) * G::PPS + px - (x0 - HS);
-                                        const float w = gw[j * WK + i];
-#pragma unroll
-                                        for (int ch = 0; ch < 3; ++ch)
-                                            gp[ch][e] = __fmaf_rn(w, gSs[ch * G::PLANE_S + o], gp[ch][e]);
-                                    }
-                    }
-                    const int op = (r + HP - 1) * G::PPP + c0 + e + HP - 1;
-                    const float ix = Ixs[op], iy = Iys[op];
-                    gix = 2.f * ix * gp[0][e] + iy * gp[2][e];
-                    giy = 2.f * iy * gp[1][e] + ix * gp[2][e];
-                }
-                const int o = r * G::PPG + c0 + e;
-                gIs[o] = gix;
-                gIs[G::PLANE_G + o] = giy;
+                for (int py = 0; py < 4; ++py)
+                    *reinterpret_cast<float4*>(gq + py * G::PPP) = make_float4(gp[py][0], gp[py][1], gp[py][2], gp[py][3]);
             }
         }
         __syncthreads();
-        // (6) dI on the tile (Sobel adjoint with the clamp folds) and the Sobel tap gradients
-        for (int q = tid; q < TB * TB; q += nth) {
-            const int ty = q / TB, tx = q - ty * TB;
-            const int gy = y0 + ty, gx = x0 + tx;
-            if (gy >= H || gx >= W) continue;
-            float acc = 0.f;
-#pragma unroll
-            for (int j = 0; j < 3; ++j)
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    // gI at q - o: gI-region (ty + 1 - (j - 1), tx + 1 - (i - 1))
-                    const int o = (ty + 2 - j) * G::PPG + tx + 2 - i;
-                    acc = __fmaf_rn(sxw[j * 3 + i], gIs[o], acc);
-                    acc = __fmaf_rn(syw[j * 3 + i], gIs[G::PLANE_G + o], acc);
-                }
-            if (gx == 0 || gy == 0 || gx == W - 1 || gy == H - 1) {
-                for (int py = max(gy - 1, 0); py <= min(gy + 1, H - 1); ++py)
-                    for (int px = max(gx - 1, 0); px <= min(gx + 1, W - 1); ++px)
-                        for (int j = 0; j < 3; ++j)
-                            for (int i = 0; i < 3; ++i) {
-                                const int qy = py + j - 1, qx = px + i - 1;
-                                if (qx >= 0 && qx < W && qy >= 0 && qy < H) continue;
-                                if (clampi(qx, 0, W - 1) != gx || clampi(qy, 0, H - 1) != gy) continue;
-                                const int o = (py - (y0 - 1)) * G::PPG + px - (x0 - 1);
-                                acc = __fmaf_rn(sxw[j * 3 + i], gIs[o], acc);
-                                acc = __fmaf_rn(syw[j * 3 + i], gIs[G::PLANE_G + o], acc);
-                            }
+        // (5b) gI from gP and (Ix, Iy), in place over Ix, Iy (zero outside the image); on the
+        //     image's edges gP first collects the window offsets clamped onto the pixel
+        for (int q = tid; q < G::RG * G::CG; q += kHbThreads) {
+            const int r = q / G::CG, c = q - r * G::CG;
+            const int gy = y0 - 1 + r, gx = x0 - 1 + c;
+            const int o = r * G::PPG + c, op = r * G::PPP + c;
+            float gix = 0.f, giy = 0.f;
+            if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+                const float ix = gIs[o], iy = gIs[G::PLANE_G + o];
+                float gxx = Ps[op], gyy = Ps[G::PLANE_P + op], gxy = Ps[2 * G::PLANE_P + op];
+                if (border_tile && (gx == 0 || gy == 0 || gx == W - 1 || gy == H - 1))
+                    hb_clamp_fold<RW>(gx, gy, W, H, [&](int j, int i, int py, int px) {
+                        const int os = (py - (y0 - HS)) * G::PPS + px - (x0 - HS);
+                        const float w = gw[j * WK + i];
+                        gxx = __fmaf_rn(w, gSs[os], gxx);
+                        gyy = __fmaf_rn(w, gSs[G::PLANE_S + os], gyy);
+                        gxy = __fmaf_rn(w, gSs[2 * G::PLANE_S + os], gxy);
+                    });
+                gix = 2.f * ix * gxx + iy * gxy;
+                giy = 2.f * iy * gyy + ix * gxy;
             }
-            if (dI) dI[(long long)gy * d_pitch + gx] = acc;
-            const int og = (ty + 1) * G::PPG + tx + 1;
-            const float gix = gIs[og], giy = gIs[G::PLANE_G + og];
+            gIs[o] = gix;
+            gIs[G::PLANE_G + o] = giy;
+        }
+        __syncthreads();
+        // (6) dI on the tile (Sobel adjoint with the clamp folds) and the Sobel tap
+        //     gradients: columns fastest, 4 rows per item over gI rows r0 .. r0 + 5
+        for (int q = tid; q < G::NRT * TW; q += nth) {
+            const int r0 = (q / TW) * 4, tx = q - (r0 / 4) * TW;
+            const int gx = x0 + tx;
+            if (gx >= W || y0 + r0 >= H) continue;
+            float gc[2][4];                       // gIx, gIy at the item's pixels
+            {
+                float ga[6][3], gb[6][3];
 #pragma unroll
-            for (int j = 0; j < 3; ++j)
+                for (int jj = 0; jj < 6; ++jj)
 #pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    const float u = Is[(ty + HI + j - 1) * G::PPI + tx + XI + i - 1];   // I(b(p + o))
-                    asx[j * 3 + i] = __fmaf_rn(gix, u, asx[j * 3 + i]);
-                    asy[j * 3 + i] = __fmaf_rn(giy, u, asy[j * 3 + i]);
+                    for (int i = 0; i < 3; ++i) {
+                        ga[jj][i] = gIs[(r0 + jj) * G::PPG + tx + i];
+                        gb[jj][i] = gIs[G::PLANE_G + (r0 + jj) * G::PPG + tx + i];
+                    }
+#pragma unroll
+                for (int py = 0; py < 4; ++py) {
+                    const int gy = y0 + r0 + py;
+                    gc[0][py] = ga[py + 1][1];
+                    gc[1][py] = gb[py + 1][1];
+                    if (gy >= H) continue;
+                    float acc = 0.f;
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) {
+                            // gI at q - o: gI-region (ty + 1 - (j - 1), tx + 1 - (i - 1))
+                            acc = __fmaf_rn(sxw[j * 3 + i], ga[py + 2 - j][2 - i], acc);
+                            acc = __fmaf_rn(syw[j * 3 + i], gb[py + 2 - j][2 - i], acc);
+                        }
+                    if (border_tile && (gx == 0 || gy == 0 || gx == W - 1 || gy == H - 1))
+                        hb_clamp_fold<1>(gx, gy, W, H, [&](int j, int i, int py2, int px2) {
+                            const int o = (py2 - (y0 - 1)) * G::PPG + px2 - (x0 - 1);
+                            acc = __fmaf_rn(sxw[j * 3 + i], gIs[o], acc);
+                            acc = __fmaf_rn(syw[j * 3 + i], gIs[G::PLANE_G + o], acc);
+                        });
+                    if (dI) dI[(long long)gy * d_pitch + gx] = acc;
                 }
+            }
+            float u[6][3];                        // I(b(p + o)) rows around the item
+#pragma unroll
+            for (int jj = 0; jj < 6; ++jj)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) u[jj][i] = Is[(r0 + jj + HI - 1) * G::PPI + tx + HI - 1 + i];
+#pragma unroll
+            for (int py = 0; py < 4; ++py) {
+                if (y0 + r0 + py >= H) break;
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        asx[j * 3 + i] = __fmaf_rn(gc[0][py], u[py + j][i], asx[j * 3 + i]);
+                        asy[j * 3 + i] = __fmaf_rn(gc[1][py], u[py + j][i], asy[j * 3 + i]);
+                    }
+            }
         }
     }
     // combine the threads' tap sums in a fixed order into this CTA's partials

@@ -88,7 +88,8 @@ def test_harris_backward_matches_oracle(wk):
     sx = synth.sobel_x() + 0.1 * g.standard_normal((3, 3)).astype(np.float32)
     sy = synth.sobel_y() + 0.1 * g.standard_normal((3, 3)).astype(np.float32)
     win = synth.gaussian_window(wk, 1.0) if wk % 2 else (g.random((wk, wk)) + 0.5).astype(np.float32)
-    for (h, wd) in [(1, 1), (3, 7), (16, 16), (45, 60), (100, 133)]:
+    # 150 x 300 holds interior tiles of the fused adjoint (64 x 32 tiles with a 6-pixel halo)
+    for (h, wd) in [(1, 1), (3, 7), (16, 16), (45, 60), (100, 133), (150, 300)]:
         img = synth.rectangles_image(g, h, wd, n_rect=10, side_lo=2, side_hi=max(3, min(h, wd)))
         gR = g.standard_normal((h, wd)).astype(np.float32)
         ref = oracle.harris_backward(img, sx, sy, win, gR, 0.04)
