@@ -73,7 +73,7 @@ struct HbGeo {
     static constexpr int PPP = hb_odd_quads(hb_max(hb_max(CP, 4 * NCG), hb_max(4 * (NCS - 1) + 4 * NV, 4 * (NCT - 1) + 4 * NV4)));
     static constexpr int SRS = hb_max(4 * NRS, 4 * NRG + 2 * RW);
     static constexpr int PPS = hb_odd_quads(hb_max(4 * NCS, 4 * (NCG - 1) + 4 * NV));
-    static constexpr int PPG = CG;
+    static constexpr int PPG = round_up(CG, 4);                          // quads, for (5b)
     static constexpr int NTAP = WK * WK + 18;                               // window, Sobel x, Sobel y
     // shared memory (floats): taps, I, Pxx Pyy Pxy (later gPxx gPyy gPxy),
     // gSxx gSyy gSxy (first the window sums), Ix Iy (later gIx gIy)
@@ -86,7 +86,7 @@ struct HbGeo {
     static constexpr int PLANE_G = PPG * RG;
     static constexpr int O_G = O_S + 3 * PLANE_S;
     static constexpr int TOTAL = O_G + 2 * PLANE_G;
-    static_assert(PLANE_P % 4 == 0 && PLANE_S % 4 == 0, "quad-aligned planes");
+    static_assert(PLANE_P % 4 == 0 && PLANE_S % 4 == 0 && PLANE_G % 4 == 0, "quad-aligned planes");
 };
 
 constexpr int kHbThreads = 256;                   // threads per CTA (the launch uses exactly this)
@@ -163,8 +163,31 @@ __global__ void __launch_bounds__(kHbThreads, 2)
     for (int q = 0; q < 9; ++q) { asx[q] = 0.f; asy[q] = 0.f; }
 
     const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH;
+    // Tiles whose halo leaves the image take the slower clamped paths.  They lie in tile
+    // row 0 and rows ryb.., tile column 0 and columns cxb.. (TH, TW > HI); the CTAs take
+    // tiles round-robin in the order border rows, then the border columns of the other
+    // rows, then the interior, so each gets about the same share of border tiles (a
+    // static order: the tap-gradient partials stay reproducible).
+    int ryb = tiles_y, cxb = tiles_x;
+    while (ryb > 1 && (ryb - 1) * TH + TH + HI > H) --ryb;
+    while (cxb > 1 && (cxb - 1) * TW + TW + HI > W) --cxb;
+    const int nbr = 1 + tiles_y - ryb, nbc = 1 + tiles_x - cxb, nic = cxb - 1;
     for (int t = blockIdx.x; t < tiles_x * tiles_y; t += gridDim.x) {
-        const int x0 = (t % tiles_x) * TW, y0 = (t / tiles_x) * TH;
+        int tx, ty;
+        if (t < nbr * tiles_x) {
+            const int rr = t / tiles_x;
+            ty = rr == 0 ? 0 : ryb + rr - 1;
+            tx = t - rr * tiles_x;
+        } else if (t < nbr * tiles_x + (ryb - 1) * nbc) {
+            const int o = t - nbr * tiles_x, cc = o % nbc;
+            ty = 1 + o / nbc;
+            tx = cc == 0 ? 0 : cxb + cc - 1;
+        } else {
+            const int o = t - nbr * tiles_x - (ryb - 1) * nbc;
+            ty = 1 + o / nic;
+            tx = 1 + o % nic;
+        }
+        const int x0 = tx * TW, y0 = ty * TH;
         const bool border_tile = x0 - HI < 0 || y0 - HI < 0 || x0 + TW + HI > W || y0 + TH + HI > H;
         __syncthreads();   // taps staged / the previous tile's planes are no longer read
         // (1) I on the I region (rows from y0 - HI, columns from x0 - HI), at clamped positions
@@ -268,35 +291,43 @@ __global__ void __launch_bounds__(kHbThreads, 2)
             }
         }
         __syncthreads();
-        // (3b) gS from the window sums and gR, in place (zero outside the image); all of a
-        //     thread's gR loads issued first
+        // (3b) gS from the window sums and gR, in place (zero outside the image), one quad
+        //     of columns per item; all of a thread's gR loads issued first
         {
-            constexpr int N = G::RS * G::CS, NQ = (N + kHbThreads - 1) / kHbThreads;
-            float gv[NQ];
+            constexpr int N = G::RS * G::NCS, NQ = (N + kHbThreads - 1) / kHbThreads;
+            float gv[NQ][4];
 #pragma unroll
             for (int n = 0; n < NQ; ++n) {
-                const int q = tid + n * kHbThreads, r = q / G::CS, c = q - r * G::CS;
+                const int q = tid + n * kHbThreads, r = q / G::NCS, c = (q - r * G::NCS) * 4;
                 const int gy = y0 - HS + r, gx = x0 - HS + c;
-                gv[n] = q < N && gx >= 0 && gx < W && gy >= 0 && gy < H ? gR[(long long)gy * g_pitch + gx] : 0.f;
+                const bool row_in = q < N && gy >= 0 && gy < H;
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    gv[n][e] = row_in && gx + e >= 0 && gx + e < W && c + e < G::CS ? gR[(long long)gy * g_pitch + gx + e] : 0.f;
             }
 #pragma unroll
             for (int n = 0; n < NQ; ++n) {
-                const int q = tid + n * kHbThreads, r = q / G::CS, c = q - r * G::CS;
+                const int q = tid + n * kHbThreads, r = q / G::NCS, c = (q - r * G::NCS) * 4;
                 if (q >= N) continue;
+                float* o = gSs + r * G::PPS + c;
+                const float4 sxx = *reinterpret_cast<const float4*>(o);
+                const float4 syy = *reinterpret_cast<const float4*>(o + G::PLANE_S);
+                const float4 sxy = *reinterpret_cast<const float4*>(o + 2 * G::PLANE_S);
+                const float a[4] = {sxx.x, sxx.y, sxx.z, sxx.w}, b[4] = {syy.x, syy.y, syy.z, syy.w};
+                const float d[4] = {sxy.x, sxy.y, sxy.z, sxy.w};
                 const int gy = y0 - HS + r, gx = x0 - HS + c;
-                const int o = r * G::PPS + c;
-                float gxx = 0.f, gyy = 0.f, gxy = 0.f;
-                if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-                    const float g = gv[n];
-                    const float sxx = gSs[o], syy = gSs[G::PLANE_S + o], sxy = gSs[2 * G::PLANE_S + o];
-                    const float tr = sxx + syy;
-                    gxx = g * (syy - 2.f * k * tr);
-                    gyy = g * (sxx - 2.f * k * tr);
-                    gxy = -2.f * g * sxy;
+                float gxx[4], gyy[4], gxy[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const bool in = gy >= 0 && gy < H && gx + e >= 0 && gx + e < W;
+                    const float g = gv[n][e], tr = a[e] + b[e];
+                    gxx[e] = in ? g * (b[e] - 2.f * k * tr) : 0.f;
+                    gyy[e] = in ? g * (a[e] - 2.f * k * tr) : 0.f;
+                    gxy[e] = in ? -2.f * g * d[e] : 0.f;
                 }
-                gSs[o] = gxx;
-                gSs[G::PLANE_S + o] = gyy;
-                gSs[2 * G::PLANE_S + o] = gxy;
+                *reinterpret_cast<float4*>(o) = make_float4(gxx[0], gxx[1], gxx[2], gxx[3]);
+                *reinterpret_cast<float4*>(o + G::PLANE_S) = make_float4(gyy[0], gyy[1], gyy[2], gyy[3]);
+                *reinterpret_cast<float4*>(o + 2 * G::PLANE_S) = make_float4(gxy[0], gxy[1], gxy[2], gxy[3]);
             }
         }
         __syncthreads();
@@ -371,29 +402,39 @@ __global__ void __launch_bounds__(kHbThreads, 2)
             }
         }
         __syncthreads();
-        // (5b) gI from gP and (Ix, Iy), in place over Ix, Iy (zero outside the image); on the
-        //     image's edges gP first collects the window offsets clamped onto the pixel
-        for (int q = tid; q < G::RG * G::CG; q += kHbThreads) {
-            const int r = q / G::CG, c = q - r * G::CG;
+        // (5b) gI from gP and (Ix, Iy), in place over Ix, Iy (zero outside the image), one
+        //     quad of columns per item; on the image's edges gP first collects the window
+        //     offsets clamped onto the pixel
+        for (int q = tid; q < G::RG * G::NCG; q += kHbThreads) {
+            const int r = q / G::NCG, c = (q - r * G::NCG) * 4;
             const int gy = y0 - 1 + r, gx = x0 - 1 + c;
-            const int o = r * G::PPG + c, op = r * G::PPP + c;
-            float gix = 0.f, giy = 0.f;
-            if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-                const float ix = gIs[o], iy = gIs[G::PLANE_G + o];
-                float gxx = Ps[op], gyy = Ps[G::PLANE_P + op], gxy = Ps[2 * G::PLANE_P + op];
-                if (border_tile && (gx == 0 || gy == 0 || gx == W - 1 || gy == H - 1))
-                    hb_clamp_fold<RW>(gx, gy, W, H, [&](int j, int i, int py, int px) {
-                        const int os = (py - (y0 - HS)) * G::PPS + px - (x0 - HS);
+            float* o = gIs + r * G::PPG + c;
+            const float* op = Ps + r * G::PPP + c;
+            const float4 vx = *reinterpret_cast<const float4*>(o), vy = *reinterpret_cast<const float4*>(o + G::PLANE_G);
+            const float4 vxx = *reinterpret_cast<const float4*>(op);
+            const float4 vyy = *reinterpret_cast<const float4*>(op + G::PLANE_P);
+            const float4 vxy = *reinterpret_cast<const float4*>(op + 2 * G::PLANE_P);
+            const float ix[4] = {vx.x, vx.y, vx.z, vx.w}, iy[4] = {vy.x, vy.y, vy.z, vy.w};
+            float gxx[4] = {vxx.x, vxx.y, vxx.z, vxx.w}, gyy[4] = {vyy.x, vyy.y, vyy.z, vyy.w};
+            float gxy[4] = {vxy.x, vxy.y, vxy.z, vxy.w};
+            float gix[4], giy[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int px = gx + e;
+                const bool in = c + e < G::CG && px >= 0 && px < W && gy >= 0 && gy < H;
+                if (in && border_tile && (px == 0 || gy == 0 || px == W - 1 || gy == H - 1))
+                    hb_clamp_fold<RW>(px, gy, W, H, [&](int j, int i, int sy, int sx) {
+                        const int os = (sy - (y0 - HS)) * G::PPS + sx - (x0 - HS);
                         const float w = gw[j * WK + i];
-                        gxx = __fmaf_rn(w, gSs[os], gxx);
-                        gyy = __fmaf_rn(w, gSs[G::PLANE_S + os], gyy);
-                        gxy = __fmaf_rn(w, gSs[2 * G::PLANE_S + os], gxy);
+                        gxx[e] = __fmaf_rn(w, gSs[os], gxx[e]);
+                        gyy[e] = __fmaf_rn(w, gSs[G::PLANE_S + os], gyy[e]);
+                        gxy[e] = __fmaf_rn(w, gSs[2 * G::PLANE_S + os], gxy[e]);
                     });
-                gix = 2.f * ix * gxx + iy * gxy;
-                giy = 2.f * iy * gyy + ix * gxy;
+                gix[e] = in ? 2.f * ix[e] * gxx[e] + iy[e] * gxy[e] : 0.f;
+                giy[e] = in ? 2.f * iy[e] * gyy[e] + ix[e] * gxy[e] : 0.f;
             }
-            gIs[o] = gix;
-            gIs[G::PLANE_G + o] = giy;
+            *reinterpret_cast<float4*>(o) = make_float4(gix[0], gix[1], gix[2], gix[3]);
+            *reinterpret_cast<float4*>(o + G::PLANE_G) = make_float4(giy[0], giy[1], giy[2], giy[3]);
         }
         __syncthreads();
         // (6) dI on the tile (Sobel adjoint with the clamp folds) and the Sobel tap
