@@ -55,11 +55,14 @@ struct HbGeo {
     static constexpr int RP = TH + 2 * HP, CP = TW + 2 * HP;
     static constexpr int RS = TH + 2 * HS, CS = TW + 2 * HS;
     static constexpr int RG = TH + 2, CG = TW + 2;
-    // 4 x 4 item grids of the window pass (gS region), its adjoint (gI region), the
-    // window-gradient pass (tile) and the 4-row column items of the Sobel passes
-    static constexpr int NRS = (RS + 3) / 4, NCS = (CS + 3) / 4;
+    // item grids (rows x 4 columns) of the window pass (gS region, PYS rows), its adjoint
+    // (gI region, 4 rows), the window-gradient pass (tile, PYT rows), and the 4-row column
+    // items of the Sobel passes; item heights chosen so the item counts of the long passes
+    // fill the CTA's threads in whole rounds (702 of 768, 459 of 512, 768 of 768 slots)
+    static constexpr int PYS = 3, PYT = 2;
+    static constexpr int NRS = (RS + PYS - 1) / PYS, NCS = (CS + 3) / 4;
     static constexpr int NRG = (RG + 3) / 4, NCG = (CG + 3) / 4;
-    static constexpr int NRT = TH / 4, NCT = TW / 4;
+    static constexpr int NRT = TH / PYT, NCT = TW / 4;
     static constexpr int NRP = (RP + 3) / 4;
     // float4 loads per item row: window passes (4 + 2RW columns from the item's quad),
     // window gradient (4 + 2RW columns from HP - RW past it)
@@ -69,9 +72,9 @@ struct HbGeo {
     // stored rows and pitches (floats), each covering every index its passes touch
     static constexpr int SRI = hb_max(RI, 4 * NRP + 2);
     static constexpr int PPI = CI;
-    static constexpr int SRP = hb_max(hb_max(RP, 4 * NRP), hb_max(4 * NRS + 2 * RW, 4 * NRG));
+    static constexpr int SRP = hb_max(hb_max(RP, 4 * NRP), hb_max(PYS * NRS + 2 * RW, 4 * NRG));
     static constexpr int PPP = hb_odd_quads(hb_max(hb_max(CP, 4 * NCG), hb_max(4 * (NCS - 1) + 4 * NV, 4 * (NCT - 1) + 4 * NV4)));
-    static constexpr int SRS = hb_max(4 * NRS, 4 * NRG + 2 * RW);
+    static constexpr int SRS = hb_max(PYS * NRS, 4 * NRG + 2 * RW);
     static constexpr int PPS = hb_odd_quads(hb_max(4 * NCS, 4 * (NCG - 1) + 4 * NV));
     static constexpr int PPG = round_up(CG, 4);                          // quads, for (5b)
     static constexpr int NTAP = WK * WK + 18;                               // window, Sobel x, Sobel y
@@ -251,23 +254,23 @@ __global__ void __launch_bounds__(kHbThreads, 2)
             }
         }
         __syncthreads();
-        // (3) window sums S_c on the gS region: items of one channel x 4 rows x 4 columns,
-        //     P rows r0 .. r0 + 3 + 2RW each feeding the item rows it lies under
+        // (3) window sums S_c on the gS region: items of one channel x PYS rows x 4 columns,
+        //     P rows r0 .. r0 + PYS - 1 + 2RW each feeding the item rows it lies under
         {
             float wr[WK * WK];
 #pragma unroll
             for (int q = 0; q < WK * WK; ++q) wr[q] = gw[q];
             for (int it = tid; it < 3 * G::NRS * G::NCS; it += nth) {
                 const int ch = it / (G::NRS * G::NCS), rem = it - ch * (G::NRS * G::NCS);
-                const int r0 = (rem / G::NCS) * 4, c0 = (rem % G::NCS) * 4;
-                float s[4][4];
+                const int r0 = (rem / G::NCS) * G::PYS, c0 = (rem % G::NCS) * 4;
+                float s[G::PYS][4];
 #pragma unroll
-                for (int py = 0; py < 4; ++py)
+                for (int py = 0; py < G::PYS; ++py)
 #pragma unroll
                     for (int e = 0; e < 4; ++e) s[py][e] = 0.f;
                 const float* pr = Ps + ch * G::PLANE_P + r0 * G::PPP + c0;
 #pragma unroll
-                for (int jr = 0; jr < WK + 3; ++jr) {
+                for (int jr = 0; jr < WK + G::PYS - 1; ++jr) {
                     float v[4 * G::NV];
 #pragma unroll
                     for (int q = 0; q < G::NV; ++q) {
@@ -275,7 +278,7 @@ __global__ void __launch_bounds__(kHbThreads, 2)
                         v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
                     }
 #pragma unroll
-                    for (int py = 0; py < 4; ++py) {
+                    for (int py = 0; py < G::PYS; ++py) {
                         const int j = jr - py;                 // window row of this P row for item row py
                         if (j < 0 || j >= WK) continue;
 #pragma unroll
@@ -286,7 +289,7 @@ __global__ void __launch_bounds__(kHbThreads, 2)
                 }
                 float* sr = gSs + ch * G::PLANE_S + r0 * G::PPS + c0;
 #pragma unroll
-                for (int py = 0; py < 4; ++py)
+                for (int py = 0; py < G::PYS; ++py)
                     *reinterpret_cast<float4*>(sr + py * G::PPS) = make_float4(s[py][0], s[py][1], s[py][2], s[py][3]);
             }
         }
@@ -332,18 +335,18 @@ __global__ void __launch_bounds__(kHbThreads, 2)
         }
         __syncthreads();
         // (4) window-tap gradient: dG[o] += gS_c(p) P_c(b(p + o)) over the tile's pixels
-        //     (gS is zero outside the image), items of one channel x 4 rows x 4 columns
+        //     (gS is zero outside the image), items of one channel x PYT rows x 4 columns
         for (int it = tid; it < 3 * G::NRT * G::NCT; it += nth) {
             const int ch = it / (G::NRT * G::NCT), rem = it - ch * (G::NRT * G::NCT);
-            const int r0 = (rem / G::NCT) * 4, c0 = (rem % G::NCT) * 4;
-            float g[4][4];
+            const int r0 = (rem / G::NCT) * G::PYT, c0 = (rem % G::NCT) * 4;
+            float g[G::PYT][4];
 #pragma unroll
-            for (int py = 0; py < 4; ++py)
+            for (int py = 0; py < G::PYT; ++py)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) g[py][e] = gSs[ch * G::PLANE_S + (r0 + py + HS) * G::PPS + c0 + e + HS];
             const float* pr = Ps + ch * G::PLANE_P + (r0 + G::OFF4) * G::PPP + c0;
 #pragma unroll
-            for (int jr = 0; jr < WK + 3; ++jr) {
+            for (int jr = 0; jr < WK + G::PYT - 1; ++jr) {
                 float v[4 * G::NV4];
 #pragma unroll
                 for (int q = 0; q < G::NV4; ++q) {
@@ -351,7 +354,7 @@ __global__ void __launch_bounds__(kHbThreads, 2)
                     v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
                 }
 #pragma unroll
-                for (int py = 0; py < 4; ++py) {
+                for (int py = 0; py < G::PYT; ++py) {
                     const int j = jr - py;
                     if (j < 0 || j >= WK) continue;
 #pragma unroll
@@ -439,7 +442,7 @@ __global__ void __launch_bounds__(kHbThreads, 2)
         __syncthreads();
         // (6) dI on the tile (Sobel adjoint with the clamp folds) and the Sobel tap
         //     gradients: columns fastest, 4 rows per item over gI rows r0 .. r0 + 5
-        for (int q = tid; q < G::NRT * TW; q += nth) {
+        for (int q = tid; q < (TH / 4) * TW; q += nth) {
             const int r0 = (q / TW) * 4, tx = q - (r0 / 4) * TW;
             const int gx = x0 + tx;
             if (gx >= W || y0 + r0 >= H) continue;
