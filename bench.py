@@ -609,7 +609,7 @@ def extra_stencils(hbm_gbs, fp32_peak, budget, imad_peak=None, bf16_tflops=FALLB
     px = 5120 * 5120
     flops_box2 = 2 * 18 * (5122 * 5122) / px + 3 + 2 * 3 * 4 + 7   # algorithmic: a 2x2 window
     out["paper_harris_5120_f32_box2"] = _entry(px, tt, tp, 8, flops_box2, hbm_gbs, fp32_peak, res["variant"],
-                                               "even window run as the 3x3 kernel with a zero row and column")
+                                               "the 2x2 block runs in its own fused kernels (products over one extra row and column, 4 window taps)")
     del x, y, ws
 
     # ragged batch: 256 f16 images, one graph launch forward and one backward
