@@ -651,7 +651,7 @@ def extra_stencils(hbm_gbs, fp32_peak, budget, imad_peak=None, bf16_tflops=FALLB
     roof_bwd_ms = sum(max(it.width * it.height * 10 / (hbm_gbs * 1e9), f / (fp32_peak * 1e12))
                       for it, f in zip(items, bw_flops)) * 1e3
     eb = _entry(info["pixels"], tbw, None, 10.0, sum(bw_flops) / info["pixels"], hbm_gbs, fp32_peak,
-                note="input and tap gradients of every image, one graph launch (three persistent phases)")
+                note="input and tap gradients of every image, one graph launch (the input gradients in the pipelined tile kernel beside the tap-gradient tiles, then per-image reductions)")
     eb["roofline_frac"] = roof_bwd_ms / tbw
     out["batch256_f16_bwd"] = eb
     b.close()

@@ -280,12 +280,13 @@ imcl_status imagecl_batch_create(const imcl_batch_item *items, int32_t n, double
 imcl_status imagecl_batch_run(imcl_batch *batch, void *stream);
 /*
  * Backward over the whole batch (the adjoints of imagecl_conv2d_backward and
- * imagecl_sepconv_backward for every item with a grad_out): one graph launch that runs
- * three persistent phases in order -- (1) conv2d input-gradient tiles with their tap
- * partial sums, the folded edge pixels of clamped conv2d items, and the separable column
- * adjoint (into a plan-owned plane) with its column-tap partials; (2) the separable row
- * adjoint with its row-tap partials; (3) fixed-order reductions of the partial sums into
- * grad_taps / grad_taps2.  IMCL_ERR_INVALID if no item carries gradient buffers.
+ * imagecl_sepconv_backward for every item with a grad_out): one graph launch.  On one
+ * branch the forward's pipelined tile kernel computes every grad_in as the correlation of
+ * grad_out with the flipped taps under a zero border and adds the clamp folds at the edge
+ * pixels of clamped items; beside it a persistent phase computes each tile's tap-gradient
+ * partial sums (conv2d: the K x K taps; separable: column and row taps from one staging),
+ * followed by fixed-order reductions of the partial sums into grad_taps / grad_taps2.
+ * IMCL_ERR_INVALID if no item carries gradient buffers.
  */
 imcl_status imagecl_batch_backward(imcl_batch *batch, void *stream);
 imcl_status imagecl_batch_info(const imcl_batch *batch, imcl_batch_info_t *info);

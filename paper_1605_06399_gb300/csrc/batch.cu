@@ -98,17 +98,24 @@ static const void* fwd_kernel(int py) {
     return py == 4 ? (const void*)k_batch_fwd<4> : (const void*)k_batch_fwd<2>;
 }
 
-static imcl_status launch_fwd(const Batch& b, const BFwdTile* tiles, int ntiles, int py, int bx, int by,
-                              cudaStream_t s) {
+// One persistent launch of the pipelined tile kernel over `tiles`, taking indices from the
+// counter `queue` (reset first), with the image descriptors `imgs`.
+static imcl_status launch_fwd_list(const Batch& b, const BImg* imgs, int* queue, const BFwdTile* tiles, int ntiles,
+                                   int py, int bx, int by, cudaStream_t s) {
     const size_t smem = batch_smem_bytes(py, bx, by);
     const int occ = cached_occupancy(fwd_kernel(py), kFwdThreads, (int)smem);
     if (occ <= 0) return fail(IMCL_ERR_UNSUPPORTED, "batch: kernel cannot be resident");
     const int grid = std::max(1, std::min(ntiles, occ * b.dev->sm_count));
-    cudaError_t e = cudaMemsetAsync(b.queue, 0, sizeof(int), s);
+    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), s);
     if (e != cudaSuccess) return cuda_fail(e, "batch queue reset");
-    if (py == 4) k_batch_fwd<4><<<grid, kFwdThreads, smem, s>>>(b.dimgs, tiles, ntiles, b.queue, bx, by, b.dev->status);
-    else k_batch_fwd<2><<<grid, kFwdThreads, smem, s>>>(b.dimgs, tiles, ntiles, b.queue, bx, by, b.dev->status);
-    return cuda_fail(cudaGetLastError(), "batch forward launch");
+    if (py == 4) k_batch_fwd<4><<<grid, kFwdThreads, smem, s>>>(imgs, tiles, ntiles, queue, bx, by, b.dev->status);
+    else k_batch_fwd<2><<<grid, kFwdThreads, smem, s>>>(imgs, tiles, ntiles, queue, bx, by, b.dev->status);
+    return cuda_fail(cudaGetLastError(), "batch tile launch");
+}
+
+static imcl_status launch_fwd(const Batch& b, const BFwdTile* tiles, int ntiles, int py, int bx, int by,
+                              cudaStream_t s) {
+    return launch_fwd_list(b, b.dimgs, b.queue, tiles, ntiles, py, bx, by, s);
 }
 
 static const void* bwd_kernel(int py) {
@@ -117,20 +124,26 @@ static const void* bwd_kernel(int py) {
 
 size_t batch_bwd_smem_bytes(int py, int bx, int by) {
     const size_t TW = 4 * bx, TH = (size_t)py * by, K = kBatchMaxK, R = kBatchMaxR;
-    const size_t conv_dx = (TW + 16) * (TH + K - 1) + K * kTapStride;
-    const size_t conv_wg = std::max(TW * TH + (size_t)wg_xpitch<kBatchMaxK>((int)TW) * (TH + K - 1),
-                                    (size_t)256 * WgCfg<kBatchMaxK>::JR * K + K * K);
+    // conv2d tap-gradient tiles: g (TW x TH), x staged from column x0 - 8 (the widest
+    // filter's pitch), then the combine scratch and the K x K sums
+    const size_t conv_xw = (size_t)round_up(wg_xpitch<kBatchMaxK>((int)TW) + 4, 8);
+    const size_t conv_wg = std::max(TW * TH + conv_xw * (TH + K - 1),
+                                    (size_t)256 * BatchWg<kBatchMaxK>::JR * K + K * K);
+    // separable tap-gradient tiles: g, x, the row pass / column adjoint, taps, combine
     const size_t HH = TH + 2 * R, XW = TW + 16;
-    const size_t sep_dt = 2 * TW * HH + XW * HH + 32 + 1024;
-    const size_t sep_dx = 2 * XW * TH + 16 + 256 * K + 4;   // + the row-tap combine scratch
-    return std::max(std::max(conv_dx, conv_wg), std::max(sep_dt, sep_dx)) * sizeof(float);
+    const size_t sep = TW * HH + XW * HH + std::max(TW * HH, XW * TH) + 32 + 1024;
+    return std::max(conv_wg, sep) * sizeof(float);
 }
 
-// Backward plan: gradient pointers into the image descriptors, intermediate planes and
-// partial-sum buffers, three work lists, and the graph that runs them in order.
+// Backward plan: gradient pointers into the image descriptors, partial-sum buffers, the
+// input-gradient tiles for the pipelined tile kernel (on a second set of descriptors: g as
+// the image, gin as the output, a zero border, flipped taps, clamp folds at the edges),
+// the tap-gradient tiles, the per-image reductions, and the graph that runs them.
 static imcl_status plan_backward(Batch* b) {
     const int TW = 4 * b->bx, TH = b->py * b->by;
-    std::vector<BTile> l1, l2, l3;
+    std::vector<BTile> l1, l3;
+    std::vector<BImg> dxi = b->himgs;
+    std::vector<std::pair<double, BFwdTile>> dxt;
     bool any = false;
     for (int i = 0; i < (int)b->items.size(); ++i) {
         const imcl_batch_item& it = b->items[i];
@@ -164,25 +177,47 @@ static imcl_status plan_backward(Batch* b) {
             if (e != cudaSuccess) return cuda_fail(e, "batch partial sums");
             b->owned.push_back(im.part);
         }
-        if (it.op == IMCL_OP_SEPCONV && (im.gin || im.gtaps)) {
-            im.dt_pitch = ((long long)im.W + 31) / 32 * 32;
-            cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&im.dt), (size_t)im.dt_pitch * im.H * sizeof(float));
-            if (e != cudaSuccess) return cuda_fail(e, "batch intermediate plane");
-            b->owned.push_back(im.dt);
-        }
-        for (int y = 0; y < im.H; y += TH)
-            for (int x = 0; x < im.W; x += TW) {
-                if (it.op == IMCL_OP_CONV2D) {
-                    l1.push_back(BTile{i, BT_CONV_DX, x, y});
-                } else {
-                    l1.push_back(BTile{i, BT_SEP_DT, x, y});
-                    if (im.gin || im.gtaps) l2.push_back(BTile{i, BT_SEP_DX, x, y});
+        if (im.gin) {
+            // dx = the correlation of g with the taps rotated by 180 degrees under a zero
+            // border (the separable pair each flipped: the adjoint of row then column pass),
+            // plus the clamp folds at the edge pixels: the forward's own tiles, with g as the
+            // f32 image and gin as the output
+            BImg& d = dxi[i];
+            d.in = im.g;
+            d.in_dt = IMCL_F32;
+            d.in_pitch = im.g_pitch;
+            d.in_vec = im.g_vec;
+            d.out = im.gin;
+            d.out_dt = IMCL_F32;
+            d.out_pitch = im.gin_pitch;
+            d.border = IMCL_BORDER_CONSTANT;
+            d.bv = 0.f;
+            d.fold = im.border == IMCL_BORDER_CLAMP;
+            for (int y = 0; y < im.H; y += TH)
+                for (int x = 0; x < im.W; x += TW) {
+                    BFwdTile t{};
+                    t.in = im.g;
+                    t.taps = im.taps;
+                    t.taps2 = im.taps2;
+                    t.pitch_b = im.g_pitch * 4;
+                    t.W = im.W;
+                    t.H = im.H;
+                    t.K = im.K;
+                    t.es = 4;
+                    t.op = im.op;
+                    t.kw = im.kw;
+                    t.kh = im.kh;
+                    t.img = i;
+                    t.x0 = x;
+                    t.y0 = y;
+                    t.flip = 1;
+                    dxt.push_back({tile_cost(im, std::min(TW, im.W - x), std::min(TH, im.H - y)), t});
                 }
-            }
-        if (it.op == IMCL_OP_CONV2D && im.gin && im.border == IMCL_BORDER_CLAMP) {
-            const int nedge = (im.H > 1 ? 2 * im.W : im.W) + (im.W > 1 ? 2 : 1) * std::max(im.H - 2, 0);
-            for (int c = 0; c * 1024 < nedge; ++c) l1.push_back(BTile{i, BT_CONV_EDGE, c, 0});
         }
+        if (im.gtaps || im.gtaps2)
+            for (int y = 0; y < im.H; y += TH)
+                for (int x = 0; x < im.W; x += TW)
+                    l1.push_back(BTile{i, it.op == IMCL_OP_CONV2D ? BT_CONV_DW : BT_SEP_TAPS, x, y});
         if (im.gtaps || im.gtaps2) l3.push_back(BTile{i, BT_FINAL, 0, 0});
     }
     if (!any) return IMCL_OK;
@@ -193,26 +228,49 @@ static imcl_status plan_backward(Batch* b) {
         });
     };
     by_cost(l1);
-    by_cost(l2);
     imcl_status st;
     // the descriptors now carry gradient pointers: refresh the device copy
     cudaError_t e = cudaMemcpy(b->dimgs, b->himgs.data(), b->himgs.size() * sizeof(BImg), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "batch descriptors");
-    BTile *d1 = nullptr, *d2 = nullptr, *d3 = nullptr;
+    std::stable_sort(dxt.begin(), dxt.end(), [](const auto& a, const auto& c) { return a.first > c.first; });
+    std::vector<BFwdTile> dx_tiles;
+    dx_tiles.reserve(dxt.size());
+    for (auto& p : dxt) dx_tiles.push_back(p.second);
+    BImg* ddx = nullptr;
+    BFwdTile* ddxt = nullptr;
+    if ((st = upload(&ddx, dxi, &b->owned)) != IMCL_OK) return st;
+    if ((st = upload(&ddxt, dx_tiles, &b->owned)) != IMCL_OK) return st;
+    BTile *d1 = nullptr, *d3 = nullptr;
     if ((st = upload(&d1, l1, &b->owned)) != IMCL_OK) return st;
-    if ((st = upload(&d2, l2, &b->owned)) != IMCL_OK) return st;
     if ((st = upload(&d3, l3, &b->owned)) != IMCL_OK) return st;
     const size_t smem = batch_bwd_smem_bytes(b->py, b->bx, b->by);
     if ((st = set_smem_limit(bwd_kernel(b->py), (int)smem)) != IMCL_OK) return st;
     const int occ = cached_occupancy(bwd_kernel(b->py), 256, (int)smem);
     if (occ <= 0) return fail(IMCL_ERR_UNSUPPORTED, "batch backward: kernel cannot be resident");
     const int slots = occ * b->dev->sm_count;
+    const int ndx = (int)dx_tiles.size();
+    if (ndx > 0) {
+        e = cudaStreamCreateWithFlags(&b->cap_stream2, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "batch backward stream");
+    }
+    // The graph: the input-gradient tiles run on a branch beside the tap-gradient tiles
+    // (they write only grad_in, which the tap phases do not touch); the per-image
+    // reductions follow the tap tiles, and the branch joins at the end.
     e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "batch backward capture");
-    cudaMemsetAsync(b->queue, 0, 4 * sizeof(int), b->cap_stream);
-    const BTile* lists[3] = {d1, d2, d3};
-    const int counts[3] = {(int)l1.size(), (int)l2.size(), (int)l3.size()};
-    for (int ph = 0; ph < 3; ++ph) {
+    cudaMemsetAsync(b->queue + 1, 0, (kQueueSlots - 1) * sizeof(int), b->cap_stream);
+    imcl_status lst = IMCL_OK;
+    if (ndx > 0) {
+        cudaEventRecord(b->ev_fork, b->cap_stream);
+        cudaStreamWaitEvent(b->cap_stream2, b->ev_fork, 0);
+        lst = launch_fwd_list(*b, ddx, b->queue + 4, ddxt, ndx, b->py, b->bx, b->by, b->cap_stream2);
+        cudaEventRecord(b->ev_join, b->cap_stream2);
+    }
+    const BTile* lists[2] = {d1, d3};
+    const int counts[2] = {(int)l1.size(), (int)l3.size()};
+    for (int ph = 0; ph < 2; ++ph) {
         if (counts[ph] == 0) continue;
         const int grid = std::max(1, std::min(counts[ph], slots));
         if (b->py == 4)
@@ -220,15 +278,17 @@ static imcl_status plan_backward(Batch* b) {
         else
             k_batch_bwd<2><<<grid, 256, smem, b->cap_stream>>>(b->dimgs, lists[ph], counts[ph], b->queue + 1 + ph, b->bx, b->by);
     }
+    if (ndx > 0) cudaStreamWaitEvent(b->cap_stream, b->ev_join, 0);
     cudaError_t le = cudaGetLastError();
     e = cudaStreamEndCapture(b->cap_stream, &b->bwd_graph);
+    if (lst != IMCL_OK) return lst;
     if (le != cudaSuccess) return cuda_fail(le, "batch backward launch");
     if (e != cudaSuccess) return cuda_fail(e, "batch backward capture end");
     e = cudaGraphInstantiate(&b->bwd_exec, b->bwd_graph, 0);
     if (e != cudaSuccess) return cuda_fail(e, "batch backward graph instantiate");
     b->bwd_items[0] = counts[0];
     b->bwd_items[1] = counts[1];
-    b->bwd_items[2] = counts[2];
+    b->bwd_dx_tiles = ndx;
     return IMCL_OK;
 }
 
@@ -237,6 +297,9 @@ Batch::~Batch() {
     if (fwd_graph) cudaGraphDestroy(fwd_graph);
     if (bwd_exec) cudaGraphExecDestroy(bwd_exec);
     if (bwd_graph) cudaGraphDestroy(bwd_graph);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (cap_stream2) cudaStreamDestroy(cap_stream2);
     for (void* p : owned) cudaFree(p);
     if (cap_stream) cudaStreamDestroy(cap_stream);
 }
@@ -303,7 +366,7 @@ imcl_status batch_create(const imcl_batch_item* items, int n, double budget_s, B
     cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return bail(cuda_fail(e, "batch stream"));
     if ((st = upload(&b->dimgs, b->himgs, &b->owned)) != IMCL_OK) return bail(st);
-    e = cudaMalloc(reinterpret_cast<void**>(&b->queue), 4 * sizeof(int));
+    e = cudaMalloc(reinterpret_cast<void**>(&b->queue), kQueueSlots * sizeof(int));
     if (e != cudaSuccess) return bail(cuda_fail(e, "batch queue"));
     b->owned.push_back(b->queue);
 

@@ -11,6 +11,8 @@ struct BImg;
 struct BTile;
 struct BFwdTile;
 
+constexpr int kQueueSlots = 8;
+
 struct Batch {
     const DeviceInfo* dev = nullptr;
     std::vector<imcl_batch_item> items;
@@ -18,17 +20,22 @@ struct Batch {
     BImg* dimgs = nullptr;                 // device copy
     BFwdTile* tiles = nullptr;             // forward work list (device)
     int ntiles = 0;
-    int* queue = nullptr;                  // work-list counters (device), one per phase
+    int* queue = nullptr;                  // work-list counters (device): [0] forward, [1] the
+                                           // tap-gradient tiles, [2] the per-image reductions,
+                                           // [4] the input-gradient tiles
     int py = 4, bx = 32, by = 8;           // chosen tile shape (PX = 4)
     double pixels = 0;
     double fwd_ms_at_create = 0;
     double shape_ms[4] = {0, 0, 0, 0};
     cudaStream_t cap_stream = nullptr;     // private stream the graphs are recorded on
+    cudaStream_t cap_stream2 = nullptr;    // the backward graph's second branch
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraph_t fwd_graph = nullptr;
     cudaGraphExec_t fwd_exec = nullptr;
     cudaGraph_t bwd_graph = nullptr;
     cudaGraphExec_t bwd_exec = nullptr;
-    int bwd_items[3] = {0, 0, 0};          // work items per backward phase
+    int bwd_items[2] = {0, 0};             // tap-gradient tiles, per-image reductions
+    int bwd_dx_tiles = 0;                  // conv2d input-gradient tiles (pipelined kernel)
     std::vector<void*> owned;              // device allocations freed with the handle
     ~Batch();
 };

@@ -8,10 +8,13 @@
 // each tile's image rows into shared memory with bulk asynchronous copies, while the
 // consumer warps convert the previous tile to f32 (the image's storage type, its boundary
 // rule) and run the specialised device code for its operator and filter side: register-
-// blocked conv2d rows and the fused row+column separable computation.  The backward runs
-// as a few persistent phases of 256-thread CTAs that stage their own tiles
-// (input-gradient tiles, separable second pass, tap-gradient reductions), all recorded
-// in one CUDA graph.
+// blocked conv2d rows and the fused row+column separable computation.  In the backward
+// the conv2d items' input gradient is that same pipelined kernel run on the upstream
+// gradient with flipped taps and a zero border (the adjoint of a correlation); clamp folds
+// at the image's edge pixels are added after it.  The rest of the backward runs as a few
+// persistent phases of 256-thread CTAs that stage their own tiles (tap-gradient tiles,
+// the separable adjoint's two passes, per-image reductions), all recorded in one CUDA
+// graph.
 #pragma once
 
 #include "bulk_copy.cuh"
@@ -43,19 +46,16 @@ struct alignas(16) BImg {
     long long gin_pitch;
     float* gtaps;                      // tap gradients or nullptr
     float* gtaps2;
-    float* dt;                         // sep: batch-owned intermediate (pitch dt_pitch)
-    long long dt_pitch;
     float* part;                       // batch-owned partial sums: [tiles][ntap_parts]
     int tiles_x, tiles_y;
+    int fold;                          // input-gradient descriptors: add the clamp folds
 };
 
 // work item kinds
 enum : int {
     BT_FWD = 0,        // forward tile
-    BT_CONV_DX = 1,    // conv2d: input-gradient tile (zero-border flipped correlation) + tap partials
-    BT_CONV_EDGE = 2,  // conv2d: folded input gradient on the image's edge pixels (clamp rule)
-    BT_SEP_DT = 3,     // sep: dt tile (column adjoint with folds) + column-tap partials
-    BT_SEP_DX = 4,     // sep: dx tile (row adjoint with folds) + row-tap partials
+    BT_CONV_DW = 1,    // conv2d: tap-gradient partial sums of one tile
+    BT_SEP_TAPS = 3,   // sep: column- and row-tap partial sums of one tile
     BT_FINAL = 5,      // reduce one image's partial sums to its tap gradients
 };
 
@@ -220,12 +220,9 @@ constexpr int kTapStride = 16;
 
 // conv2d: accumulate one tile from a staged region (rows SW wide, origin (x0 - 8, y0 - R))
 // and the K x K taps (rows kTapStride apart) in shared memory, and store it.
-// flipped_zero: the backward's dx tiles (edge pixels of a clamped image belong to the
-// edge items).
 template <int K, int PY>
 __device__ __forceinline__ void conv_tile_compute(const BImg& im, int x0, int y0, int bx, int by, const float* st,
-                                                  int SW, const float* w, bool flipped_zero, void* dst,
-                                                  long long dst_pitch, int dst_dt, const int tid) {
+                                                  int SW, const float* w, const int tid) {
     constexpr int PX = 4;
     using G = TileGeo<__half, K, PX>;    // halo padded to 8 columns: 16-byte aligned staging
     if (tid >= bx * by) return;
@@ -260,58 +257,9 @@ __device__ __forceinline__ void conv_tile_compute(const BImg& im, int x0, int y0
                 for (int ox = 0; ox < PX; ++ox) acc[oy][ox] = __fmaf_rn(wr[i], seg[G::LO + ox + i], acc[oy][ox]);
         }
     }
-    if (!flipped_zero) {
 #pragma unroll
-        for (int oy = 0; oy < PY; ++oy)
-            store_row_any<PX>(dst, dst_dt, dst_pitch, x0 + tx * PX, y0 + ty * PY + oy, im.W, im.H, acc[oy]);
-        return;
-    }
-    const bool skip_edges = im.border == IMCL_BORDER_CLAMP;   // edge items own those
-#pragma unroll
-    for (int oy = 0; oy < PY; ++oy) {
-        const int gy = y0 + ty * PY + oy;
-        if (gy >= im.H) continue;
-#pragma unroll
-        for (int ox = 0; ox < PX; ++ox) {
-            const int gx = x0 + tx * PX + ox;
-            if (gx >= im.W) continue;
-            if (skip_edges && (gx == 0 || gy == 0 || gx == im.W - 1 || gy == im.H - 1)) continue;
-            store_px(dst, dst_dt, dst_pitch, gx, gy, acc[oy][ox]);
-        }
-    }
-}
-
-// conv2d tile with its own staging (the backward's input-gradient tiles): sm holds the
-// staged region (TW + 16) x (TH + K - 1), then the K x kTapStride tap table.
-template <int K, int PY>
-__device__ void batch_conv_tile(const BImg& im, int x0, int y0, int bx, int by, float* sm, bool flipped_zero,
-                                const float* g_src, long long g_pitch, void* dst, long long dst_pitch, int dst_dt,
-                                const int tid, const int nth) {
-    constexpr int PX = 4;
-    using G = TileGeo<__half, K, PX>;
-    const int TW = bx * PX, TH = by * PY, SW = TW + 2 * G::PAD, SH = TH + K - 1;
-    float* st = sm;
-    float* w = sm + SW * SH;
-    const int R = (K - 1) / 2, rx = (im.kw - 1) / 2, ry = (im.kh - 1) / 2;
-    // taps, centred into K x K (zero elsewhere); flipped for the adjoint
-    for (int i = tid; i < K * kTapStride; i += nth) {
-        const int j = i / kTapStride, c = i % kTapStride;
-        const int sj = j - (R - ry), sc = c - (R - rx);
-        float v = 0.f;
-        if (c < K && sj >= 0 && sj < im.kh && sc >= 0 && sc < im.kw) {
-            const int o = flipped_zero ? (im.kh - 1 - sj) * im.kw + (im.kw - 1 - sc) : sj * im.kw + sc;
-            v = im.taps[o];
-        }
-        w[i] = v;
-    }
-    if (flipped_zero)
-        stage_region(st, SW, SH, g_src, IMCL_F32, g_pitch, x0 - G::PAD, y0 - R, im.W, im.H, IMCL_BORDER_CONSTANT, 0.f, 1,
-                     tid, nth, im.g_vec);
-    else
-        stage_region(st, SW, SH, im.in, im.in_dt, im.in_pitch, x0 - G::PAD, y0 - R, im.W, im.H, im.border, im.bv, 0,
-                     tid, nth, im.in_vec);
-    __syncthreads();
-    conv_tile_compute<K, PY>(im, x0, y0, bx, by, st, SW, w, flipped_zero, dst, dst_pitch, dst_dt, tid);
+    for (int oy = 0; oy < PY; ++oy)
+        store_row_any<PX>(im.out, im.out_dt, im.out_pitch, x0 + tx * PX, y0 + ty * PY + oy, im.W, im.H, acc[oy]);
 }
 
 // The forward runs warp-specialised: 8 consumer warps (256 threads, named barrier 1)
@@ -338,7 +286,8 @@ struct alignas(16) BFwdTile {
     long long pitch_b;       // row pitch in bytes
     int W, H, K, es;         // size, compiled side, bytes per pixel
     int op, kw, kh, img;     // operator, caller's tap counts, image index
-    int x0, y0, pad0, pad1;  // tile origin
+    int x0, y0;              // tile origin
+    int flip, pad;           // flip: conv taps read rotated by 180 degrees (the adjoint)
 };
 
 // The forward's staged rows are TW + 16 pixels, stored kFwdPitchPad floats further
@@ -464,16 +413,17 @@ __device__ __forceinline__ void fwd_load_taps(const BFwdTile& ft, int lane, floa
             if (j < K && c < K) {
                 const int R = (K - 1) / 2;
                 const int sj = j - (R - (ft.kh - 1) / 2), sc = c - (R - (ft.kw - 1) / 2);
-                if (sj >= 0 && sj < ft.kh && sc >= 0 && sc < ft.kw) v = __ldg(ft.taps + sj * ft.kw + sc);
+                if (sj >= 0 && sj < ft.kh && sc >= 0 && sc < ft.kw)
+                    v = __ldg(ft.taps + (ft.flip ? (ft.kh - 1 - sj) * ft.kw + (ft.kw - 1 - sc) : sj * ft.kw + sc));
             }
         } else if (i < 2 * K) {
             const int R = (K - 1) / 2;
             if (i < K) {
                 const int o = i - (R - (ft.kw - 1) / 2);
-                if (o >= 0 && o < ft.kw) v = __ldg(ft.taps + o);
+                if (o >= 0 && o < ft.kw) v = __ldg(ft.taps + (ft.flip ? ft.kw - 1 - o : o));
             } else {
                 const int o = i - K - (R - (ft.kh - 1) / 2);
-                if (o >= 0 && o < ft.kh) v = __ldg(ft.taps2 + o);
+                if (o >= 0 && o < ft.kh) v = __ldg(ft.taps2 + (ft.flip ? ft.kh - 1 - o : o));
             }
         }
         tv[k] = v;
@@ -703,9 +653,9 @@ __device__ __forceinline__ void batch_fwd_dispatch(const BImg& im, int x0, int y
     if (im.op == IMCL_OP_CONV2D) {
         switch (im.K) {
             // small filters: 4 x PY blocks (contiguous stores; the segment loads are cheap)
-            case 3: conv_tile_compute<3, PY>(im, x0, y0, bx, by, st, SWP, w, false, im.out, im.out_pitch, im.out_dt, tid); break;
-            case 5: conv_tile_compute<5, PY>(im, x0, y0, bx, by, st, SWP, w, false, im.out, im.out_pitch, im.out_dt, tid); break;
-            case 7: conv_tile_compute<7, PY>(im, x0, y0, bx, by, st, SWP, w, false, im.out, im.out_pitch, im.out_dt, tid); break;
+            case 3: conv_tile_compute<3, PY>(im, x0, y0, bx, by, st, SWP, w, tid); break;
+            case 5: conv_tile_compute<5, PY>(im, x0, y0, bx, by, st, SWP, w, tid); break;
+            case 7: conv_tile_compute<7, PY>(im, x0, y0, bx, by, st, SWP, w, tid); break;
             // larger ones: a row of PXC pixels per thread (fewer shared-memory wavefronts per FMA)
             case 9: conv_fwd_compute<9, PXC>(im, x0, y0, TW, st, SWP, w, tid); break;
             case 11: conv_fwd_compute<11, PXC>(im, x0, y0, TW, st, SWP, w, tid); break;
@@ -722,6 +672,63 @@ __device__ __forceinline__ void batch_fwd_dispatch(const BImg& im, int x0, int y
             case 13: sep_tile_compute<6, PY>(im, x0, y0, bx, by, st, tb, w, tid); break;
             default: sep_tile_compute<7, PY>(im, x0, y0, bx, by, st, tb, w, tid); break;
         }
+    }
+}
+
+// Input-gradient tiles of clamped images: the transpose of the clamp folds every read the
+// forward made outside the image back onto the edge pixel it was clamped to.  The tile's
+// main pass stored z(q) at each pixel q, the correlation of g (zero outside the image)
+// with the flipped taps; z at an outside position e is the gradient the forward's read of
+// e received, so an edge pixel q adds z(e) for every outside e that clamps to q.  One
+// thread per edge pixel of the tile sums those positions in a fixed order, reading g from
+// the staged region (origin (x0 - 8, y0 - R), rows SWP apart: it holds every in-image g
+// position these sums reach) and skipping the terms that fall outside the image.  conv2d:
+// w is the K x K flipped table; separable: NT flipped row taps then NT column taps, the
+// 2D filter being their outer product (the clamped separable forward equals the clamped
+// 2D correlation with it).
+__device__ void fwd_fold_edges(const BImg& im, int x0, int y0, int TW, int TH, const float* st, int SWP,
+                               const float* w, int tid) {
+    const int W = im.W, H = im.H, K = im.K, R = (K - 1) / 2;
+    const int rx = (im.kw - 1) / 2, ry = (im.kh - 1) / 2;
+    const bool top = y0 == 0, bot = y0 + TH >= H, lft = x0 == 0, rgt = x0 + TW >= W;
+    const int tw = min(TW, W - x0), th = min(TH, H - y0);
+    const int ntop = top ? tw : 0, nbot = (bot && H > 1) ? tw : 0;
+    const int r0 = top ? 1 : y0, r1 = bot ? H - 2 : y0 + th - 1;   // side rows without the corners
+    const int nside = max(0, r1 - r0 + 1);
+    const int nl = lft ? nside : 0, nr = (rgt && W > 1) ? nside : 0;
+    const int n = ntop + nbot + nl + nr;
+    for (int k = tid; k < n; k += kFwdConsumers) {
+        int qx, qy, t = k;
+        if (t < ntop) { qx = x0 + t; qy = 0; }
+        else if ((t -= ntop) < nbot) { qx = x0 + t; qy = H - 1; }
+        else if ((t -= nbot) < nl) { qx = 0; qy = r0 + t; }
+        else { t -= nl; qx = W - 1; qy = r0 + t; }
+        const int xlo = qx == 0 ? -rx : qx, xhi = qx == W - 1 ? W - 1 + rx : qx;
+        const int ylo = qy == 0 ? -ry : qy, yhi = qy == H - 1 ? H - 1 + ry : qy;
+        float acc = 0.f;
+        for (int ey = ylo; ey <= yhi; ++ey) {
+            const int a0 = max(0, R - ey), a1 = min(K - 1, H - 1 - ey + R);
+            for (int ex = xlo; ex <= xhi; ++ex) {
+                if (ex == qx && ey == qy) continue;           // the pixel's own term, already stored
+                const int b0 = max(0, R - ex), b1 = min(K - 1, W - 1 - ex + R);
+                float z = 0.f;
+                for (int a = a0; a <= a1; ++a) {
+                    // g(ex - R + b, ey + a - R) is staged at row ey + a - y0, column ex - R + b - x0 + 8
+                    const int gb = (ey + a - y0) * SWP + (ex - R - x0 + 8);
+                    if (im.op == IMCL_OP_CONV2D) {
+                        const float* wr = w + a * kTapStride;
+                        for (int b = b0; b <= b1; ++b) z = __fmaf_rn(wr[b], st[gb + b], z);
+                    } else {
+                        float rs = 0.f;
+                        for (int b = b0; b <= b1; ++b) rs = __fmaf_rn(w[b], st[gb + b], rs);
+                        z = __fmaf_rn(w[K + a], rs, z);
+                    }
+                }
+                acc += z;
+            }
+        }
+        float* o = static_cast<float*>(im.out) + (long long)qy * im.out_pitch + qx;
+        *o += acc;
     }
 }
 
@@ -814,6 +821,10 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
         consumer_sync();
         batch_fwd_dispatch<PY>(*cur, x0, y0, bx, by, st, tb, w, tid);
         consumer_sync();   // st, tb, w and cur are reused by the next tile
+        if (cur->fold) {   // the tile's own stores are visible to the consumers after the barrier
+            fwd_fold_edges(*cur, x0, y0, 4 * bx, PY * by, st, 4 * bx + 16 + kFwdPitchPad, w, tid);
+            consumer_sync();
+        }
     }
 }
 
@@ -854,80 +865,47 @@ __device__ void tile_wgrad(const float* gs, int gsw, int gs_row0, const float* x
     }
 }
 
-// conv2d: input-gradient tile (all but the image's edge pixels under the clamp rule) and
-// the tile's tap partial sums.
-template <int K, int PY>
-__device__ void batch_conv_dx_tile(const BImg& im, int x0, int y0, int bx, int by, float* sm, int tid, int nth) {
-    const int TW = 4 * bx, TH = PY * by;
-    if (im.gin) {
-        batch_conv_tile<K, PY>(im, x0, y0, bx, by, sm, true, im.g, im.g_pitch, im.gin, im.gin_pitch, IMCL_F32, tid, nth);
-        __syncthreads();
-    }
-    if (im.gtaps) {
-        // the K x K centred tap gradient by the register-blocked reduction; a kw x kh
-        // filter (kw, kh <= K) takes its block of it
-        constexpr int R = (K - 1) / 2, JR = WgCfg<K>::JR;
-        const int XW = wg_xpitch<K>(TW), XH = TH + K - 1;
-        float* gs = sm;
-        float* xs = gs + TW * TH;
-        stage_region(gs, TW, TH, im.g, IMCL_F32, im.g_pitch, x0, y0, im.W, im.H, IMCL_BORDER_CONSTANT, 0.f, 1, tid, nth,
-                     im.g_vec);
-        stage_region(xs, XW, XH, im.in, im.in_dt, im.in_pitch, x0 - R, y0 - R, im.W, im.H, im.border, im.bv, 0, tid,
-                     nth);
-        __syncthreads();
-        const int G = (K + JR - 1) / JR, T = nth / G, grp = tid / T, lt = tid - grp * T;
-        const bool active = grp < G;
-        float acc[JR][K];
-#pragma unroll
-        for (int jr = 0; jr < JR; ++jr)
-#pragma unroll
-            for (int i = 0; i < K; ++i) acc[jr][i] = 0.f;
-        if (active) wgrad_accumulate<K>(gs, TW, xs, XW, TW, TH, K, grp * JR, lt, T, acc);
-        float* kk = sm + nth * JR * K;                  // the K x K sums, after the combine scratch
-        wgrad_combine<K>(acc, active, sm, K, T, kk, tid, nth);
-        const int tile = (y0 / TH) * im.tiles_x + x0 / TW;
-        const int rx = (im.kw - 1) / 2, ry = (im.kh - 1) / 2;
-        float* out = im.part + (size_t)tile * im.kw * im.kh;
-        for (int q = tid; q < im.kw * im.kh; q += nth) {
-            const int j = q / im.kw, i = q - j * im.kw;
-            out[q] = kk[(j - ry + R) * K + (i - rx + R)];
-        }
-    }
-}
+// Tap rows per thread in the batch's tap-gradient tiles: JR x K accumulators, the 32
+// values of a 4 x 8 block of g and one x row segment must fit the registers of a kernel
+// that runs three CTAs of 256 threads per SM.
+template <int K>
+struct BatchWg {
+    static constexpr int JR = K <= 7 ? 4 : (K <= 9 ? 3 : 2);
+};
 
-// conv2d, clamp rule: the input gradient at a chunk of the image's edge pixels, with the
-// contributions of clamped taps folded in (the transpose of the clamp).
-__device__ void batch_conv_edges(const BImg& im, int chunk, int tid, int nth) {
-    const int W = im.W, H = im.H;
-    const int ntop = W, nside = H > 2 ? H - 2 : 0;
-    const int rows = H > 1 ? 2 * ntop : ntop;
-    const int nedge = rows + (W > 1 ? 2 * nside : nside);
+// conv2d: the tap-gradient partial sums of one tile, dw[j][i] = sum_p g(p) x(p + (i - rx,
+// j - ry)) over the tile's pixels, by the register-blocked reduction on the K x K centred
+// form (a kw x kh filter, kw, kh <= K, takes its block of it).
+template <int K>
+__device__ void batch_conv_dw_tile(const BImg& im, int x0, int y0, int TW, int TH, float* sm, int tid, int nth) {
+    constexpr int R = (K - 1) / 2, JR = BatchWg<K>::JR;
+    // x staged from column x0 - 8 (16-byte chunks); the reduction's region starts at x0 - R,
+    // (8 - R) columns in: the aligned column C below it and D = (8 - R) % 4 more
+    constexpr int C = (8 - R) / 4 * 4, D = (8 - R) % 4;
+    const int XW = round_up(C + wg_xpitch<K>(TW) + 4, 8), XH = TH + K - 1;
+    float* gs = sm;
+    float* xs = gs + TW * TH;
+    stage_region(gs, TW, TH, im.g, IMCL_F32, im.g_pitch, x0, y0, im.W, im.H, IMCL_BORDER_CONSTANT, 0.f, 1, tid, nth,
+                 im.g_vec);
+    stage_region(xs, XW, XH, im.in, im.in_dt, im.in_pitch, x0 - 8, y0 - R, im.W, im.H, im.border, im.bv, 0, tid, nth,
+                 im.in_vec);
+    __syncthreads();
+    const int G = (K + JR - 1) / JR, T = nth / G, grp = tid / T, lt = tid - grp * T;
+    const bool active = grp < G;
+    float acc[JR][K];
+#pragma unroll
+    for (int jr = 0; jr < JR; ++jr)
+#pragma unroll
+        for (int i = 0; i < K; ++i) acc[jr][i] = 0.f;
+    if (active) wgrad_accumulate<K, D, JR>(gs, TW, xs + C, XW, TW, TH, K, grp * JR, lt, T, acc);
+    float* kk = sm + nth * JR * K;                  // the K x K sums, after the combine scratch
+    wgrad_combine<K, JR>(acc, active, sm, K, T, kk, tid, nth);
+    const int tile = (y0 / TH) * im.tiles_x + x0 / TW;
     const int rx = (im.kw - 1) / 2, ry = (im.kh - 1) / 2;
-    for (int e = chunk * 1024 + tid; e < min(nedge, (chunk + 1) * 1024); e += nth) {
-        int qx, qy;
-        if (e < rows) {
-            qx = e % W;
-            qy = e < ntop ? 0 : H - 1;
-        } else {
-            const int k = e - rows;
-            qy = 1 + (k % nside);
-            qx = k < nside ? 0 : W - 1;
-        }
-        const int xlo = qx == 0 ? -rx : qx, xhi = qx == W - 1 ? W - 1 + rx : qx;
-        const int ylo = qy == 0 ? -ry : qy, yhi = qy == H - 1 ? H - 1 + ry : qy;
-        float acc = 0.f;
-        for (int ey = ylo; ey <= yhi; ++ey)
-            for (int ex = xlo; ex <= xhi; ++ex)
-                for (int j = 0; j < im.kh; ++j) {
-                    const int sy = ey - j + ry;
-                    if (sy < 0 || sy >= H) continue;
-                    for (int i = 0; i < im.kw; ++i) {
-                        const int sx = ex - i + rx;
-                        if (sx < 0 || sx >= W) continue;
-                        acc = __fmaf_rn(im.taps[j * im.kw + i], im.g[(long long)sy * im.g_pitch + sx], acc);
-                    }
-                }
-        im.gin[(long long)qy * im.gin_pitch + qx] = acc;
+    float* out = im.part + (size_t)tile * im.kw * im.kh;
+    for (int q = tid; q < im.kw * im.kh; q += nth) {
+        const int j = q / im.kw, i = q - j * im.kw;
+        out[q] = kk[(j - ry + R) * K + (i - rx + R)];
     }
 }
 
@@ -967,93 +945,6 @@ __device__ __forceinline__ void batch_sep_rows_t(const BImg& im, const float* xs
     }
 }
 
-// separable, first backward pass: dt = C^T g on the tile (with the clamp folds on the
-// first and last rows) into the plan's dt plane, and the column-tap partial sums
-// dcol[j] = sum_p g(p) t(p + (0, j - rc)), t the forward row pass.
-template <int R>
-__device__ void batch_sep_dt_tile(const BImg& im, int x0, int y0, int TW, int TH, float* sm, int tid, int nth) {
-    constexpr int PADR = 8;                             // >= R, 16 bytes of f32
-    const int nr = im.kw, nc = im.kh, rc = (nc - 1) / 2;
-    const int XW = TW + 2 * PADR, HH = TH + 2 * R;      // R >= rc rows of halo
-    float* gs = sm;                                     // TW x HH, rows y0 - R ..
-    float* w = gs + TW * HH;                            // row taps [0, 16), column taps [16, 32)
-    float* red = w + 32;
-    for (int i = tid; i < 32; i += nth) w[i] = i < 16 ? (i < nr ? im.taps[i] : 0.f) : (i - 16 < nc ? im.taps2[i - 16] : 0.f);
-    stage_region(gs, TW, HH, im.g, IMCL_F32, im.g_pitch, x0, y0 - R, im.W, im.H, IMCL_BORDER_CONSTANT, 0.f, 1, tid, nth,
-                 im.g_vec);
-    __syncthreads();
-    const float* cw = w + 16;
-    // dt for the tile's pixels
-    if (im.dt) {
-        // 4 pixels of a row per item: one 16-byte load of g per column tap
-        const int ng = TW / 4;
-        for (int k = tid; k < ng * TH; k += nth) {
-            const int py = k / ng, px = (k - py * ng) * 4;
-            const int gx = x0 + px, gy = y0 + py;
-            if (gx >= im.W || gy >= im.H) continue;
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
-            for (int j = 0; j < nc; ++j) {
-                const float4 s4 = *reinterpret_cast<const float4*>(gs + (py + R + rc - j) * TW + px);
-                acc[0] = __fmaf_rn(cw[j], s4.x, acc[0]);
-                acc[1] = __fmaf_rn(cw[j], s4.y, acc[1]);
-                acc[2] = __fmaf_rn(cw[j], s4.z, acc[2]);
-                acc[3] = __fmaf_rn(cw[j], s4.w, acc[3]);
-            }
-            if (im.border == IMCL_BORDER_CLAMP && (gy == 0 || gy == im.H - 1)) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (gy == 0)
-                        for (int e = -rc; e <= -1; ++e)
-                            for (int j = 0; j < nc; ++j) {
-                                const int sy = e - j + rc;   // image row, < rc
-                                if (sy >= 0 && sy < im.H) acc[q] = __fmaf_rn(cw[j], gs[(sy - y0 + R) * TW + px + q], acc[q]);
-                            }
-                    if (gy == im.H - 1)
-                        for (int e = im.H; e <= im.H - 1 + rc; ++e)
-                            for (int j = 0; j < nc; ++j) {
-                                const int sy = e - j + rc;
-                                if (sy >= 0 && sy < im.H) acc[q] = __fmaf_rn(cw[j], gs[(sy - y0 + R) * TW + px + q], acc[q]);
-                            }
-                }
-            }
-            float* o = im.dt + (long long)gy * im.dt_pitch + gx;
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (gx + q < im.W) o[q] = acc[q];
-        }
-    }
-    if (im.gtaps2) {
-        // t on rows y0 - rc .. y0 + TH + rc of the tile's columns (boundary rule on x and t)
-        float* xs = red + 4 * 256;                      // XW x HH
-        float* ts = xs + XW * HH;                       // TW x HH
-        stage_region(xs, XW, HH, im.in, im.in_dt, im.in_pitch, x0 - PADR, y0 - R, im.W, im.H, im.border, im.bv, 0,
-                     tid, nth, im.in_vec);
-        __syncthreads();
-        switch (nr) {
-            case 1: batch_sep_rows_t<1>(im, xs, XW, ts, TW, HH, y0 - R, w, tid, nth); break;
-            case 3: batch_sep_rows_t<3>(im, xs, XW, ts, TW, HH, y0 - R, w, tid, nth); break;
-            case 5: batch_sep_rows_t<5>(im, xs, XW, ts, TW, HH, y0 - R, w, tid, nth); break;
-            case 7: batch_sep_rows_t<7>(im, xs, XW, ts, TW, HH, y0 - R, w, tid, nth); break;
-            case 9: batch_sep_rows_t<9>(im, xs, XW, ts, TW, HH, y0 - R, w, tid, nth); break;
-            case 11: batch_sep_rows_t<11>(im, xs, XW, ts, TW, HH, y0 - R, w, tid, nth); break;
-            case 13: batch_sep_rows_t<13>(im, xs, XW, ts, TW, HH, y0 - R, w, tid, nth); break;
-            default: batch_sep_rows_t<15>(im, xs, XW, ts, TW, HH, y0 - R, w, tid, nth); break;
-        }
-        __syncthreads();
-        const int tile = (y0 / TH) * im.tiles_x + x0 / TW;
-        // column taps: the register-blocked reduction with one tap per row (KW = 1, nc tap
-        // rows); g rows of the tile start at row R of gs, t rows at offset R - rc
-        constexpr int JR = WgCfg<1>::JR;
-        const int G = (nc + JR - 1) / JR, T = nth / G, grp = tid / T, lt = tid - grp * T;
-        const bool active = grp < G;
-        float acc[JR][1];
-#pragma unroll
-        for (int jr = 0; jr < JR; ++jr) acc[jr][0] = 0.f;
-        if (active) wgrad_accumulate<1>(gs + R * TW, TW, ts + (R - rc) * TW, TW, TW, TH, nc, grp * JR, lt, T, acc);
-        wgrad_combine<1>(acc, active, red, nc, T, im.part + (size_t)tile * nc, tid, nth);
-    }
-}
-
 // Row-tap partial sums of a separable tile: out[i] = sum_p dt(p) x(p + (i - rr, 0)), with
 // dt staged at columns PADR.. of ds and x at columns PADR - rr + i of xs (rows XW wide).
 // x reads start PADR - rr columns in: the aligned column below and D = (PADR - rr) % 4.
@@ -1068,113 +959,141 @@ __device__ void batch_row_wgrad(const float* ds, const float* xs, int XW, int TW
     wgrad_combine<NR, 1>(acc, true, red, 1, nth, out, tid, nth);
 }
 
-// separable, second backward pass: dx = R^T dt on the tile (with the clamp folds on the
-// first and last columns) and the row-tap partials drow[i] = sum_p dt(p) x(p + (i - rr, 0)).
-// dx = R^T dt on a separable tile, 4 pixels per item: one 20-float segment of dt (staged at
-// columns PADR = 8 ..) serves the NR taps of all 4; the clamp folds of columns 0 and W-1
-// are added after, as in the per-pixel form (same order of operations).
-template <int NR>
-__device__ __forceinline__ void batch_sep_dx_compute(const BImg& im, const float* ds, int XW, int x0, int y0, int TW,
-                                                     int TH, const float* w, int tid, int nth) {
-    constexpr int RR = (NR - 1) / 2, PADR = 8;
-    float wr[NR];
-#pragma unroll
-    for (int i = 0; i < NR; ++i) wr[i] = w[i];
-    const int ng = TW / 4;
-    for (int k = tid; k < ng * TH; k += nth) {
-        const int py = k / ng, px = (k - py * ng) * 4;
-        const int gx = x0 + px, gy = y0 + py;
-        if (gx >= im.W || gy >= im.H) continue;
-        float seg[20];
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            const float4 s4 = *reinterpret_cast<const float4*>(ds + py * XW + px + 4 * q);
-            seg[4 * q] = s4.x; seg[4 * q + 1] = s4.y; seg[4 * q + 2] = s4.z; seg[4 * q + 3] = s4.w;
-        }
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int i = 0; i < NR; ++i)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] = __fmaf_rn(wr[i], seg[PADR + RR - i + q], acc[q]);
-        if (im.border == IMCL_BORDER_CLAMP && (gx == 0 || gx + 3 >= im.W - 1)) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int qx = gx + q;
-                if (qx == 0)
-                    for (int e = -RR; e <= -1; ++e)
-                        for (int i = 0; i < NR; ++i) {
-                            const int sx = e - i + RR;
-                            if (sx >= 0 && sx < im.W) acc[q] = __fmaf_rn(wr[i], ds[py * XW + sx - x0 + PADR], acc[q]);
-                        }
-                if (qx == im.W - 1)
-                    for (int e = im.W; e <= im.W - 1 + RR; ++e)
-                        for (int i = 0; i < NR; ++i) {
-                            const int sx = e - i + RR;
-                            if (sx >= 0 && sx < im.W) acc[q] = __fmaf_rn(wr[i], ds[py * XW + sx - x0 + PADR], acc[q]);
-                        }
-            }
-        }
-        float* o = im.gin + (long long)gy * im.gin_pitch + gx;
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (gx + q < im.W) o[q] = acc[q];
-    }
-}
-
-__device__ void batch_sep_dx_tile(const BImg& im, int x0, int y0, int TW, int TH, float* sm, int tid, int nth) {
-    constexpr int PADR = 8;
-    const int nr = im.kw;
-    const int XW = TW + 2 * PADR;
-    float* ds = sm;                                     // XW x TH, columns x0 - PADR ..
-    float* xs = ds + XW * TH;                           // XW x TH
-    float* w = xs + XW * TH;
-    float* red = w + 16;
-    for (int i = tid; i < 16; i += nth) w[i] = i < nr ? im.taps[i] : 0.f;
-    stage_region(ds, XW, TH, im.dt, IMCL_F32, im.dt_pitch, x0 - PADR, y0, im.W, im.H, IMCL_BORDER_CONSTANT, 0.f, 1, tid,
-                 nth, 16);
-    stage_region(xs, XW, TH, im.in, im.in_dt, im.in_pitch, x0 - PADR, y0, im.W, im.H, im.border, im.bv, 0, tid, nth,
-                 im.in_vec);
+// separable: the tile's tap-gradient partial sums, from one staging of g (zero outside
+// the image) and of x (the image's rule), rows y0 - R .. y0 + TH + R:
+//   column taps  dcol[j] = sum_p g(p) t(p + (0, j - rc)),  t = R x the forward row pass;
+//   row taps     drow[i] = sum_p dt(p) x(p + (i - rr, 0)), dt = C^T g the column adjoint
+//                (with the clamp folds on the image's first and last rows).
+// The input gradient itself (R^T dt) runs in the pipelined tile kernel, so dt never
+// leaves shared memory.
+template <int R>
+__device__ void batch_sep_taps_tile(const BImg& im, int x0, int y0, int TW, int TH, float* sm, int tid, int nth) {
+    constexpr int PADR = 8;                             // >= R, 16 bytes of f32
+    const int nr = im.kw, nc = im.kh, rc = (nc - 1) / 2;
+    const int XW = TW + 2 * PADR, HH = TH + 2 * R;      // R >= rc rows of halo
+    float* gs = sm;                                     // TW x HH, rows y0 - R ..
+    float* xs = gs + TW * HH;                           // XW x HH, origin (x0 - PADR, y0 - R)
+    float* u = xs + XW * HH;                            // t (TW x HH), later dt (XW x TH, columns PADR ..)
+    float* w = u + max(TW * HH, XW * TH);               // row taps [0, 16), column taps [16, 32)
+    float* red = w + 32;                                // the column-tap combine (nth * 4 floats)
+    for (int i = tid; i < 32; i += nth) w[i] = i < 16 ? (i < nr ? im.taps[i] : 0.f) : (i - 16 < nc ? im.taps2[i - 16] : 0.f);
+    stage_region(gs, TW, HH, im.g, IMCL_F32, im.g_pitch, x0, y0 - R, im.W, im.H, IMCL_BORDER_CONSTANT, 0.f, 1, tid, nth,
+                 im.g_vec);
+    stage_region(xs, XW, HH, im.in, im.in_dt, im.in_pitch, x0 - PADR, y0 - R, im.W, im.H, im.border, im.bv, 0, tid,
+                 nth, im.in_vec);
     __syncthreads();
-    if (im.gin) {
+    const int tile = (y0 / TH) * im.tiles_x + x0 / TW;
+    const int ntiles = im.tiles_x * im.tiles_y;
+    if (im.gtaps2) {
+        float* ts = u;
         switch (nr) {
-            case 1: batch_sep_dx_compute<1>(im, ds, XW, x0, y0, TW, TH, w, tid, nth); break;
-            case 3: batch_sep_dx_compute<3>(im, ds, XW, x0, y0, TW, TH, w, tid, nth); break;
-            case 5: batch_sep_dx_compute<5>(im, ds, XW, x0, y0, TW, TH, w, tid, nth); break;
-            case 7: batch_sep_dx_compute<7>(im, ds, XW, x0, y0, TW, TH, w, tid, nth); break;
-            case 9: batch_sep_dx_compute<9>(im, ds, XW, x0, y0, TW, TH, w, tid, nth); break;
-            case 11: batch_sep_dx_compute<11>(im, ds, XW, x0, y0, TW, TH, w, tid, nth); break;
-            case 13: batch_sep_dx_compute<13>(im, ds, XW, x0, y0, TW, TH, w, tid, nth); break;
-            default: batch_sep_dx_compute<15>(im, ds, XW, x0, y0, TW, TH, w, tid, nth); break;
+            case 1: batch_sep_rows_t<1>(im, xs, XW, ts, TW, HH, y0 - R, w, tid, nth); break;
+            case 3: batch_sep_rows_t<3>(im, xs, XW, ts, TW, HH, y0 - R, w, tid, nth); break;
+            case 5: batch_sep_rows_t<5>(im, xs, XW, ts, TW, HH, y0 - R, w, tid, nth); break;
+            case 7: batch_sep_rows_t<7>(im, xs, XW, ts, TW, HH, y0 - R, w, tid, nth); break;
+            case 9: batch_sep_rows_t<9>(im, xs, XW, ts, TW, HH, y0 - R, w, tid, nth); break;
+            case 11: batch_sep_rows_t<11>(im, xs, XW, ts, TW, HH, y0 - R, w, tid, nth); break;
+            case 13: batch_sep_rows_t<13>(im, xs, XW, ts, TW, HH, y0 - R, w, tid, nth); break;
+            default: batch_sep_rows_t<15>(im, xs, XW, ts, TW, HH, y0 - R, w, tid, nth); break;
         }
+        __syncthreads();
+        // column taps: the register-blocked reduction with one tap per row (KW = 1, nc tap
+        // rows); g rows of the tile start at row R of gs, t rows at offset R - rc
+        constexpr int JR = WgCfg<1>::JR;
+        const int G = (nc + JR - 1) / JR, T = nth / G, grp = tid / T, lt = tid - grp * T;
+        const bool active = grp < G;
+        float acc[JR][1];
+#pragma unroll
+        for (int jr = 0; jr < JR; ++jr) acc[jr][0] = 0.f;
+        if (active) wgrad_accumulate<1>(gs + R * TW, TW, ts + (R - rc) * TW, TW, TW, TH, nc, grp * JR, lt, T, acc);
+        wgrad_combine<1>(acc, active, red, nc, T, im.part + (size_t)tile * nc, tid, nth);   // ends synchronised
     }
     if (im.gtaps) {
-        const int tile = (y0 / TH) * im.tiles_x + x0 / TW;
-        const int ntiles = im.tiles_x * im.tiles_y;
-        // dt rows of the tile are ds rows 0..TH at columns PADR..; x at columns PADR - rr + i
-        float* out = im.part + (size_t)ntiles * im.kh + (size_t)tile * nr;
-        switch (nr) {   // row taps: the register-blocked reduction, one tap row
-            case 1: batch_row_wgrad<1>(ds, xs, XW, TW, TH, red, out, tid, nth); break;
-            case 3: batch_row_wgrad<3>(ds, xs, XW, TW, TH, red, out, tid, nth); break;
-            case 5: batch_row_wgrad<5>(ds, xs, XW, TW, TH, red, out, tid, nth); break;
-            case 7: batch_row_wgrad<7>(ds, xs, XW, TW, TH, red, out, tid, nth); break;
-            case 9: batch_row_wgrad<9>(ds, xs, XW, TW, TH, red, out, tid, nth); break;
-            case 11: batch_row_wgrad<11>(ds, xs, XW, TW, TH, red, out, tid, nth); break;
-            case 13: batch_row_wgrad<13>(ds, xs, XW, TW, TH, red, out, tid, nth); break;
-            default: batch_row_wgrad<15>(ds, xs, XW, TW, TH, red, out, tid, nth); break;
+        // dt = C^T g on the tile's pixels (zero outside the image), 4 pixels of a row per
+        // item, into u with rows XW apart and the tile at columns PADR ..
+        float* ds = u;
+        const float* cw = w + 16;
+        const int ng = TW / 4;
+        for (int k = tid; k < ng * TH; k += nth) {
+            const int py = k / ng, px = (k - py * ng) * 4;
+            const int gx = x0 + px, gy = y0 + py;
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            if (gy < im.H && gx < im.W) {
+                for (int j = 0; j < nc; ++j) {
+                    const float4 s4 = *reinterpret_cast<const float4*>(gs + (py + R + rc - j) * TW + px);
+                    acc[0] = __fmaf_rn(cw[j], s4.x, acc[0]);
+                    acc[1] = __fmaf_rn(cw[j], s4.y, acc[1]);
+                    acc[2] = __fmaf_rn(cw[j], s4.z, acc[2]);
+                    acc[3] = __fmaf_rn(cw[j], s4.w, acc[3]);
+                }
+                if (im.border == IMCL_BORDER_CLAMP && (gy == 0 || gy == im.H - 1)) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (gy == 0)
+                            for (int e = -rc; e <= -1; ++e)
+                                for (int j = 0; j < nc; ++j) {
+                                    const int sy = e - j + rc;   // image row, < rc
+                                    if (sy >= 0 && sy < im.H) acc[q] = __fmaf_rn(cw[j], gs[(sy - y0 + R) * TW + px + q], acc[q]);
+                                }
+                        if (gy == im.H - 1)
+                            for (int e = im.H; e <= im.H - 1 + rc; ++e)
+                                for (int j = 0; j < nc; ++j) {
+                                    const int sy = e - j + rc;
+                                    if (sy >= 0 && sy < im.H) acc[q] = __fmaf_rn(cw[j], gs[(sy - y0 + R) * TW + px + q], acc[q]);
+                                }
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (gx + q >= im.W) acc[q] = 0.f;
+            *reinterpret_cast<float4*>(ds + py * XW + PADR + px) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        }
+        __syncthreads();
+        // row taps: the register-blocked reduction, one tap row; x rows of the tile start at
+        // row R of xs; the combine scratch takes gs, which nothing reads any more
+        float* out = im.part + (size_t)ntiles * nc + (size_t)tile * nr;
+        const float* xt = xs + R * XW;
+        switch (nr) {
+            case 1: batch_row_wgrad<1>(ds, xt, XW, TW, TH, gs, out, tid, nth); break;
+            case 3: batch_row_wgrad<3>(ds, xt, XW, TW, TH, gs, out, tid, nth); break;
+            case 5: batch_row_wgrad<5>(ds, xt, XW, TW, TH, gs, out, tid, nth); break;
+            case 7: batch_row_wgrad<7>(ds, xt, XW, TW, TH, gs, out, tid, nth); break;
+            case 9: batch_row_wgrad<9>(ds, xt, XW, TW, TH, gs, out, tid, nth); break;
+            case 11: batch_row_wgrad<11>(ds, xt, XW, TW, TH, gs, out, tid, nth); break;
+            case 13: batch_row_wgrad<13>(ds, xt, XW, TW, TH, gs, out, tid, nth); break;
+            default: batch_row_wgrad<15>(ds, xt, XW, TW, TH, gs, out, tid, nth); break;
         }
     }
 }
 
-// Reduce an image's tap partial sums over its tiles (fixed order) into the gradients.
-__device__ void batch_final(const BImg& im, int tid, int nth) {
+// Reduce an image's tap partial sums over its tiles into the gradients.  The order of the
+// additions depends only on the tile count, the tap count n and the block size: G =
+// min(nth / n, tiles) thread groups take the tiles t = g, g + G, ..., each thread keeps
+// eight running sums over consecutive rounds of its tiles (eight loads in flight) and adds
+// them in a fixed tree, and the group sums are added in group order.
+__device__ void batch_final(const BImg& im, float* red, int tid, int nth) {
     const int ntiles = im.tiles_x * im.tiles_y;
-    // sum_t part[t * n + q] over the tiles, in tile order, for taps q < n
     auto reduce = [&](const float* part, int n, float* out) {
-        for (int q = tid; q < n; q += nth) {
-            float s = 0.f;
-            for (int t = 0; t < ntiles; ++t) s += part[(size_t)t * n + q];
-            out[q] = s;
+        const int G = max(1, min(nth / n, ntiles));
+        const int g = tid / n, q = tid - g * n;
+        if (g < G) {
+            float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            int t = g;
+            for (; t + 7 * G < ntiles; t += 8 * G) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) a[u] += part[(size_t)(t + u * G) * n + q];
+            }
+            for (; t < ntiles; t += G) a[0] += part[(size_t)t * n + q];
+            red[g * n + q] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
         }
+        __syncthreads();
+        if (tid < n) {
+            float s = 0.f;
+            for (int k = 0; k < G; ++k) s += red[k * n + tid];
+            out[tid] = s;
+        }
+        __syncthreads();
     };
     if (im.op == IMCL_OP_CONV2D) {
         if (im.gtaps) reduce(im.part, im.kw * im.kh, im.gtaps);
@@ -1188,21 +1107,19 @@ template <int PY>
 __device__ void batch_bwd_dispatch(const BImg& im, const BTile& tl, int bx, int by, float* sm, int tid, int nth) {
     const int TW = 4 * bx, TH = PY * by;
     switch (tl.kind) {
-        case BT_CONV_DX:
+        case BT_CONV_DW:
             switch (im.K) {
-                case 3: batch_conv_dx_tile<3, PY>(im, tl.x0, tl.y0, bx, by, sm, tid, nth); break;
-                case 5: batch_conv_dx_tile<5, PY>(im, tl.x0, tl.y0, bx, by, sm, tid, nth); break;
-                case 7: batch_conv_dx_tile<7, PY>(im, tl.x0, tl.y0, bx, by, sm, tid, nth); break;
-                case 9: batch_conv_dx_tile<9, PY>(im, tl.x0, tl.y0, bx, by, sm, tid, nth); break;
-                case 11: batch_conv_dx_tile<11, PY>(im, tl.x0, tl.y0, bx, by, sm, tid, nth); break;
-                case 13: batch_conv_dx_tile<13, PY>(im, tl.x0, tl.y0, bx, by, sm, tid, nth); break;
-                default: batch_conv_dx_tile<15, PY>(im, tl.x0, tl.y0, bx, by, sm, tid, nth); break;
+                case 3: batch_conv_dw_tile<3>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
+                case 5: batch_conv_dw_tile<5>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
+                case 7: batch_conv_dw_tile<7>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
+                case 9: batch_conv_dw_tile<9>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
+                case 11: batch_conv_dw_tile<11>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
+                case 13: batch_conv_dw_tile<13>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
+                default: batch_conv_dw_tile<15>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
             }
             break;
-        case BT_CONV_EDGE: batch_conv_edges(im, tl.x0, tid, nth); break;
-        case BT_SEP_DT: batch_sep_dt_tile<kBatchMaxR>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
-        case BT_SEP_DX: batch_sep_dx_tile(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
-        default: batch_final(im, tid, nth); break;
+        case BT_SEP_TAPS: batch_sep_taps_tile<kBatchMaxR>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
+        default: batch_final(im, sm, tid, nth); break;
     }
 }
 

@@ -171,8 +171,10 @@ def test_batch_backward_matches_oracle():
     i = 0
     for (h, w) in shapes:
         for spec in (("conv", 3), ("conv", 15), ("conv", (5, 9)), ("sep", (3, 3)), ("sep", (15, 5)), ("sep", (1, 7))):
-            st = ("f16", "f32", "bf16")[i % 3]
-            border, bv = (("clamp", 0.0), ("constant", 0.375))[i % 2]
+            # six specs per shape: shift the storage type and border per shape so that each
+            # spec meets every type and both borders
+            st = ("f16", "f32", "bf16")[(i + i // 6) % 3]
+            border, bv = (("clamp", 0.0), ("constant", 0.375))[(i + i // 6) % 2]
             x = synth.to_storage(synth.uniform_f32(g, h, w), st)
             gr = torch.from_numpy(g.standard_normal((h, w)).astype(np.float32))
             if spec[0] == "conv":
