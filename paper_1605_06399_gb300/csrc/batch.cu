@@ -118,21 +118,42 @@ static imcl_status launch_fwd(const Batch& b, const BFwdTile* tiles, int ntiles,
     return launch_fwd_list(b, b.dimgs, b.queue, tiles, ntiles, py, bx, by, s);
 }
 
+template <int CLS>
 static const void* bwd_kernel(int py) {
-    return py == 4 ? (const void*)k_batch_bwd<4> : (const void*)k_batch_bwd<2>;
+    return py == 4 ? (const void*)k_batch_bwd<4, CLS> : (const void*)k_batch_bwd<2, CLS>;
 }
 
-size_t batch_bwd_smem_bytes(int py, int bx, int by) {
+// Shared memory of a backward phase kernel of class cls.
+static size_t batch_bwd_smem_bytes(int cls, int py, int bx, int by) {
     const size_t TW = 4 * bx, TH = (size_t)py * by, K = kBatchMaxK, R = kBatchMaxR;
-    // conv2d tap-gradient tiles: g (TW x TH), x staged from column x0 - 8 (the widest
-    // filter's pitch), then the combine scratch and the K x K sums
-    const size_t conv_xw = (size_t)round_up(wg_xpitch<kBatchMaxK>((int)TW) + 4, 8);
-    const size_t conv_wg = std::max(TW * TH + conv_xw * (TH + K - 1),
-                                    (size_t)256 * BatchWg<kBatchMaxK>::JR * K + K * K);
-    // separable tap-gradient tiles: g, x, the row pass / column adjoint, taps, combine
-    const size_t HH = TH + 2 * R, XW = TW + 16;
-    const size_t sep = TW * HH + XW * HH + std::max(TW * HH, XW * TH) + 32 + 1024;
-    return std::max(conv_wg, sep) * sizeof(float);
+    if (cls == BCLS_CONV_TAPS) {
+        // g (TW x TH), x staged from column x0 - 8 (the widest filter's pitch), then the
+        // combine scratch and the K x K sums
+        const size_t conv_xw = (size_t)round_up(wg_xpitch<kBatchMaxK>((int)TW) + 4, 8);
+        return std::max(TW * TH + conv_xw * (TH + K - 1), (size_t)256 * BatchWg<kBatchMaxK>::JR * K + K * K) *
+               sizeof(float);
+    }
+    if (cls == BCLS_SEP_TAPS) {
+        // g, x, the row pass / column adjoint, taps, combine
+        const size_t HH = TH + 2 * R, XW = TW + 16;
+        return (TW * HH + XW * HH + std::max(TW * HH, XW * TH) + 32 + 1024) * sizeof(float);
+    }
+    return 256 * sizeof(float);   // the reductions' group sums
+}
+
+// One persistent launch of the backward phase kernel of class CLS over a work list.
+template <int CLS>
+static imcl_status launch_bwd_list(const Batch& b, const BTile* items, int n, int* queue, cudaStream_t s) {
+    if (n == 0) return IMCL_OK;
+    const size_t smem = batch_bwd_smem_bytes(CLS, b.py, b.bx, b.by);
+    imcl_status st = set_smem_limit(bwd_kernel<CLS>(b.py), (int)smem);
+    if (st != IMCL_OK) return st;
+    const int occ = cached_occupancy(bwd_kernel<CLS>(b.py), 256, (int)smem);
+    if (occ <= 0) return fail(IMCL_ERR_UNSUPPORTED, "batch backward: kernel cannot be resident");
+    const int grid = std::max(1, std::min(n, occ * b.dev->sm_count));
+    if (b.py == 4) k_batch_bwd<4, CLS><<<grid, 256, smem, s>>>(b.dimgs, items, n, queue, b.bx, b.by);
+    else k_batch_bwd<2, CLS><<<grid, 256, smem, s>>>(b.dimgs, items, n, queue, b.bx, b.by);
+    return cuda_fail(cudaGetLastError(), "batch backward launch");
 }
 
 // Backward plan: gradient pointers into the image descriptors, partial-sum buffers, the
@@ -141,7 +162,7 @@ size_t batch_bwd_smem_bytes(int py, int bx, int by) {
 // the tap-gradient tiles, the per-image reductions, and the graph that runs them.
 static imcl_status plan_backward(Batch* b) {
     const int TW = 4 * b->bx, TH = b->py * b->by;
-    std::vector<BTile> l1, l3;
+    std::vector<BTile> lc, ls, l3;   // conv2d tap tiles, separable tap tiles, reductions
     std::vector<BImg> dxi = b->himgs;
     std::vector<std::pair<double, BFwdTile>> dxt;
     bool any = false;
@@ -216,8 +237,10 @@ static imcl_status plan_backward(Batch* b) {
         }
         if (im.gtaps || im.gtaps2)
             for (int y = 0; y < im.H; y += TH)
-                for (int x = 0; x < im.W; x += TW)
-                    l1.push_back(BTile{i, it.op == IMCL_OP_CONV2D ? BT_CONV_DW : BT_SEP_TAPS, x, y});
+                for (int x = 0; x < im.W; x += TW) {
+                    if (it.op == IMCL_OP_CONV2D) lc.push_back(BTile{i, BT_CONV_DW, x, y});
+                    else ls.push_back(BTile{i, BT_SEP_TAPS, x, y});
+                }
         if (im.gtaps || im.gtaps2) l3.push_back(BTile{i, BT_FINAL, 0, 0});
     }
     if (!any) return IMCL_OK;
@@ -227,7 +250,8 @@ static imcl_status plan_backward(Batch* b) {
             return b->himgs[a.img].K > b->himgs[c.img].K;
         });
     };
-    by_cost(l1);
+    by_cost(lc);
+    by_cost(ls);
     imcl_status st;
     // the descriptors now carry gradient pointers: refresh the device copy
     cudaError_t e = cudaMemcpy(b->dimgs, b->himgs.data(), b->himgs.size() * sizeof(BImg), cudaMemcpyHostToDevice);
@@ -240,54 +264,48 @@ static imcl_status plan_backward(Batch* b) {
     BFwdTile* ddxt = nullptr;
     if ((st = upload(&ddx, dxi, &b->owned)) != IMCL_OK) return st;
     if ((st = upload(&ddxt, dx_tiles, &b->owned)) != IMCL_OK) return st;
-    BTile *d1 = nullptr, *d3 = nullptr;
-    if ((st = upload(&d1, l1, &b->owned)) != IMCL_OK) return st;
+    BTile *dc = nullptr, *dsp = nullptr, *d3 = nullptr;
+    if ((st = upload(&dc, lc, &b->owned)) != IMCL_OK) return st;
+    if ((st = upload(&dsp, ls, &b->owned)) != IMCL_OK) return st;
     if ((st = upload(&d3, l3, &b->owned)) != IMCL_OK) return st;
-    const size_t smem = batch_bwd_smem_bytes(b->py, b->bx, b->by);
-    if ((st = set_smem_limit(bwd_kernel(b->py), (int)smem)) != IMCL_OK) return st;
-    const int occ = cached_occupancy(bwd_kernel(b->py), 256, (int)smem);
-    if (occ <= 0) return fail(IMCL_ERR_UNSUPPORTED, "batch backward: kernel cannot be resident");
-    const int slots = occ * b->dev->sm_count;
     const int ndx = (int)dx_tiles.size();
-    if (ndx > 0) {
-        e = cudaStreamCreateWithFlags(&b->cap_stream2, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
+    for (int k = 0; k < 2; ++k) {
+        e = cudaStreamCreateWithFlags(&b->br_stream[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming);
         if (e != cudaSuccess) return cuda_fail(e, "batch backward stream");
     }
-    // The graph: the input-gradient tiles run on a branch beside the tap-gradient tiles
-    // (they write only grad_in, which the tap phases do not touch); the per-image
-    // reductions follow the tap tiles, and the branch joins at the end.
+    e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "batch backward event");
+    // The graph: three branches from one fork -- the input-gradient tiles (they write only
+    // grad_in), the conv2d tap tiles and the separable tap tiles (each writes its own
+    // items' partial sums); the per-image reductions wait for both tap branches, and
+    // everything joins at the end.
     e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "batch backward capture");
     cudaMemsetAsync(b->queue + 1, 0, (kQueueSlots - 1) * sizeof(int), b->cap_stream);
-    imcl_status lst = IMCL_OK;
-    if (ndx > 0) {
-        cudaEventRecord(b->ev_fork, b->cap_stream);
-        cudaStreamWaitEvent(b->cap_stream2, b->ev_fork, 0);
-        lst = launch_fwd_list(*b, ddx, b->queue + 4, ddxt, ndx, b->py, b->bx, b->by, b->cap_stream2);
-        cudaEventRecord(b->ev_join, b->cap_stream2);
-    }
-    const BTile* lists[2] = {d1, d3};
-    const int counts[2] = {(int)l1.size(), (int)l3.size()};
-    for (int ph = 0; ph < 2; ++ph) {
-        if (counts[ph] == 0) continue;
-        const int grid = std::max(1, std::min(counts[ph], slots));
-        if (b->py == 4)
-            k_batch_bwd<4><<<grid, 256, smem, b->cap_stream>>>(b->dimgs, lists[ph], counts[ph], b->queue + 1 + ph, b->bx, b->by);
-        else
-            k_batch_bwd<2><<<grid, 256, smem, b->cap_stream>>>(b->dimgs, lists[ph], counts[ph], b->queue + 1 + ph, b->bx, b->by);
-    }
-    if (ndx > 0) cudaStreamWaitEvent(b->cap_stream, b->ev_join, 0);
+    cudaEventRecord(b->ev_fork, b->cap_stream);
+    cudaStreamWaitEvent(b->br_stream[0], b->ev_fork, 0);
+    cudaStreamWaitEvent(b->br_stream[1], b->ev_fork, 0);
+    imcl_status lst = IMCL_OK, s1, s2, s3, s4;
+    if (ndx > 0) lst = launch_fwd_list(*b, ddx, b->queue + 4, ddxt, ndx, b->py, b->bx, b->by, b->br_stream[0]);
+    s1 = launch_bwd_list<BCLS_CONV_TAPS>(*b, dc, (int)lc.size(), b->queue + 1, b->cap_stream);
+    s2 = launch_bwd_list<BCLS_SEP_TAPS>(*b, dsp, (int)ls.size(), b->queue + 2, b->br_stream[1]);
+    cudaEventRecord(b->ev_join[1], b->br_stream[1]);
+    cudaStreamWaitEvent(b->cap_stream, b->ev_join[1], 0);
+    s3 = launch_bwd_list<BCLS_FINAL>(*b, d3, (int)l3.size(), b->queue + 3, b->cap_stream);
+    cudaEventRecord(b->ev_join[0], b->br_stream[0]);
+    cudaStreamWaitEvent(b->cap_stream, b->ev_join[0], 0);
+    s4 = IMCL_OK;
     cudaError_t le = cudaGetLastError();
     e = cudaStreamEndCapture(b->cap_stream, &b->bwd_graph);
-    if (lst != IMCL_OK) return lst;
+    for (imcl_status q : {lst, s1, s2, s3, s4})
+        if (q != IMCL_OK) return q;
     if (le != cudaSuccess) return cuda_fail(le, "batch backward launch");
     if (e != cudaSuccess) return cuda_fail(e, "batch backward capture end");
     e = cudaGraphInstantiate(&b->bwd_exec, b->bwd_graph, 0);
     if (e != cudaSuccess) return cuda_fail(e, "batch backward graph instantiate");
-    b->bwd_items[0] = counts[0];
-    b->bwd_items[1] = counts[1];
+    b->bwd_items[0] = (int)(lc.size() + ls.size());
+    b->bwd_items[1] = (int)l3.size();
     b->bwd_dx_tiles = ndx;
     return IMCL_OK;
 }
@@ -298,8 +316,10 @@ Batch::~Batch() {
     if (bwd_exec) cudaGraphExecDestroy(bwd_exec);
     if (bwd_graph) cudaGraphDestroy(bwd_graph);
     if (ev_fork) cudaEventDestroy(ev_fork);
-    if (ev_join) cudaEventDestroy(ev_join);
-    if (cap_stream2) cudaStreamDestroy(cap_stream2);
+    for (int k = 0; k < 2; ++k) {
+        if (ev_join[k]) cudaEventDestroy(ev_join[k]);
+        if (br_stream[k]) cudaStreamDestroy(br_stream[k]);
+    }
     for (void* p : owned) cudaFree(p);
     if (cap_stream) cudaStreamDestroy(cap_stream);
 }

@@ -20,16 +20,16 @@ struct Batch {
     BImg* dimgs = nullptr;                 // device copy
     BFwdTile* tiles = nullptr;             // forward work list (device)
     int ntiles = 0;
-    int* queue = nullptr;                  // work-list counters (device): [0] forward, [1] the
-                                           // tap-gradient tiles, [2] the per-image reductions,
-                                           // [4] the input-gradient tiles
+    int* queue = nullptr;                  // work-list counters (device): [0] forward, [1] conv2d
+                                           // tap tiles, [2] separable tap tiles, [3] per-image
+                                           // reductions, [4] input-gradient tiles
     int py = 4, bx = 32, by = 8;           // chosen tile shape (PX = 4)
     double pixels = 0;
     double fwd_ms_at_create = 0;
     double shape_ms[4] = {0, 0, 0, 0};
     cudaStream_t cap_stream = nullptr;     // private stream the graphs are recorded on
-    cudaStream_t cap_stream2 = nullptr;    // the backward graph's second branch
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t br_stream[2] = {nullptr, nullptr};   // the backward graph's other branches
+    cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
     cudaGraph_t fwd_graph = nullptr;
     cudaGraphExec_t fwd_exec = nullptr;
     cudaGraph_t bwd_graph = nullptr;

@@ -679,21 +679,58 @@ __device__ __forceinline__ void batch_fwd_dispatch(const BImg& im, int x0, int y
 // forward made outside the image back onto the edge pixel it was clamped to.  The tile's
 // main pass stored z(q) at each pixel q, the correlation of g (zero outside the image)
 // with the flipped taps; z at an outside position e is the gradient the forward's read of
-// e received, so an edge pixel q adds z(e) for every outside e that clamps to q.  One
-// thread per edge pixel of the tile sums those positions in a fixed order, reading g from
-// the staged region (origin (x0 - 8, y0 - R), rows SWP apart: it holds every in-image g
-// position these sums reach) and skipping the terms that fall outside the image.  conv2d:
-// w is the K x K flipped table; separable: NT flipped row taps then NT column taps, the
-// 2D filter being their outer product (the clamped separable forward equals the clamped
-// 2D correlation with it).
+// e received, so an edge pixel q adds z(e) for every outside e that clamps to q.
+//
+// The outside positions that clamp into this tile form up to four bands: left (columns
+// -rx .. -1) and right (W .. W - 1 + rx) over the tile's rows, extended by ry rows at the
+// image's top and bottom (the corners), and top (rows -ry .. -1) and bottom (H .. H - 1 +
+// ry) over the tile's columns.  Step 1 computes z for every band position (one position
+// per thread at a time) into zb; step 2 gives each edge pixel of the tile its positions'
+// sum in a fixed order (left, right, top, bottom band; rows, then columns).  g is read
+// from the staged region (origin (x0 - 8, y0 - R), rows SWP apart), which holds every
+// in-image g position these sums reach; terms outside the image are skipped.  conv2d: w
+// is the K x K flipped table; separable: NT flipped row taps then NT column taps, the 2D
+// filter being their outer product (the clamped separable forward equals the clamped 2D
+// correlation with it).  Ends synchronised (named barrier of the consumers).
 __device__ void fwd_fold_edges(const BImg& im, int x0, int y0, int TW, int TH, const float* st, int SWP,
-                               const float* w, int tid) {
+                               const float* w, float* zb, int tid) {
     const int W = im.W, H = im.H, K = im.K, R = (K - 1) / 2;
     const int rx = (im.kw - 1) / 2, ry = (im.kh - 1) / 2;
     const bool top = y0 == 0, bot = y0 + TH >= H, lft = x0 == 0, rgt = x0 + TW >= W;
     const int tw = min(TW, W - x0), th = min(TH, H - y0);
+    // step 1: z at the band positions
+    const int Y0 = top ? -ry : y0, Y1 = bot ? H - 1 + ry : y0 + th - 1;
+    const int nL = lft ? rx * (Y1 - Y0 + 1) : 0, nR = rgt ? rx * (Y1 - Y0 + 1) : 0;
+    const int nT = top ? ry * tw : 0, nB = bot ? ry * tw : 0;
+    const int nz = nL + nR + nT + nB;
+    for (int k = tid; k < nz; k += kFwdConsumers) {
+        int ex, ey, t = k;
+        if (t < nL) { ey = Y0 + t / rx; ex = -rx + t % rx; }
+        else if ((t -= nL) < nR) { ey = Y0 + t / rx; ex = W + t % rx; }
+        else if ((t -= nR) < nT) { ey = -ry + t / tw; ex = x0 + t % tw; }
+        else { t -= nT; ey = H + t / tw; ex = x0 + t % tw; }
+        const int a0 = max(0, R - ey), a1 = min(K - 1, H - 1 - ey + R);
+        const int b0 = max(0, R - ex), b1 = min(K - 1, W - 1 - ex + R);
+        float z = 0.f;
+        for (int a = a0; a <= a1; ++a) {
+            // g(ex - R + b, ey + a - R) is staged at row ey + a - y0, column ex - R + b - x0 + 8
+            const int gb = (ey + a - y0) * SWP + (ex - R - x0 + 8);
+            if (im.op == IMCL_OP_CONV2D) {
+                const float* wr = w + a * kTapStride;
+                for (int b = b0; b <= b1; ++b) z = __fmaf_rn(wr[b], st[gb + b], z);
+            } else {
+                float rs = 0.f;
+                for (int b = b0; b <= b1; ++b) rs = __fmaf_rn(w[b], st[gb + b], rs);
+                z = __fmaf_rn(w[K + a], rs, z);
+            }
+        }
+        zb[k] = z;
+    }
+    consumer_sync();
+    // step 2: each edge pixel of the tile (top row, bottom row, then the side columns
+    // without the corners) adds the z of the band positions that clamp to it
     const int ntop = top ? tw : 0, nbot = (bot && H > 1) ? tw : 0;
-    const int r0 = top ? 1 : y0, r1 = bot ? H - 2 : y0 + th - 1;   // side rows without the corners
+    const int r0 = top ? 1 : y0, r1 = bot ? H - 2 : y0 + th - 1;
     const int nside = max(0, r1 - r0 + 1);
     const int nl = lft ? nside : 0, nr = (rgt && W > 1) ? nside : 0;
     const int n = ntop + nbot + nl + nr;
@@ -703,33 +740,22 @@ __device__ void fwd_fold_edges(const BImg& im, int x0, int y0, int TW, int TH, c
         else if ((t -= ntop) < nbot) { qx = x0 + t; qy = H - 1; }
         else if ((t -= nbot) < nl) { qx = 0; qy = r0 + t; }
         else { t -= nl; qx = W - 1; qy = r0 + t; }
-        const int xlo = qx == 0 ? -rx : qx, xhi = qx == W - 1 ? W - 1 + rx : qx;
-        const int ylo = qy == 0 ? -ry : qy, yhi = qy == H - 1 ? H - 1 + ry : qy;
+        const int ya = qy == 0 ? -ry : qy, yb = qy == H - 1 ? H - 1 + ry : qy;
         float acc = 0.f;
-        for (int ey = ylo; ey <= yhi; ++ey) {
-            const int a0 = max(0, R - ey), a1 = min(K - 1, H - 1 - ey + R);
-            for (int ex = xlo; ex <= xhi; ++ex) {
-                if (ex == qx && ey == qy) continue;           // the pixel's own term, already stored
-                const int b0 = max(0, R - ex), b1 = min(K - 1, W - 1 - ex + R);
-                float z = 0.f;
-                for (int a = a0; a <= a1; ++a) {
-                    // g(ex - R + b, ey + a - R) is staged at row ey + a - y0, column ex - R + b - x0 + 8
-                    const int gb = (ey + a - y0) * SWP + (ex - R - x0 + 8);
-                    if (im.op == IMCL_OP_CONV2D) {
-                        const float* wr = w + a * kTapStride;
-                        for (int b = b0; b <= b1; ++b) z = __fmaf_rn(wr[b], st[gb + b], z);
-                    } else {
-                        float rs = 0.f;
-                        for (int b = b0; b <= b1; ++b) rs = __fmaf_rn(w[b], st[gb + b], rs);
-                        z = __fmaf_rn(w[K + a], rs, z);
-                    }
-                }
-                acc += z;
-            }
-        }
+        if (qx == 0 && lft)
+            for (int ey = ya; ey <= yb; ++ey)
+                for (int c = 0; c < rx; ++c) acc += zb[(ey - Y0) * rx + c];
+        if (qx == W - 1 && rgt)
+            for (int ey = ya; ey <= yb; ++ey)
+                for (int c = 0; c < rx; ++c) acc += zb[nL + (ey - Y0) * rx + c];
+        if (qy == 0 && top)
+            for (int r = 0; r < ry; ++r) acc += zb[nL + nR + r * tw + (qx - x0)];
+        if (qy == H - 1 && bot)
+            for (int r = 0; r < ry; ++r) acc += zb[nL + nR + nT + r * tw + (qx - x0)];
         float* o = static_cast<float*>(im.out) + (long long)qy * im.out_pitch + qx;
         *o += acc;
     }
+    consumer_sync();
 }
 
 // Persistent forward (kFwdThreads threads: warps 0-7 consume, warp 8 produces).
@@ -821,10 +847,8 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
         consumer_sync();
         batch_fwd_dispatch<PY>(*cur, x0, y0, bx, by, st, tb, w, tid);
         consumer_sync();   // st, tb, w and cur are reused by the next tile
-        if (cur->fold) {   // the tile's own stores are visible to the consumers after the barrier
-            fwd_fold_edges(*cur, x0, y0, 4 * bx, PY * by, st, 4 * bx + 16 + kFwdPitchPad, w, tid);
-            consumer_sync();
-        }
+        if (cur->fold)     // the tile's own stores are visible to the consumers after the barrier
+            fwd_fold_edges(*cur, x0, y0, 4 * bx, PY * by, st, 4 * bx + 16 + kFwdPitchPad, w, tb, tid);
     }
 }
 
@@ -1103,28 +1127,35 @@ __device__ void batch_final(const BImg& im, float* red, int tid, int nth) {
     }
 }
 
-template <int PY>
-__device__ void batch_bwd_dispatch(const BImg& im, const BTile& tl, int bx, int by, float* sm, int tid, int nth) {
+// Work-item classes of the backward phases, one kernel each (a kernel then carries only
+// the device code of its class, which keeps its instruction footprint and register
+// budget to that class).
+enum : int { BCLS_CONV_TAPS = 0, BCLS_SEP_TAPS = 1, BCLS_FINAL = 2 };
+
+template <int PY, int CLS>
+__device__ __forceinline__ void batch_bwd_dispatch(const BImg& im, const BTile& tl, int bx, int by, float* sm, int tid,
+                                                   int nth) {
     const int TW = 4 * bx, TH = PY * by;
-    switch (tl.kind) {
-        case BT_CONV_DW:
-            switch (im.K) {
-                case 3: batch_conv_dw_tile<3>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
-                case 5: batch_conv_dw_tile<5>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
-                case 7: batch_conv_dw_tile<7>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
-                case 9: batch_conv_dw_tile<9>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
-                case 11: batch_conv_dw_tile<11>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
-                case 13: batch_conv_dw_tile<13>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
-                default: batch_conv_dw_tile<15>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
-            }
-            break;
-        case BT_SEP_TAPS: batch_sep_taps_tile<kBatchMaxR>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
-        default: batch_final(im, sm, tid, nth); break;
+    if constexpr (CLS == BCLS_CONV_TAPS) {
+        switch (im.K) {
+            case 3: batch_conv_dw_tile<3>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
+            case 5: batch_conv_dw_tile<5>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
+            case 7: batch_conv_dw_tile<7>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
+            case 9: batch_conv_dw_tile<9>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
+            case 11: batch_conv_dw_tile<11>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
+            case 13: batch_conv_dw_tile<13>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
+            default: batch_conv_dw_tile<15>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
+        }
+    } else if constexpr (CLS == BCLS_SEP_TAPS) {
+        batch_sep_taps_tile<kBatchMaxR>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth);
+    } else {
+        batch_final(im, sm, tid, nth);
     }
 }
 
-// Persistent backward phase: CTAs take work items from one list until it is exhausted.
-template <int PY>
+// Persistent backward phase: CTAs take work items of one class from one list until it is
+// exhausted.
+template <int PY, int CLS>
 __global__ void __launch_bounds__(256, 3)
     k_batch_bwd(const BImg* __restrict__ imgs, const BTile* __restrict__ items, int nitems, int* queue, int bx, int by) {
     extern __shared__ __align__(16) float bsm[];
@@ -1137,7 +1168,7 @@ __global__ void __launch_bounds__(256, 3)
         if (t >= nitems) break;
         const BTile tl = items[t];
         const BImg im = imgs[tl.img];
-        batch_bwd_dispatch<PY>(im, tl, bx, by, bsm, tid, nth);
+        batch_bwd_dispatch<PY, CLS>(im, tl, bx, by, bsm, tid, nth);
         __syncthreads();
     }
 }
