@@ -923,7 +923,7 @@ __device__ void batch_conv_dw_tile(const BImg& im, int x0, int y0, int TW, int T
         for (int i = 0; i < K; ++i) acc[jr][i] = 0.f;
     if (active) wgrad_accumulate<K, D, JR>(gs, TW, xs + C, XW, TW, TH, K, grp * JR, lt, T, acc);
     float* kk = sm + nth * JR * K;                  // the K x K sums, after the combine scratch
-    wgrad_combine<K, JR>(acc, active, sm, K, T, kk, tid, nth);
+    wgrad_combine_wide<K, JR>(acc, active, sm, K, T, kk, tid, nth);
     const int tile = (y0 / TH) * im.tiles_x + x0 / TW;
     const int rx = (im.kw - 1) / 2, ry = (im.kh - 1) / 2;
     float* out = im.part + (size_t)tile * im.kw * im.kh;
@@ -980,7 +980,7 @@ __device__ void batch_row_wgrad(const float* ds, const float* xs, int XW, int TW
 #pragma unroll
     for (int i = 0; i < NR; ++i) acc[0][i] = 0.f;
     wgrad_accumulate<NR, D, 1>(ds + PADR, XW, xs + (PADR - RR - D), XW, TW, TH, 1, 0, tid, nth, acc);
-    wgrad_combine<NR, 1>(acc, true, red, 1, nth, out, tid, nth);
+    wgrad_combine_wide<NR, 1>(acc, true, red, 1, nth, out, tid, nth);
 }
 
 // separable: the tile's tap-gradient partial sums, from one staging of g (zero outside
@@ -988,6 +988,7 @@ __device__ void batch_row_wgrad(const float* ds, const float* xs, int XW, int TW
 //   column taps  dcol[j] = sum_p g(p) t(p + (0, j - rc)),  t = R x the forward row pass;
 //   row taps     drow[i] = sum_p dt(p) x(p + (i - rr, 0)), dt = C^T g the column adjoint
 //                (with the clamp folds on the image's first and last rows).
+// R: the item's compiled radius (>= its column radius rc).
 // The input gradient itself (R^T dt) runs in the pipelined tile kernel, so dt never
 // leaves shared memory.
 template <int R>
@@ -1030,7 +1031,7 @@ __device__ void batch_sep_taps_tile(const BImg& im, int x0, int y0, int TW, int 
 #pragma unroll
         for (int jr = 0; jr < JR; ++jr) acc[jr][0] = 0.f;
         if (active) wgrad_accumulate<1>(gs + R * TW, TW, ts + (R - rc) * TW, TW, TW, TH, nc, grp * JR, lt, T, acc);
-        wgrad_combine<1>(acc, active, red, nc, T, im.part + (size_t)tile * nc, tid, nth);   // ends synchronised
+        wgrad_combine_wide<1>(acc, active, red, nc, T, im.part + (size_t)tile * nc, tid, nth);   // ends synchronised
     }
     if (im.gtaps) {
         // dt = C^T g on the tile's pixels (zero outside the image), 4 pixels of a row per
@@ -1147,7 +1148,15 @@ __device__ __forceinline__ void batch_bwd_dispatch(const BImg& im, const BTile& 
             default: batch_conv_dw_tile<15>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
         }
     } else if constexpr (CLS == BCLS_SEP_TAPS) {
-        batch_sep_taps_tile<kBatchMaxR>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth);
+        switch (im.K) {   // the staged halo rows follow the item's radius
+            case 3: batch_sep_taps_tile<1>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
+            case 5: batch_sep_taps_tile<2>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
+            case 7: batch_sep_taps_tile<3>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
+            case 9: batch_sep_taps_tile<4>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
+            case 11: batch_sep_taps_tile<5>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
+            case 13: batch_sep_taps_tile<6>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
+            default: batch_sep_taps_tile<7>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
+        }
     } else {
         batch_final(im, sm, tid, nth);
     }

@@ -100,4 +100,35 @@ __device__ void wgrad_combine(const float (&acc)[JR][KW], bool active, float* re
     __syncthreads();
 }
 
+// The same sums as wgrad_combine, for kernels that combine once per tile: each tap's T
+// partial sums are split over S lanes of one warp (S a power of two, at most 32, as many
+// as the block has threads for), each lane adding every S-th of them in order, and the S
+// lane sums are added in a fixed shuffle tree.  The order depends only on T, S and the
+// block size, so results stay deterministic.  Ends synchronised.
+template <int KW, int JR = WgCfg<KW>::JR>
+__device__ void wgrad_combine_wide(const float (&acc)[JR][KW], bool active, float* red, int kh, int T, float* out,
+                                   int tid, int nth) {
+    __syncthreads();
+#pragma unroll
+    for (int jr = 0; jr < JR; ++jr)
+#pragma unroll
+        for (int i = 0; i < KW; ++i) red[tid * JR * KW + jr * KW + i] = active ? acc[jr][i] : 0.f;
+    __syncthreads();
+    const int nq = KW * kh;
+    int S = 1;
+    while (S < 32 && S * 2 * nq <= nth) S *= 2;
+    for (int base = 0; base < nq * S; base += nth) {          // uniform trip count
+        const int idx = base + tid, q = idx / S, sub = idx - q * S;
+        float sum = 0.f;
+        if (q < nq) {
+            const int j = q / KW, i = q - j * KW;
+            const int gq = j / JR, jr = j - gq * JR;
+            for (int r = sub; r < T; r += S) sum += red[(gq * T + r) * JR * KW + jr * KW + i];
+        }
+        for (int o = S >> 1; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (q < nq && sub == 0) out[q] = sum;
+    }
+    __syncthreads();
+}
+
 }  // namespace imcl
