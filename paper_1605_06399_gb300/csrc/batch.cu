@@ -94,28 +94,34 @@ static imcl_status upload(T** dst, const std::vector<T>& src, std::vector<void*>
     return IMCL_OK;
 }
 
+template <bool ADJ = false>
 static const void* fwd_kernel(int py) {
-    return py == 4 ? (const void*)k_batch_fwd<4> : (const void*)k_batch_fwd<2>;
+    return py == 4 ? (const void*)k_batch_fwd<4, ADJ> : (const void*)k_batch_fwd<2, ADJ>;
 }
 
 // One persistent launch of the pipelined tile kernel over `tiles`, taking indices from the
-// counter `queue` (reset first), with the image descriptors `imgs`.
+// counter `queue` (reset first), with the image descriptors `imgs`.  ADJ: the backward's
+// input-gradient instantiation.
+template <bool ADJ>
 static imcl_status launch_fwd_list(const Batch& b, const BImg* imgs, int* queue, const BFwdTile* tiles, int ntiles,
                                    int py, int bx, int by, cudaStream_t s) {
     const size_t smem = batch_smem_bytes(py, bx, by);
-    const int occ = cached_occupancy(fwd_kernel(py), kFwdThreads, (int)smem);
+    const void* fn = fwd_kernel<ADJ>(py);
+    imcl_status st = set_smem_limit(fn, (int)smem);
+    if (st != IMCL_OK) return st;
+    const int occ = cached_occupancy(fn, kFwdThreads, (int)smem);
     if (occ <= 0) return fail(IMCL_ERR_UNSUPPORTED, "batch: kernel cannot be resident");
     const int grid = std::max(1, std::min(ntiles, occ * b.dev->sm_count));
     cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), s);
     if (e != cudaSuccess) return cuda_fail(e, "batch queue reset");
-    if (py == 4) k_batch_fwd<4><<<grid, kFwdThreads, smem, s>>>(imgs, tiles, ntiles, queue, bx, by, b.dev->status);
-    else k_batch_fwd<2><<<grid, kFwdThreads, smem, s>>>(imgs, tiles, ntiles, queue, bx, by, b.dev->status);
+    if (py == 4) k_batch_fwd<4, ADJ><<<grid, kFwdThreads, smem, s>>>(imgs, tiles, ntiles, queue, bx, by, b.dev->status);
+    else k_batch_fwd<2, ADJ><<<grid, kFwdThreads, smem, s>>>(imgs, tiles, ntiles, queue, bx, by, b.dev->status);
     return cuda_fail(cudaGetLastError(), "batch tile launch");
 }
 
 static imcl_status launch_fwd(const Batch& b, const BFwdTile* tiles, int ntiles, int py, int bx, int by,
                               cudaStream_t s) {
-    return launch_fwd_list(b, b.dimgs, b.queue, tiles, ntiles, py, bx, by, s);
+    return launch_fwd_list<false>(b, b.dimgs, b.queue, tiles, ntiles, py, bx, by, s);
 }
 
 template <int CLS>
@@ -287,7 +293,7 @@ static imcl_status plan_backward(Batch* b) {
     cudaStreamWaitEvent(b->br_stream[0], b->ev_fork, 0);
     cudaStreamWaitEvent(b->br_stream[1], b->ev_fork, 0);
     imcl_status lst = IMCL_OK, s1, s2, s3, s4;
-    if (ndx > 0) lst = launch_fwd_list(*b, ddx, b->queue + 4, ddxt, ndx, b->py, b->bx, b->by, b->br_stream[0]);
+    if (ndx > 0) lst = launch_fwd_list<true>(*b, ddx, b->queue + 4, ddxt, ndx, b->py, b->bx, b->by, b->br_stream[0]);
     s1 = launch_bwd_list<BCLS_CONV_TAPS>(*b, dc, (int)lc.size(), b->queue + 1, b->cap_stream);
     s2 = launch_bwd_list<BCLS_SEP_TAPS>(*b, dsp, (int)ls.size(), b->queue + 2, b->br_stream[1]);
     cudaEventRecord(b->ev_join[1], b->br_stream[1]);

@@ -401,8 +401,11 @@ __device__ __forceinline__ void fwd_fill(const BFwdTile& ft, const BImg* imgs, u
 
 // Producer: this lane's entries of the tile's tap table (conv: K rows kTapStride apart
 // with the caller's kh x kw centred, zeros elsewhere; sep: NT row taps then NT column
-// taps, centred).
+// taps, centred).  ADJ: the input-gradient kernel, whose tiles may ask for the taps
+// rotated by 180 degrees.
+template <bool ADJ>
 __device__ __forceinline__ void fwd_load_taps(const BFwdTile& ft, int lane, float* tv) {
+    const bool flip = ADJ && ft.flip;
     const int K = ft.K;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -414,16 +417,16 @@ __device__ __forceinline__ void fwd_load_taps(const BFwdTile& ft, int lane, floa
                 const int R = (K - 1) / 2;
                 const int sj = j - (R - (ft.kh - 1) / 2), sc = c - (R - (ft.kw - 1) / 2);
                 if (sj >= 0 && sj < ft.kh && sc >= 0 && sc < ft.kw)
-                    v = __ldg(ft.taps + (ft.flip ? (ft.kh - 1 - sj) * ft.kw + (ft.kw - 1 - sc) : sj * ft.kw + sc));
+                    v = __ldg(ft.taps + (flip ? (ft.kh - 1 - sj) * ft.kw + (ft.kw - 1 - sc) : sj * ft.kw + sc));
             }
         } else if (i < 2 * K) {
             const int R = (K - 1) / 2;
             if (i < K) {
                 const int o = i - (R - (ft.kw - 1) / 2);
-                if (o >= 0 && o < ft.kw) v = __ldg(ft.taps + (ft.flip ? ft.kw - 1 - o : o));
+                if (o >= 0 && o < ft.kw) v = __ldg(ft.taps + (flip ? ft.kw - 1 - o : o));
             } else {
                 const int o = i - K - (R - (ft.kh - 1) / 2);
-                if (o >= 0 && o < ft.kh) v = __ldg(ft.taps2 + (ft.flip ? ft.kh - 1 - o : o));
+                if (o >= 0 && o < ft.kh) v = __ldg(ft.taps2 + (flip ? ft.kh - 1 - o : o));
             }
         }
         tv[k] = v;
@@ -758,8 +761,10 @@ __device__ void fwd_fold_edges(const BImg& im, int x0, int y0, int TW, int TH, c
     consumer_sync();
 }
 
-// Persistent forward (kFwdThreads threads: warps 0-7 consume, warp 8 produces).
-template <int PY>
+// Persistent forward (kFwdThreads threads: warps 0-7 consume, warp 8 produces).  ADJ:
+// the instantiation that runs the input-gradient tiles of the backward (flipped taps,
+// clamp folds); the forward's own instantiation carries neither.
+template <int PY, bool ADJ>
 __global__ void __launch_bounds__(kFwdThreads, 2)
     k_batch_fwd(const BImg* __restrict__ imgs, const BFwdTile* __restrict__ tiles, int ntiles, int* queue, int bx,
                 int by, int* status) {
@@ -800,7 +805,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
                 raw_next = ntiles;
             }
             float tv[8];
-            if (cur < ntiles) fwd_load_taps(ft, lane, tv);
+            if (cur < ntiles) fwd_load_taps<ADJ>(ft, lane, tv);
             bool ok = true;
             if (i >= 2) ok = mbar_wait(&empty[b], ((i >> 1) - 1) & 1u, status) && !*abort_flag;
             if (!__all_sync(0xffffffffu, ok)) {
@@ -847,8 +852,10 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
         consumer_sync();
         batch_fwd_dispatch<PY>(*cur, x0, y0, bx, by, st, tb, w, tid);
         consumer_sync();   // st, tb, w and cur are reused by the next tile
-        if (cur->fold)     // the tile's own stores are visible to the consumers after the barrier
-            fwd_fold_edges(*cur, x0, y0, 4 * bx, PY * by, st, 4 * bx + 16 + kFwdPitchPad, w, tb, tid);
+        if constexpr (ADJ) {
+            if (cur->fold)     // the tile's own stores are visible to the consumers after the barrier
+                fwd_fold_edges(*cur, x0, y0, 4 * bx, PY * by, st, 4 * bx + 16 + kFwdPitchPad, w, tb, tid);
+        }
     }
 }
 
