@@ -387,12 +387,23 @@ def error_report(dev):
 
 # ----------------------------------------------------------------------------- other stencils
 
+def _flush_l2(flush, r):
+    """Leave L2 cold and clean before a timed call: overwrite one buffer larger than L2,
+    then read another one.  After the write alone L2 is full of that buffer's dirty lines,
+    and the timed kernel would pay for writing them back to HBM as its own lines evict
+    them; the read pushes them out before the timed region and leaves clean lines only."""
+    w, rd = flush
+    w.fill_(float(r))
+    rd.sum()
+
+
 def _median_ms(fn, reps, flush=None, calls=8):
     """Median device time of one fn() call.  `calls` calls are recorded in a CUDA graph
     (so host-side argument marshalling is not timed), the graph is replayed `reps` times
     between CUDA events on the current stream, and each replay is divided by `calls`.
-    `flush` (a buffer larger than L2) is rewritten before each replay, outside the events,
-    and then one call is recorded per replay so that every timed call starts cold."""
+    With `flush` (two buffers larger than L2), L2 is flushed before each replay, outside
+    the events (_flush_l2), and one call is recorded per replay so that every timed call
+    starts cold."""
     import torch
     if flush is not None and calls > 1:
         calls = 1
@@ -403,7 +414,7 @@ def _median_ms(fn, reps, flush=None, calls=8):
         ts = []
         for r in range(reps):
             if flush is not None:
-                flush.fill_(float(r))
+                _flush_l2(flush, r)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             fn()
@@ -421,7 +432,7 @@ def _median_ms(fn, reps, flush=None, calls=8):
     ts = []
     for r in range(reps):
         if flush is not None:
-            flush.fill_(float(r))
+            _flush_l2(flush, r)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         g.replay()
@@ -466,7 +477,8 @@ def extra_stencils(hbm_gbs, fp32_peak, budget, imad_peak=None, bf16_tflops=FALLB
     from paper_1605_06399_gb300 import Batch, _abi, ops, synth
     out = {}
     dev = torch.device("cuda")
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    flush = (torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev),    # 256 MB each, > L2
+             torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev))
     plain = {"kind": _abi.KIND_PLAIN, "bx": 16, "by": 16}
 
     # 512x512 u8, 3x3 integer taps: launch-latency bound, timed by CUDA-graph replay
