@@ -135,10 +135,24 @@ std::vector<imcl_variant> expand_shapes(const std::vector<imcl_variant>& base) {
     return out;
 }
 
+// Reads n 16-byte words (the second half of the L2 flush): the loads evict what the
+// first half's memset left dirty in L2.  The sink is written only for one sum value, so
+// the loads are kept but nothing depends on the data.
+__global__ void k_l2_read(const uint4* __restrict__ p, size_t n, unsigned int* sink) {
+    unsigned int acc = 0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const uint4 v = __ldg(p + i);
+        acc ^= v.x ^ v.y ^ v.z ^ v.w;
+    }
+    if (acc == 0x9e3779b9u) atomicOr(sink, 1u);
+}
+
 // Runs candidates of one tuning job: the PLAIN kernel's output is the reference; a
 // candidate counts if it launches, sets no device error and matches the reference
 // within the job's tolerance; its time is the median of `reps` CUDA-event timings after
-// a warm-up, with L2 flushed between runs when the working set would stay in L2.
+// a warm-up, with L2 flushed between runs when the working set would stay in L2: a
+// buffer of twice L2 is overwritten and another of the same size is read, so each timed
+// run starts with L2 holding neither its own data nor dirty lines it would write back.
 class TuneRunner {
 public:
     TuneRunner(TuneJob& job, int reps, cudaStream_t s) : job_(job), reps_(reps < 1 ? 1 : reps), s_(s) {}
@@ -152,7 +166,7 @@ public:
         cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, 0);
         if ((double)job_.working_set_bytes < 2.0 * l2) {
             flush_bytes_ = (size_t)l2 * 2;
-            if (job_.scratch.alloc(&flush_, flush_bytes_) != IMCL_OK) { flush_ = nullptr; flush_bytes_ = 0; }
+            if (job_.scratch.alloc(&flush_, 2 * flush_bytes_) != IMCL_OK) { flush_ = nullptr; flush_bytes_ = 0; }
         }
         imcl_status st = job_.scratch.alloc(reinterpret_cast<void**>(&res_), 4 * sizeof(unsigned int));
         if (st != IMCL_OK) return st;
@@ -201,7 +215,12 @@ private:
     imcl_status time_one(const imcl_variant& v, double* ms_out) {
         std::vector<float> t;
         for (int r = 0; r < reps_ + 1; ++r) {
-            if (flush_) cudaMemsetAsync(flush_, r & 0xff, flush_bytes_, s_);
+            if (flush_) {
+                cudaMemsetAsync(flush_, r & 0xff, flush_bytes_, s_);
+                k_l2_read<<<4 * dev_->sm_count, 256, 0, s_>>>(
+                    reinterpret_cast<const uint4*>(static_cast<uint8_t*>(flush_) + flush_bytes_), flush_bytes_ / 16,
+                    res_ + 3);
+            }
             cudaEventRecord(e0_, s_);
             imcl_status rs = job_.run(v, s_);
             cudaEventRecord(e1_, s_);
