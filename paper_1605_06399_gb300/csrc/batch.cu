@@ -247,7 +247,10 @@ static imcl_status plan_backward(Batch* b) {
                     if (it.op == IMCL_OP_CONV2D) lc.push_back(BTile{i, BT_CONV_DW, x, y});
                     else ls.push_back(BTile{i, BT_SEP_TAPS, x, y});
                 }
-        if (im.gtaps || im.gtaps2) l3.push_back(BTile{i, BT_FINAL, 0, 0});
+        if (im.gtaps || im.gtaps2) {
+            const int nchunk = it.op == IMCL_OP_CONV2D ? (im.kw * im.kh + kFinalChunk - 1) / kFinalChunk : 1;
+            for (int c = 0; c < nchunk; ++c) l3.push_back(BTile{i, BT_FINAL, c, 0});
+        }
     }
     if (!any) return IMCL_OK;
     // costliest first within each phase (large filters, then the rest in plan order)
@@ -258,6 +261,10 @@ static imcl_status plan_backward(Batch* b) {
     };
     by_cost(lc);
     by_cost(ls);
+    // the reductions: images with the most tiles first
+    std::stable_sort(l3.begin(), l3.end(), [&](const BTile& a, const BTile& c) {
+        return b->himgs[a.img].tiles_x * b->himgs[a.img].tiles_y > b->himgs[c.img].tiles_x * b->himgs[c.img].tiles_y;
+    });
     imcl_status st;
     // the descriptors now carry gradient pointers: refresh the device copy
     cudaError_t e = cudaMemcpy(b->dimgs, b->himgs.data(), b->himgs.size() * sizeof(BImg), cudaMemcpyHostToDevice);

@@ -25,6 +25,7 @@ namespace imcl {
 
 constexpr int kBatchMaxK = 15;    // conv2d side
 constexpr int kBatchMaxR = 7;     // separable radius
+constexpr int kFinalChunk = 32;  // conv2d taps per reduction work item
 
 // One image operation of the batch (device copy).  Pitches in elements.  16-byte
 // aligned: the forward copies descriptors into shared memory with bulk copies.
@@ -56,7 +57,7 @@ enum : int {
     BT_FWD = 0,        // forward tile
     BT_CONV_DW = 1,    // conv2d: tap-gradient partial sums of one tile
     BT_SEP_TAPS = 3,   // sep: column- and row-tap partial sums of one tile
-    BT_FINAL = 5,      // reduce one image's partial sums to its tap gradients
+    BT_FINAL = 5,      // reduce one image's partial sums to its tap gradients (x0: tap chunk)
 };
 
 struct BTile {
@@ -1099,16 +1100,20 @@ __device__ void batch_sep_taps_tile(const BImg& im, int x0, int y0, int TW, int 
     }
 }
 
-// Reduce an image's tap partial sums over its tiles into the gradients.  The order of the
-// additions depends only on the tile count, the tap count n and the block size: G =
-// min(nth / n, tiles) thread groups take the tiles t = g, g + G, ..., each thread keeps
-// eight running sums over consecutive rounds of its tiles (eight loads in flight) and adds
-// them in a fixed tree, and the group sums are added in group order.
-__device__ void batch_final(const BImg& im, float* red, int tid, int nth) {
+// Reduce an image's tap partial sums over its tiles into the gradients.  A conv2d image's
+// taps are split into work items of kFinalChunk taps (chunk = the item's x0), so a large
+// filter over many tiles spreads over several CTAs.  The order of the additions depends
+// only on the tile count, the item's tap count m and the block size: G = min(nth / m,
+// tiles) thread groups take the tiles t = g, g + G, ..., each thread keeps eight running
+// sums over consecutive rounds of its tiles (eight loads in flight) and adds them in a
+// fixed tree, and the group sums are added in group order.
+__device__ void batch_final(const BImg& im, int chunk, float* red, int tid, int nth) {
     const int ntiles = im.tiles_x * im.tiles_y;
-    auto reduce = [&](const float* part, int n, float* out) {
-        const int G = max(1, min(nth / n, ntiles));
-        const int g = tid / n, q = tid - g * n;
+    // taps q0 .. q1 - 1 of a set of n: part[t * n + q] summed over the tiles t
+    auto reduce = [&](const float* part, int n, int q0, int q1, float* out) {
+        const int m = q1 - q0;
+        const int G = max(1, min(nth / m, ntiles));
+        const int g = tid / m, q = q0 + (tid - g * m);
         if (g < G) {
             float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             int t = g;
@@ -1117,21 +1122,22 @@ __device__ void batch_final(const BImg& im, float* red, int tid, int nth) {
                 for (int u = 0; u < 8; ++u) a[u] += part[(size_t)(t + u * G) * n + q];
             }
             for (; t < ntiles; t += G) a[0] += part[(size_t)t * n + q];
-            red[g * n + q] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+            red[tid] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
         }
         __syncthreads();
-        if (tid < n) {
+        if (tid < m) {
             float s = 0.f;
-            for (int k = 0; k < G; ++k) s += red[k * n + tid];
-            out[tid] = s;
+            for (int k = 0; k < G; ++k) s += red[k * m + tid];
+            out[q0 + tid] = s;
         }
         __syncthreads();
     };
     if (im.op == IMCL_OP_CONV2D) {
-        if (im.gtaps) reduce(im.part, im.kw * im.kh, im.gtaps);
+        const int n = im.kw * im.kh, q0 = chunk * kFinalChunk;
+        if (im.gtaps) reduce(im.part, n, q0, min(n, q0 + kFinalChunk), im.gtaps);
     } else {
-        if (im.gtaps2) reduce(im.part, im.kh, im.gtaps2);                                // column taps
-        if (im.gtaps) reduce(im.part + (size_t)ntiles * im.kh, im.kw, im.gtaps);        // row taps
+        if (im.gtaps2) reduce(im.part, im.kh, 0, im.kh, im.gtaps2);                                  // column taps
+        if (im.gtaps) reduce(im.part + (size_t)ntiles * im.kh, im.kw, 0, im.kw, im.gtaps);          // row taps
     }
 }
 
@@ -1165,7 +1171,7 @@ __device__ __forceinline__ void batch_bwd_dispatch(const BImg& im, const BTile& 
             default: batch_sep_taps_tile<7>(im, tl.x0, tl.y0, TW, TH, sm, tid, nth); break;
         }
     } else {
-        batch_final(im, sm, tid, nth);
+        batch_final(im, tl.x0, sm, tid, nth);
     }
 }
 
